@@ -1,0 +1,200 @@
+/*
+ * eod_abe.h - C ABI of the GB300 (sm_103a) implementation of power-free
+ * EOD-ABE: efficient orthogonal decomposition with automatic basis
+ * extraction (Xu, Shen, Liu, Jia; arXiv 2506.22713).
+ *
+ * The method (paper Sec. 3): for A (m x n) and a tolerance eps > 0,
+ *   Alg. 1 (BasisExt)  draws Gaussian blocks Omega_j (n x k), forms
+ *                      Y_j = (I - Q Q^T) A Omega_j, factors Y_j = P_j T_j and
+ *                      stops at the first diagonal entry |T_j(l,l)| <= eps,
+ *                      keeping Q = [Q, P_j(:, 1:l-1)]; r = columns of Q;
+ *   Alg. 2, tau = 0    C = Q^T A;  C^T = V R (QR);  R^T = Qh Dh (QR);
+ *                      U = Q Qh, D = Dh;  A ~= A_hat = U D V^T = Q C.
+ * The relative Frobenius error ||A - A_hat||_F / ||A||_F is the RelErr of
+ * Sec. 4.1.
+ *
+ * Conventions shared by every call:
+ *  - Matrices are column-major: entry (i, j) of A is A[i + j*lda].
+ *  - Unless a parameter says "host", pointers are CUDA device pointers in the
+ *    current device's context.  The library never modifies A.
+ *  - Work is issued on opts->stream (a cudaStream_t; NULL = the legacy
+ *    default stream).  Calls that return a rank return after synchronising
+ *    that stream, because the rank is a host value.
+ *  - Status codes: EOD_OK on success; on any other status the output
+ *    pointer is left NULL (or untouched) and nothing needs freeing.
+ *  - Not thread-safe per stream: concurrent calls must use different streams.
+ */
+#ifndef EOD_ABE_H
+#define EOD_ABE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define EOD_API __attribute__((visibility("default")))
+#else
+#define EOD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EOD_OK = 0,
+    EOD_EINVAL = 1,        /* bad argument: sizes, lda, tol <= 0 or not finite,
+                              power_iters != 0, unknown enum value, NULL pointer */
+    EOD_ENOMEM = 2,        /* device or pinned host allocation failed */
+    EOD_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    EOD_ENONFINITE = 4,    /* A holds a NaN or an infinity */
+    EOD_ETIMEOUT = 5,      /* a bounded device-side wait gave up (kernel returned
+                              an error flag instead of waiting forever) */
+    EOD_EPRECISION = 6,    /* a Cholesky factorisation broke down beyond the
+                              shifted fallback's reach */
+    EOD_EUNSUPPORTED = 7   /* valid request this build does not support */
+} eod_status;
+
+typedef enum { EOD_F64 = 0, EOD_F32 = 1 } eod_dtype;
+
+typedef enum {
+    EOD_PLAIN = 0,         /* every contraction in the storage type of A
+                              (FP64 DFMA for EOD_F64, FP32 FFMA for EOD_F32);
+                              Gram/Cholesky/rank test/core in FP64 */
+    EOD_MIXED_BF16 = 1     /* sketch, projection and reconstruction on tcgen05
+                              tensor cores with A split as A_hi + A_lo (BF16,
+                              round to nearest even) and FP32 accumulation;
+                              Gram/Cholesky/rank test/core in FP64 */
+} eod_precision;
+
+typedef enum {
+    EOD_TOL_ABS = 0,       /* eps = tol: the test |T(l,l)| <= eps of Alg. 1 as printed */
+    EOD_TOL_REL_FRO = 1    /* eps = tol * ||A||_F */
+} eod_tol_mode;
+
+/* Options.  eod_opts_default() fills: F64, PLAIN, TOL_ABS, block_k 0 (= 32),
+ * power_iters 0, compute_err 1, stream NULL, batch_index 0. */
+typedef struct {
+    int32_t a_dtype;       /* eod_dtype of A (and of A_hat in eod_abe_reconstruct) */
+    int32_t precision;     /* eod_precision */
+    int32_t tol_mode;      /* eod_tol_mode */
+    int32_t block_k;       /* block size k of Alg. 1 (1..128); 0 selects 32 */
+    int32_t power_iters;   /* tau of Alg. 2; only 0 (power-free) is accepted */
+    int32_t compute_err;   /* nonzero: compute RelErr (one more pass over A) */
+    void *stream;          /* cudaStream_t */
+    uint64_t batch_index;  /* third counter word of the Omega draw (Philox) */
+} eod_opts;
+
+/* Result of one factorisation.  All matrix fields are device pointers owned
+ * by the struct and released by eod_abe_free().  U, V, Q and C hold FP64 for
+ * a_dtype EOD_F64 with EOD_PLAIN and FP32 otherwise (f_dtype says which);
+ * D is always FP64.  For rank 0 every matrix pointer is NULL. */
+typedef struct {
+    int64_t m, n, rank;
+    int32_t f_dtype;       /* eod_dtype of U, V, Q, C */
+    int32_t precision;     /* eod_precision used */
+    void *U;               /* m x rank, ld m: U = Q Qh, orthonormal columns */
+    double *D;             /* rank x rank, ld rank: upper triangular, positive diagonal */
+    void *V;               /* n x rank, ld n: orthonormal columns */
+    void *Q;               /* m x rank, ld m: the BasisExt basis */
+    void *C;               /* n x rank, ld n: C^T = A^T Q (the projection B^T) */
+    double *tdiag;         /* host array, ntdiag entries: every computed |T_j(l,l)|, in order */
+    int64_t ntdiag;
+    double rel_err;        /* ||A - Q C||_F / ||A||_F, or -1 if not computed */
+    double norm_a;         /* ||A||_F */
+    double eps;            /* threshold used: tol or tol*||A||_F */
+    double t_margin;       /* min over tested entries of |log10(|T(l,l)| / eps)| */
+    int64_t blocks;        /* blocks of Alg. 1 processed */
+    int64_t restarts;      /* columns settled by the explicit residual check */
+    int64_t block_k;       /* k used */
+} eod_factors;
+
+/* Fills *opts with the defaults listed above. */
+EOD_API void eod_opts_default(eod_opts *opts);
+
+/* Alg. 2 with tau = 0 (paper Sec. 3.2) on device matrix A (m x n, ld lda >=
+ * m, FP64), threshold eps = tol (absolute), Omega from `seed`, default
+ * options.  On EOD_OK *out receives a new eod_factors (free with
+ * eod_abe_free).  Errors: EOD_EINVAL for m < 1, n < 1, lda < m, tol <= 0 or
+ * non-finite, out == NULL; EOD_ENONFINITE if A holds NaN/Inf; EOD_ENOMEM,
+ * EOD_ECUDA as described above.  A zero matrix gives EOD_OK with rank 0.
+ * m < n is accepted (the paper assumes m >= n and notes that the method
+ * carries over); the rank never exceeds min(m, n). */
+EOD_API eod_status eod_abe_factor(const void *A, int64_t m, int64_t n, int64_t lda,
+                          double tol, uint64_t seed, eod_factors **out);
+
+/* As eod_abe_factor with explicit options (opts may be NULL = defaults). */
+EOD_API eod_status eod_abe_factor_ex(const void *A, int64_t m, int64_t n, int64_t lda,
+                             double tol, uint64_t seed, const eod_opts *opts,
+                             eod_factors **out);
+
+/* Same computation from a HOST matrix A_host (m x n, ld lda, type
+ * opts->a_dtype); the library copies it to the device, factors it and copies
+ * the factors back into caller-owned host buffers: U_host (m x cap, ld m),
+ * D_host (cap x cap, ld cap, FP64), V_host (n x cap, ld n), where cap >=
+ * min(m, n) is the capacity the caller allocated; U/V are written in
+ * f_dtype (FP64 for F64+PLAIN, else FP32).  *rank and *rel_err receive the
+ * rank and RelErr.  Any of U_host, D_host, V_host may be NULL to skip that
+ * copy.  Pinned host memory makes the copies asynchronous; pageable memory
+ * works too.  Errors as eod_abe_factor_ex, plus EOD_EINVAL for cap <
+ * min(m, n) when a factor buffer is given. */
+EOD_API eod_status eod_abe_factor_host(const void *A_host, int64_t m, int64_t n, int64_t lda,
+                               double tol, uint64_t seed, const eod_opts *opts,
+                               void *U_host, double *D_host, void *V_host, int64_t cap,
+                               int64_t *rank, double *rel_err);
+
+/* Rebuilds A_hat = U D V^T, the product of the three factors (paper Sec. 1),
+ * into device buffer A_hat (m x n, ld ld_hat >= m), written in opts->a_dtype
+ * (NULL opts: the factors' f_dtype).  Rank 0 writes zeros.  Errors:
+ * EOD_EINVAL for NULL f or A_hat or ld_hat < m; EOD_EUNSUPPORTED when the
+ * requested type differs from f_dtype. */
+EOD_API eod_status eod_abe_reconstruct(const eod_factors *f, void *A_hat, int64_t ld_hat,
+                               const eod_opts *opts);
+
+/* Factors `count` independent matrices (the per-image use of Sec. 4.1) in
+ * one call.  A, m, n, lda, out and per_item are HOST arrays of length count;
+ * A[i] is a device pointer.  Item i draws Omega with batch_index = i.  Every
+ * item gets its own status in per_item[i] and, on EOD_OK, its own factors in
+ * out[i] (free each with eod_abe_free).  Returns EOD_OK if every item
+ * succeeded, else the first failing item's status; EOD_EINVAL for count < 1
+ * or NULL arrays. */
+EOD_API eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const int64_t *n,
+                                  const int64_t *lda, int64_t count, double tol, uint64_t seed,
+                                  const eod_opts *opts, eod_factors **out, eod_status *per_item);
+
+/* Writes columns col0 .. col0+ncols-1 of the Gaussian test matrix Omega
+ * (n rows; Alg. 1 step 3) for (seed, batch) into device buffer out (n x
+ * ncols, ld n, FP64) on `stream`.  The draw: Philox4x32-10 (Salmon et al.,
+ * SC'11) with counter (row, column, batch, 0) and key (seed low 32 bits, seed
+ * high 32 bits); u = (x + 1/2) 2^-32 for the first two output words; Box-
+ * Muller sqrt(-2 ln u1) cos(2 pi u2) in FP64, rounded to the nearest BF16
+ * value (ties to even).  Errors: EOD_EINVAL for n < 1, ncols < 1, col0 < 0,
+ * out == NULL, or a row/column index beyond 2^32 - 1. */
+EOD_API eod_status eod_abe_omega(int64_t n, int64_t col0, int64_t ncols, uint64_t seed,
+                         uint64_t batch, double *out, void *stream);
+
+/* Releases the factors and the struct.  NULL is a no-op. */
+EOD_API void eod_abe_free(eod_factors *f);
+
+/* Static English text for a status code. */
+EOD_API const char *eod_status_string(eod_status s);
+
+/* Entries stored by U (m x r), upper-triangular D and V (n x r):
+ * r(m + n) + r(r + 1)/2 (paper Sec. 1). */
+EOD_API int64_t eod_abe_storage_entries(int64_t m, int64_t n, int64_t r);
+
+/* Flops of the paper's cost model for tau = 0 (Sec. 3.4, "2mnr + mr^2 +
+ * 2nr^2 + 2r^3 + 4mrk" multiply-adds, two flops each), plus 2mnr for the
+ * reconstruction when with_err is nonzero. */
+EOD_API double eod_abe_model_flops(int64_t m, int64_t n, int64_t r, int64_t k, int32_t with_err);
+
+/* Test hook: the n-th device allocation from now (n >= 1) fails as if the
+ * device were out of memory; n <= 0 clears the hook.  Host-side only. */
+EOD_API void eod_abe_debug_fail_alloc_after(int32_t n);
+
+/* Build identification (static string). */
+EOD_API const char *eod_abe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EOD_ABE_H */

@@ -1,0 +1,144 @@
+// Shared device helpers and the internal (C++) interface between the
+// translation units of the EOD-ABE library.  Nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/eod_abe.h"
+
+namespace eod {
+
+#define EOD_CUDA_TRY(...)                                          \
+    do {                                                            \
+        cudaError_t eod_err_ = (__VA_ARGS__);                              \
+        if (eod_err_ != cudaSuccess) return eod_err_;               \
+    } while (0)
+
+constexpr double kU64 = 1.1102230246251565e-16;   // 2^-53, unit roundoff of binary64
+constexpr double kU32 = 5.9604644775390625e-08;   // 2^-24, unit roundoff of binary32
+constexpr int kNumSMs = 152;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_or(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of one double per thread (blockDim.x a multiple of 32, at
+// most 1024).  Every thread gets the total.
+__device__ __forceinline__ double block_sum(double v, double *sh32) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh32[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double t = (threadIdx.x < nw) ? sh32[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh32[0] = t;
+    __syncthreads();
+    return sh32[0];
+}
+
+template <typename T> __device__ __forceinline__ double to_f64(T x) { return (double)x; }
+
+// --------------------------------------------------------------------------
+// Bump allocator over one device buffer (the per-call workspace).
+// --------------------------------------------------------------------------
+struct Scratch {
+    char *base = nullptr;
+    size_t size = 0, used = 0, high = 0;
+    void *take(size_t bytes) {
+        size_t off = (used + 255) & ~size_t(255);
+        if (off + bytes > size) return nullptr;
+        used = off + bytes;
+        if (used > high) high = used;
+        return base + off;
+    }
+    size_t mark() const { return used; }
+    void release(size_t m) { used = m; }
+};
+
+// --------------------------------------------------------------------------
+// GEMM (SIMT, any of TA/TB/TC in {float, double}, accumulation Acc):
+//   C (M x N) = alpha * op(A) * op(B) + beta * C,  column-major,
+//   op(X) = X or X^T.  Split-K through the scratch partials when the tile
+//   grid would not fill the GPU; the split partials are summed in a fixed
+//   order, so results are deterministic.
+// --------------------------------------------------------------------------
+enum GemmEpilogue { EPI_STORE = 0, EPI_ERR = 1 };
+
+struct GemmExtra {
+    bool upper_only = false;   // only tiles that touch the upper triangle of C
+    bool a_upper = false;      // op(A) upper triangular: skip its zero K range
+    bool b_upper = false;      // op(B) upper triangular: skip its zero K range
+    int epilogue = EPI_STORE;
+    const void *ref = nullptr; // EPI_ERR: reference matrix R (M x N, type TC)
+    int64_t ldref = 0;
+    double *err_partials = nullptr; // EPI_ERR: one double per CTA (gridDim.x*gridDim.y)
+    int max_split = 64;
+};
+
+template <typename TA, typename TB, typename TC, typename Acc>
+cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                 const TA *A, int64_t lda, const TB *B, int64_t ldb, double beta, TC *C,
+                 int64_t ldc, const GemmExtra &x, Scratch *ws, cudaStream_t s);
+
+// number of CTAs the EPI_ERR form of gemm() launches for an M x N output
+int64_t gemm_err_ctas(int64_t M, int64_t N);
+
+// --------------------------------------------------------------------------
+// Streaming kernels
+// --------------------------------------------------------------------------
+// ||A||_F^2 partials (FP64) + non-finite flag; then finalize into out[0] =
+// ||A||_F, flag[0] |= 1 if a NaN/Inf was seen.
+template <typename T>
+cudaError_t fro_norm(const T *A, int64_t m, int64_t n, int64_t lda, double *out,
+                     int *flag, Scratch *ws, cudaStream_t s);
+// out = sqrt(sum(partials[0..count))) / denom (denom read from device pointer or 1)
+cudaError_t finalize_sqrt_sum(const double *partials, int64_t count, const double *denom,
+                              double *out, cudaStream_t s);
+// Omega columns col0.. into out (n x ncols, ld n) in type T (values are BF16-exact)
+template <typename T>
+cudaError_t omega_fill(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, uint64_t batch,
+                       T *out, int64_t ldo, cudaStream_t s);
+template <typename TS, typename TD>
+cudaError_t copy_matrix(const TS *src, int64_t lds, TD *dst, int64_t ldd, int64_t rows,
+                        int64_t cols, bool transpose, cudaStream_t s);
+template <typename T>
+cudaError_t scale_column(T *x, int64_t m, const double *inv_norm_src, cudaStream_t s);
+template <typename T>
+cudaError_t fill_zero(T *x, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s);
+
+// --------------------------------------------------------------------------
+// Small dense factorisations (one CTA)
+// --------------------------------------------------------------------------
+enum CholCode { CHOL_ALL = 0, CHOL_BELOW = 1, CHOL_UNCERTAIN = 2, CHOL_FAIL = 3 };
+
+// Cholesky G = R^T R of the w x w matrix G (upper triangle read, FP64) with
+// the rank decision of Alg. 1 steps 6-11 when decide != 0:
+//   info[0] = p (leading columns factored), info[1] = CholCode,
+// R (p x p upper, ld ldr) and its inverse Rinv (ld ldr); the original
+// diagonal of G is used for the rounding margin.
+cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2,
+                       double delta_coef, double rho, double shift, double *R,
+                       double *Rinv, int64_t ldr, int *info, cudaStream_t s);
+// tdiag[j] = |R1(j,j) * R2(j,j)|, j < p
+cudaError_t tdiag_product(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
+                          double *tdiag, cudaStream_t s);
+// trace(G) for the shift of shifted CholQR
+cudaError_t trace_sum(const double *G, int64_t ldg, int64_t p, double *out, cudaStream_t s);
+
+}  // namespace eod

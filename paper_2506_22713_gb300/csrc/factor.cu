@@ -1,0 +1,734 @@
+// Host orchestration of power-free EOD-ABE on one GPU and the exported C ABI
+// (include/eod_abe.h).
+//
+//   Alg. 1 (BasisExt)      omega_fill -> gemm (Y = A Omega_j)
+//                          -> 2 x [gemm (S = Q^T Y), gemm (Y -= Q S)]
+//                          -> gemm (G = Y^T Y) -> chol_small (pivots + rank test)
+//                          -> gemm (P1 = Y R1^{-1}) -> gemm (G2) -> chol_small
+//                          -> gemm (P = P1 R2^{-1}) appended to Q
+//                          undecided pivots: explicit CGS2 residual of that column
+//   Alg. 2 steps 8-11      gemm (C^T = A^T Q), [gemm with fused error: Q C vs A],
+//                          CholQR2 (C^T = V R), CholQR2 (R^T = Qh D), gemm (U = Q Qh)
+//
+// The kernels live in gemm_simt.cu, stream_kernels.cu and chol.cu (plain
+// path) and tc_gemm.cu (tensor-core path).  The rank test reads a pivot
+// decision back to the host once per sub-panel; everything else stays on the
+// device.
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+namespace eod {
+
+static int g_fail_alloc_after = 0;
+
+// Stream-ordered device allocations owned by one call.
+struct Arena {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Arena(cudaStream_t st) : s(st) {}
+    template <typename T>
+    eod_status get(T **p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        if (g_fail_alloc_after > 0) {
+            if (--g_fail_alloc_after == 0) return EOD_ENOMEM;
+        }
+        void *q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, sizeof(T) * count, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? EOD_ENOMEM : EOD_ECUDA;
+        }
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return EOD_OK;
+    }
+    void keep(void *p) {  // ownership moves to the caller's factors
+        for (auto &q : ptrs)
+            if (q == p) q = nullptr;
+    }
+    ~Arena() {
+        for (void *q : ptrs)
+            if (q) cudaFreeAsync(q, s);
+    }
+};
+
+#define EOD_TRY(...)                                    \
+    do {                                                 \
+        eod_status eod_st_ = (__VA_ARGS__);                     \
+        if (eod_st_ != EOD_OK) return eod_st_;           \
+    } while (0)
+#define EOD_CU(...)                                     \
+    do {                                                 \
+        cudaError_t eod_ce_ = (__VA_ARGS__);                    \
+        if (eod_ce_ != cudaSuccess) {                    \
+            return cuda_status(eod_ce_);                 \
+        }                                                \
+    } while (0)
+
+static eod_status cuda_status(cudaError_t e) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? EOD_ENOMEM : EOD_ECUDA;
+}
+
+// Pinned host mirror of the small device results read once per decision.
+struct HostMirror {
+    int *info = nullptr;      // [2]
+    double *val = nullptr;    // [4]
+    int *flag = nullptr;      // [1]
+    eod_status init() {
+        void *p = nullptr;
+        if (cudaMallocHost(&p, 64) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
+        info = (int *)p;
+        flag = info + 2;
+        val = (double *)((char *)p + 16);
+        return EOD_OK;
+    }
+    ~HostMirror() { if (info) cudaFreeHost(info); }
+};
+
+template <typename T> struct Traits;
+template <> struct Traits<double> { static constexpr int dtype = EOD_F64; static constexpr double rho = 1e-10; };
+template <> struct Traits<float> { static constexpr int dtype = EOD_F32; static constexpr double rho = 1e-6; };
+
+// ---------------------------------------------------------------------------
+// Blocked CholQR pass on W (rows x p, FP64 Gram, FP64 R):  G = W^T W,
+// R = chol(G + shift I) by 64-column blocks (left-looking), W <- W R^{-1}.
+// Each diagonal block's inverse is kept for the triangular solve.
+// Returns EOD_EPRECISION (without touching W) if a pivot is not positive.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CoreWork {
+    double *G = nullptr, *R = nullptr, *Rp = nullptr, *Inv = nullptr, *trace = nullptr;
+    T *InvT = nullptr, *Tmp = nullptr;
+    int *info = nullptr;
+    int64_t pcap = 0, rows_cap = 0;
+};
+
+static constexpr int kNB = 64;
+
+template <typename T>
+static eod_status chol_blocked(CoreWork<T> &w, int64_t p, double shift, HostMirror &hm, Scratch *ws,
+                               cudaStream_t s, double *Rout) {
+    const int64_t nblk = (p + kNB - 1) / kNB;
+    GemmExtra ex;
+    EOD_CU(fill_zero<double>(Rout, p, p, p, s));
+    for (int64_t J = 0; J < nblk; ++J) {
+        const int64_t j0 = J * kNB, jb = std::min<int64_t>(kNB, p - j0);
+        if (j0 > 0)
+            EOD_CU((gemm<double, double, double, double>(true, false, jb, p - j0, j0, -1.0, Rout + j0 * p, p,
+                                                          Rout + j0 * p, p, 1.0, w.G + j0 + j0 * p, p, ex, ws, s)));
+        EOD_CU(chol_small(w.G + j0 + j0 * p, p, (int)jb, 0, 0.0, 0.0, 0.0, shift, w.Rp, w.Inv + J * kNB * kNB,
+                          kNB, w.info + 2 * J, s));
+        EOD_CU(copy_matrix<double, double>(w.Rp, kNB, Rout + j0 + j0 * p, p, jb, jb, false, s));
+        if (j0 + jb < p)
+            EOD_CU((gemm<double, double, double, double>(true, false, jb, p - j0 - jb, jb, 1.0,
+                                                          w.Inv + J * kNB * kNB, kNB, w.G + j0 + (j0 + jb) * p, p,
+                                                          0.0, Rout + j0 + (j0 + jb) * p, p, ex, ws, s)));
+    }
+    std::vector<int> infos(2 * nblk);
+    EOD_CU(cudaMemcpyAsync(infos.data(), w.info, sizeof(int) * 2 * nblk, cudaMemcpyDeviceToHost, s));
+    EOD_CU(cudaStreamSynchronize(s));
+    for (int64_t J = 0; J < nblk; ++J) {
+        const int64_t jb = std::min<int64_t>(kNB, p - J * kNB);
+        if (infos[2 * J] != jb || infos[2 * J + 1] != CHOL_ALL) return EOD_EPRECISION;
+    }
+    return EOD_OK;
+}
+
+// W <- W R^{-1}, R upper p x p (ld p) with diagonal-block inverses in w.Inv.
+template <typename T>
+static eod_status trsm_right(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64_t p, const double *R,
+                             Scratch *ws, cudaStream_t s) {
+    const int64_t nblk = (p + kNB - 1) / kNB;
+    GemmExtra ex;
+    GemmExtra exb;
+    exb.b_upper = true;
+    for (int64_t J = 0; J < nblk; ++J) {
+        const int64_t j0 = J * kNB, jb = std::min<int64_t>(kNB, p - j0);
+        if (j0 > 0) {
+            const T *Rb = nullptr;
+            if (std::is_same<T, double>::value) {
+                Rb = (const T *)(R + j0 * p);
+                EOD_CU((gemm<T, T, T, T>(false, false, rows, jb, j0, -1.0, W, ldw, Rb, p, 1.0, W + j0 * ldw, ldw,
+                                         ex, ws, s)));
+            } else {
+                EOD_CU((copy_matrix<double, T>(R + j0 * p, p, w.InvT, j0, j0, jb, false, s)));
+                EOD_CU((gemm<T, T, T, T>(false, false, rows, jb, j0, -1.0, W, ldw, w.InvT, j0, 1.0, W + j0 * ldw,
+                                         ldw, ex, ws, s)));
+            }
+        }
+        const T *Inv;
+        if (std::is_same<T, double>::value) {
+            Inv = (const T *)(w.Inv + J * kNB * kNB);
+        } else {
+            EOD_CU((copy_matrix<double, T>(w.Inv + J * kNB * kNB, kNB, w.InvT, kNB, jb, jb, false, s)));
+            Inv = w.InvT;
+        }
+        EOD_CU((gemm<T, T, T, T>(false, false, rows, jb, jb, 1.0, W + j0 * ldw, ldw, Inv, kNB, 0.0, w.Tmp, rows,
+                                 exb, ws, s)));
+        EOD_CU((copy_matrix<T, T>(w.Tmp, rows, W + j0 * ldw, ldw, rows, jb, false, s)));
+    }
+    return EOD_OK;
+}
+
+// CholQR2 (shifted CholQR3 when the first Cholesky breaks down; Fukaya,
+// Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SISC 2020): W (rows x p) is
+// replaced by its orthonormal factor and Rout (p x p, ld p) by R with
+// W_in = W_out R, diag(R) > 0.
+template <typename T>
+static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64_t p, double *Rout,
+                          HostMirror &hm, Scratch *ws, cudaStream_t s) {
+    GemmExtra sym;
+    sym.upper_only = true;
+    double *Racc = w.R;  // running product
+    int passes = 2;
+    double shift = 0.0;
+    for (int pass = 0; pass < passes; ++pass) {
+        EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
+        double *Rpass = (pass == 0) ? Rout : w.Rp + kNB * kNB;  // pass factor storage
+        eod_status st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
+        if (st == EOD_EPRECISION && pass == 0 && shift == 0.0) {
+            // shifted CholQR: shift = 11 (rows p + p (p+1)) u ||W||_2^2, ||W||_2^2 <= trace(G)
+            EOD_CU(trace_sum(w.G, p, p, w.trace, s));
+            EOD_CU(cudaMemcpyAsync(hm.val, w.trace, sizeof(double), cudaMemcpyDeviceToHost, s));
+            EOD_CU(cudaStreamSynchronize(s));
+            const double u = std::is_same<T, float>::value ? kU32 : kU64;
+            shift = 11.0 * ((double)rows * p + (double)p * (p + 1)) * u * hm.val[0];
+            passes = 3;
+            EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
+            st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
+        }
+        if (st != EOD_OK) return st;
+        shift = 0.0;
+        EOD_TRY(trsm_right(w, W, rows, ldw, p, Rpass, ws, s));
+        if (pass > 0) {
+            // Racc = Rpass * Rout (both upper), then Rout = Racc
+            GemmExtra tri;
+            tri.a_upper = true;
+            tri.b_upper = true;
+            EOD_CU((gemm<double, double, double, double>(false, false, p, p, p, 1.0, Rpass, p, Rout, p, 0.0, Racc, p,
+                                                          tri, ws, s)));
+            EOD_CU((copy_matrix<double, double>(Racc, p, Rout, p, p, p, false, s)));
+        }
+    }
+    return EOD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The plain path (T = double: FP64 everywhere; T = float: FP32 contractions,
+// FP64 Gram / Cholesky / rank test / core R factors).
+// ---------------------------------------------------------------------------
+struct Result {
+    int64_t rank = 0, blocks = 0, restarts = 0;
+    double norm_a = 0, eps = 0, rel_err = -1;
+    std::vector<double> tdiag;
+};
+
+template <typename T>
+static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
+                              const eod_opts &o, cudaStream_t s, Arena &ar, eod_factors *F) {
+    const int64_t cap = std::min(m, n);
+    int64_t k = o.block_k > 0 ? o.block_k : 32;
+    if (k > cap) k = cap;
+    const bool mixed = (o.precision == EOD_MIXED_BF16);
+
+    HostMirror hm;
+    EOD_TRY(hm.init());
+
+    // ---- workspace ----
+    Scratch ws;
+    const size_t ws_bytes = (size_t)48 << 20;
+    EOD_TRY(ar.get((char **)&ws.base, ws_bytes));
+    ws.size = ws_bytes;
+
+    T *Qb, *Om, *Y, *S, *T1, *RinvT;
+    double *G, *R1, *R1i, *R2, *R2i, *tdiag_d, *dsc;
+    int *iflag, *info;
+    EOD_TRY(ar.get(&Qb, (size_t)m * cap));
+    EOD_TRY(ar.get(&Om, (size_t)n * k));
+    EOD_TRY(ar.get(&Y, (size_t)m * k));
+    EOD_TRY(ar.get(&S, (size_t)cap * k));
+    EOD_TRY(ar.get(&T1, (size_t)m * k));
+    EOD_TRY(ar.get(&RinvT, (size_t)k * k));
+    EOD_TRY(ar.get(&G, (size_t)k * k));
+    EOD_TRY(ar.get(&R1, (size_t)k * k));
+    EOD_TRY(ar.get(&R1i, (size_t)k * k));
+    EOD_TRY(ar.get(&R2, (size_t)k * k));
+    EOD_TRY(ar.get(&R2i, (size_t)k * k));
+    EOD_TRY(ar.get(&tdiag_d, (size_t)cap + 1));
+    EOD_TRY(ar.get(&dsc, 8));
+    EOD_TRY(ar.get(&iflag, 4));
+    EOD_TRY(ar.get(&info, 2));
+    double *d_norm = dsc, *d_t = dsc + 1, *d_err = dsc + 2;
+
+    // ---- S0: ||A||_F and finiteness ----
+    EOD_CU(cudaMemsetAsync(iflag, 0, sizeof(int) * 4, s));
+    EOD_CU(fro_norm<T>(A, m, n, lda, d_norm, iflag, &ws, s));
+    EOD_CU(cudaMemcpyAsync(hm.val, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    EOD_CU(cudaMemcpyAsync(hm.flag, iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EOD_CU(cudaStreamSynchronize(s));
+    if (hm.flag[0]) return EOD_ENONFINITE;
+    const double norm_a = hm.val[0];
+    const double eps = (o.tol_mode == EOD_TOL_REL_FRO) ? tol * norm_a : tol;
+    F->norm_a = norm_a;
+    F->eps = eps;
+    F->block_k = k;
+
+    MixedOps<T> mx;
+    if (mixed) EOD_TRY(mx.prepare(A, m, n, lda, ar, s));
+
+    // ---- Alg. 1 ----
+    const double eps2 = eps * eps;
+    const double delta_coef = 64.0 * ((double)k + std::sqrt((double)m)) * kU64;
+    GemmExtra ex, sym, bup;
+    sym.upper_only = true;
+    bup.b_upper = true;
+    int64_t kept = 0, blocks = 0, restarts = 0;
+    std::vector<double> tdiag;
+    tdiag.reserve(cap + 1);
+    bool stop = (norm_a == 0.0);
+    if (stop) tdiag.push_back(0.0);
+
+    while (!stop && kept < cap) {
+        const int64_t f = std::min(k, cap - kept);
+        ++blocks;
+        // steps 3-4: Omega_j and Y = A Omega_j
+        if (mixed) {
+            EOD_TRY(mx.sketch(kept, f, seed, o.batch_index, Y, m, s));
+        } else {
+            EOD_CU(omega_fill<T>(n, kept, f, seed, o.batch_index, Om, n, s));
+            EOD_CU((gemm<T, T, T, T>(false, false, m, f, n, 1.0, A, lda, Om, n, 0.0, Y, m, ex, &ws, s)));
+        }
+        int64_t cur = 0;
+        while (!stop && cur < f) {
+            T *Yc = Y + cur * m;
+            const int64_t wdt = f - cur;
+            // step 4: Y <- (I - Q Q^T) Y, twice
+            for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+                EOD_CU((gemm<T, T, T, T>(true, false, kept, wdt, m, 1.0, Qb, m, Yc, m, 0.0, S, cap, ex, &ws, s)));
+                EOD_CU((gemm<T, T, T, T>(false, false, m, wdt, kept, -1.0, Qb, m, S, cap, 1.0, Yc, m, ex, &ws, s)));
+            }
+            // step 5 (pass 1) + steps 6-11: Gram, Cholesky with the rank test
+            EOD_CU((gemm<T, T, double, double>(true, false, wdt, wdt, m, 1.0, Yc, m, Yc, m, 0.0, G, k, sym, &ws, s)));
+            EOD_CU(chol_small(G, k, (int)wdt, 1, eps2, delta_coef, Traits<T>::rho, 0.0, R1, R1i, k, info, s));
+            EOD_CU(cudaMemcpyAsync(hm.info, info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+            EOD_CU(cudaStreamSynchronize(s));
+            const int p = hm.info[0], code = hm.info[1];
+            if (p > 0) {
+                // P1 = Y(:,1:p) R1^{-1}; pass 2: G2 = P1^T P1 = R2^T R2; P = P1 R2^{-1}
+                const T *Ri = (const T *)R1i;
+                if (!std::is_same<T, double>::value) {
+                    EOD_CU((copy_matrix<double, T>(R1i, k, RinvT, k, p, p, false, s)));
+                    Ri = RinvT;
+                }
+                EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, Yc, m, Ri, k, 0.0, T1, m, bup, &ws, s)));
+                EOD_CU((gemm<T, T, double, double>(true, false, p, p, m, 1.0, T1, m, T1, m, 0.0, G, k, sym, &ws, s)));
+                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, R2i, k, info, s));
+                const T *Ri2 = (const T *)R2i;
+                if (!std::is_same<T, double>::value) {
+                    EOD_CU((copy_matrix<double, T>(R2i, k, RinvT, k, p, p, false, s)));
+                    Ri2 = RinvT;
+                }
+                EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, T1, m, Ri2, k, 0.0, Qb + kept * m, m, bup, &ws, s)));
+                EOD_CU(tdiag_product(R1, R2, k, info, tdiag_d, s));
+                std::vector<double> td(p);
+                EOD_CU(cudaMemcpyAsync(hm.info, info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+                EOD_CU(cudaMemcpyAsync(td.data(), tdiag_d, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
+                EOD_CU(cudaStreamSynchronize(s));
+                if (hm.info[0] != p || hm.info[1] != CHOL_ALL) return EOD_EPRECISION;
+                for (int j = 0; j < p; ++j) tdiag.push_back(td[j]);
+                kept += p;
+            }
+            if (code == CHOL_ALL) {
+                cur = f;
+            } else if (code == CHOL_BELOW) {
+                // d_p < eps^2 - delta: |T(p,p)| <= eps for certain
+                stop = true;
+                // record the explicit residual norm of that column (diagnostics only)
+                tdiag.push_back(-1.0);
+                T *z = Yc + (int64_t)p * m;
+                for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+                    EOD_CU((gemm<T, T, T, T>(true, false, kept, 1, m, 1.0, Qb, m, z, m, 0.0, S, cap, ex, &ws, s)));
+                    EOD_CU((gemm<T, T, T, T>(false, false, m, 1, kept, -1.0, Qb, m, S, cap, 1.0, z, m, ex, &ws, s)));
+                }
+                EOD_CU(fro_norm<T>(z, m, 1, m, d_t, iflag + 1, &ws, s));
+                EOD_CU(cudaMemcpyAsync(hm.val, d_t, sizeof(double), cudaMemcpyDeviceToHost, s));
+                EOD_CU(cudaStreamSynchronize(s));
+                tdiag.back() = hm.val[0];
+            } else {
+                // undecided pivot: settle column p by an explicit CGS2 residual norm
+                T *z = Yc + (int64_t)p * m;
+                for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+                    EOD_CU((gemm<T, T, T, T>(true, false, kept, 1, m, 1.0, Qb, m, z, m, 0.0, S, cap, ex, &ws, s)));
+                    EOD_CU((gemm<T, T, T, T>(false, false, m, 1, kept, -1.0, Qb, m, S, cap, 1.0, z, m, ex, &ws, s)));
+                }
+                EOD_CU(fro_norm<T>(z, m, 1, m, d_t, iflag + 1, &ws, s));
+                EOD_CU(cudaMemcpyAsync(hm.val, d_t, sizeof(double), cudaMemcpyDeviceToHost, s));
+                EOD_CU(cudaStreamSynchronize(s));
+                const double t = hm.val[0];
+                tdiag.push_back(t);
+                ++restarts;
+                if (!(t > eps)) {
+                    stop = true;
+                } else {
+                    EOD_CU(scale_column<T>(z, m, d_t, s));
+                    EOD_CU((copy_matrix<T, T>(z, m, Qb + kept * m, m, m, 1, false, s)));
+                    kept += 1;
+                    cur += p + 1;
+                }
+            }
+        }
+    }
+    const int64_t r = kept;
+    F->rank = r;
+    F->blocks = blocks;
+    F->restarts = restarts;
+
+    // t_margin over the tested entries
+    double margin = INFINITY;
+    for (size_t i = 0; i < tdiag.size(); ++i)
+        if (tdiag[i] > 0.0 && eps > 0.0) margin = std::min(margin, std::fabs(std::log10(tdiag[i] / eps)));
+    F->t_margin = margin;
+    F->ntdiag = (int64_t)tdiag.size();
+    F->tdiag = (double *)std::malloc(sizeof(double) * std::max<size_t>(tdiag.size(), 1));
+    if (!F->tdiag) return EOD_ENOMEM;
+    if (!tdiag.empty()) std::memcpy(F->tdiag, tdiag.data(), sizeof(double) * tdiag.size());
+
+    if (r == 0) {
+        F->rel_err = (norm_a > 0.0) ? 1.0 : 0.0;
+        if (!o.compute_err) F->rel_err = -1.0;
+        return EOD_OK;
+    }
+
+    // ---- Alg. 2 step 8: C^T = A^T Q (n x r) ----
+    T *Ct, *V, *U, *Rt;
+    double *D, *Rc;
+    EOD_TRY(ar.get(&Ct, (size_t)n * r));
+    EOD_TRY(ar.get(&V, (size_t)n * r));
+    EOD_TRY(ar.get(&U, (size_t)m * r));
+    EOD_TRY(ar.get(&Rt, (size_t)r * r));
+    EOD_TRY(ar.get(&D, (size_t)r * r));
+    EOD_TRY(ar.get(&Rc, (size_t)r * r));
+    if (mixed) {
+        EOD_TRY(mx.project(Qb, r, Ct, s));
+    } else {
+        EOD_CU((gemm<T, T, T, T>(true, false, n, r, m, 1.0, A, lda, Qb, m, 0.0, Ct, n, ex, &ws, s)));
+    }
+
+    // ---- reconstruction error: || A - Q C ||_F / ||A||_F ----
+    if (o.compute_err) {
+        if (mixed) {
+            EOD_TRY(mx.recon_error(Qb, r, Ct, d_norm, d_err, s));
+        } else {
+            const int64_t nct = gemm_err_ctas(m, n);
+            double *part;
+            EOD_TRY(ar.get(&part, (size_t)nct));
+            GemmExtra ee;
+            ee.epilogue = EPI_ERR;
+            ee.ref = A;
+            ee.ldref = lda;
+            ee.err_partials = part;
+            EOD_CU((gemm<T, T, T, T>(false, true, m, n, r, 1.0, Qb, m, Ct, n, 0.0, (T *)nullptr, m, ee, &ws, s)));
+            EOD_CU(finalize_sqrt_sum(part, nct, d_norm, d_err, s));
+        }
+    }
+
+    // ---- steps 9-11 ----
+    CoreWork<T> cw;
+    cw.pcap = r;
+    const int64_t nblk = (r + kNB - 1) / kNB;
+    EOD_TRY(ar.get(&cw.G, (size_t)r * r));
+    EOD_TRY(ar.get(&cw.R, (size_t)r * r));
+    EOD_TRY(ar.get(&cw.Rp, (size_t)kNB * kNB + (size_t)r * r));
+    EOD_TRY(ar.get(&cw.Inv, (size_t)nblk * kNB * kNB));
+    EOD_TRY(ar.get(&cw.trace, 1));
+    EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kNB) * kNB));
+    EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kNB));
+    EOD_TRY(ar.get(&cw.info, (size_t)2 * nblk));
+    EOD_CU((copy_matrix<T, T>(Ct, n, V, n, n, r, false, s)));
+    EOD_TRY(cholqr2(cw, V, n, n, r, Rc, hm, &ws, s));                 // C^T = V R
+    EOD_CU((copy_matrix<double, T>(Rc, r, Rt, r, r, r, true, s)));    // R^T
+    EOD_TRY(cholqr2(cw, Rt, r, r, r, D, hm, &ws, s));                 // R^T = Qh D
+    EOD_CU((gemm<T, T, T, T>(false, false, m, r, r, 1.0, Qb, m, Rt, r, 0.0, U, m, ex, &ws, s)));  // U = Q Qh
+
+    if (o.compute_err) {
+        EOD_CU(cudaMemcpyAsync(hm.val, d_err, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    EOD_CU(cudaStreamSynchronize(s));
+    F->rel_err = o.compute_err ? hm.val[0] : -1.0;
+
+    F->U = U; ar.keep(U);
+    F->V = V; ar.keep(V);
+    F->D = D; ar.keep(D);
+    F->Q = Qb; ar.keep(Qb);
+    F->C = Ct; ar.keep(Ct);
+    return EOD_OK;
+}
+
+eod_status factor_mixed_from_f64(const double *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
+                                 const eod_opts &o, cudaStream_t s, eod_factors *F);
+
+static eod_status validate(const void *A, int64_t m, int64_t n, int64_t lda, double tol, const eod_opts &o) {
+    if (!A || m < 1 || n < 1 || lda < m) return EOD_EINVAL;
+    if (!(tol > 0.0) || !std::isfinite(tol)) return EOD_EINVAL;
+    if (o.power_iters != 0) return EOD_EINVAL;
+    if (o.a_dtype != EOD_F64 && o.a_dtype != EOD_F32) return EOD_EINVAL;
+    if (o.precision != EOD_PLAIN && o.precision != EOD_MIXED_BF16) return EOD_EINVAL;
+    if (o.tol_mode != EOD_TOL_ABS && o.tol_mode != EOD_TOL_REL_FRO) return EOD_EINVAL;
+    if (o.block_k < 0 || o.block_k > 128) return EOD_EINVAL;
+    if (m > 0x7FFFFFFFLL || n > 0x7FFFFFFFLL) return EOD_EINVAL;
+    return EOD_OK;
+}
+
+static void free_factors_device(eod_factors *f) {
+    if (!f) return;
+    void *ptrs[] = {f->U, f->V, f->Q, f->C, (void *)f->D};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    std::free(f->tdiag);
+    f->U = f->V = f->Q = f->C = nullptr;
+    f->D = nullptr;
+    f->tdiag = nullptr;
+}
+
+eod_status factor_any(const void *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
+                      const eod_opts *opts, eod_factors **out) {
+    if (!out) return EOD_EINVAL;
+    *out = nullptr;
+    eod_opts o;
+    eod_opts_default(&o);
+    if (opts) o = *opts;
+    EOD_TRY(validate(A, m, n, lda, tol, o));
+    cudaStream_t s = (cudaStream_t)o.stream;
+    eod_factors *F = (eod_factors *)std::calloc(1, sizeof(eod_factors));
+    if (!F) return EOD_ENOMEM;
+    F->m = m;
+    F->n = n;
+    F->precision = o.precision;
+    F->f_dtype = (o.a_dtype == EOD_F64 && o.precision == EOD_PLAIN) ? EOD_F64 : EOD_F32;
+    F->rel_err = -1.0;
+    eod_status st;
+    {
+        Arena ar(s);
+        if (o.precision == EOD_PLAIN && o.a_dtype == EOD_F64)
+            st = factor_impl<double>((const double *)A, m, n, lda, tol, seed, o, s, ar, F);
+        else if (o.a_dtype == EOD_F32)
+            st = factor_impl<float>((const float *)A, m, n, lda, tol, seed, o, s, ar, F);
+        else
+            st = factor_mixed_from_f64((const double *)A, m, n, lda, tol, seed, o, s, F);
+        if (st != EOD_OK) {
+            // the arena frees its own buffers; the kept ones belong to F
+            free_factors_device(F);
+        }
+    }
+    if (st != EOD_OK) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        std::free(F);
+        return st;
+    }
+    *out = F;
+    return EOD_OK;
+}
+
+// FP64 input on the mixed path: widen nothing, narrow A to FP32 once (the
+// tensor-core path splits FP32 values into BF16 pairs).
+eod_status factor_mixed_from_f64(const double *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
+                                 const eod_opts &o, cudaStream_t s, eod_factors *F) {
+    float *A32 = nullptr;
+    cudaError_t e = cudaMallocAsync(&A32, sizeof(float) * (size_t)m * n, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
+    eod_status st = EOD_OK;
+    if (copy_matrix<double, float>(A, lda, A32, m, m, n, false, s) != cudaSuccess) st = EOD_ECUDA;
+    if (st == EOD_OK) {
+        Arena ar(s);
+        eod_opts o2 = o;
+        o2.a_dtype = EOD_F32;
+        st = factor_impl<float>(A32, m, n, m, tol, seed, o2, s, ar, F);
+        if (st != EOD_OK) free_factors_device(F);
+    }
+    cudaFreeAsync(A32, s);
+    return st;
+}
+
+template <typename T>
+static eod_status reconstruct_impl(const eod_factors *f, T *Ahat, int64_t ld, cudaStream_t s) {
+    const int64_t m = f->m, n = f->n, r = f->rank;
+    if (r == 0) {
+        EOD_CU(fill_zero<T>(Ahat, m, n, ld, s));
+        return EOD_OK;
+    }
+    Arena ar(s);
+    Scratch ws;
+    EOD_TRY(ar.get((char **)&ws.base, (size_t)32 << 20));
+    ws.size = (size_t)32 << 20;
+    T *W, *Dt;
+    EOD_TRY(ar.get(&W, (size_t)m * r));
+    EOD_TRY(ar.get(&Dt, (size_t)r * r));
+    EOD_CU((copy_matrix<double, T>(f->D, r, Dt, r, r, r, false, s)));
+    GemmExtra ex, bu;
+    bu.b_upper = true;
+    const T *U = (const T *)f->U, *V = (const T *)f->V;
+    EOD_CU((gemm<T, T, T, T>(false, false, m, r, r, 1.0, U, m, Dt, r, 0.0, W, m, bu, &ws, s)));     // W = U D
+    EOD_CU((gemm<T, T, T, T>(false, true, m, n, r, 1.0, W, m, V, n, 0.0, Ahat, ld, ex, &ws, s)));  // A_hat = W V^T
+    return EOD_OK;
+}
+
+}  // namespace eod
+
+// ===========================================================================
+// Exported C ABI
+// ===========================================================================
+using namespace eod;
+
+extern "C" {
+
+void eod_opts_default(eod_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->a_dtype = EOD_F64;
+    o->precision = EOD_PLAIN;
+    o->tol_mode = EOD_TOL_ABS;
+    o->block_k = 0;
+    o->power_iters = 0;
+    o->compute_err = 1;
+    o->stream = nullptr;
+    o->batch_index = 0;
+}
+
+eod_status eod_abe_factor(const void *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
+                          eod_factors **out) {
+    return factor_any(A, m, n, lda, tol, seed, nullptr, out);
+}
+
+eod_status eod_abe_factor_ex(const void *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
+                             const eod_opts *opts, eod_factors **out) {
+    return factor_any(A, m, n, lda, tol, seed, opts, out);
+}
+
+eod_status eod_abe_factor_host(const void *A_host, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
+                               const eod_opts *opts, void *U_host, double *D_host, void *V_host, int64_t cap,
+                               int64_t *rank, double *rel_err) {
+    eod_opts o;
+    eod_opts_default(&o);
+    if (opts) o = *opts;
+    if (!A_host || !rank || m < 1 || n < 1 || lda < m) return EOD_EINVAL;
+    if ((U_host || D_host || V_host) && cap < std::min(m, n)) return EOD_EINVAL;
+    if (o.a_dtype != EOD_F64 && o.a_dtype != EOD_F32) return EOD_EINVAL;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const size_t es = o.a_dtype == EOD_F64 ? 8 : 4;
+    void *Ad = nullptr;
+    if (g_fail_alloc_after > 0 && --g_fail_alloc_after == 0) return EOD_ENOMEM;
+    if (cudaMallocAsync(&Ad, es * (size_t)m * n, s) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
+    eod_status st = EOD_OK;
+    if (cudaMemcpy2DAsync(Ad, es * m, A_host, es * lda, es * m, n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = EOD_ECUDA;
+    eod_factors *F = nullptr;
+    if (st == EOD_OK) st = factor_any(Ad, m, n, m, tol, seed, &o, &F);
+    if (st == EOD_OK) {
+        const int64_t r = F->rank;
+        const size_t fs = F->f_dtype == EOD_F64 ? 8 : 4;
+        *rank = r;
+        if (rel_err) *rel_err = F->rel_err;
+        if (r > 0) {
+            if (U_host && cudaMemcpyAsync(U_host, F->U, fs * (size_t)m * r, cudaMemcpyDeviceToHost, s) != cudaSuccess) st = EOD_ECUDA;
+            if (V_host && cudaMemcpyAsync(V_host, F->V, fs * (size_t)n * r, cudaMemcpyDeviceToHost, s) != cudaSuccess) st = EOD_ECUDA;
+            if (D_host && cudaMemcpy2DAsync(D_host, sizeof(double) * cap, F->D, sizeof(double) * r, sizeof(double) * r, r,
+                                            cudaMemcpyDeviceToHost, s) != cudaSuccess) st = EOD_ECUDA;
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) st = EOD_ECUDA;
+        eod_abe_free(F);
+    }
+    cudaFreeAsync(Ad, s);
+    cudaStreamSynchronize(s);
+    return st;
+}
+
+eod_status eod_abe_reconstruct(const eod_factors *f, void *A_hat, int64_t ld_hat, const eod_opts *opts) {
+    if (!f || !A_hat || ld_hat < f->m) return EOD_EINVAL;
+    eod_opts o;
+    eod_opts_default(&o);
+    o.a_dtype = f->f_dtype;
+    if (opts) o = *opts;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    eod_status st;
+    if (o.a_dtype == EOD_F64 && f->f_dtype == EOD_F64)
+        st = reconstruct_impl<double>(f, (double *)A_hat, ld_hat, s);
+    else if (o.a_dtype == EOD_F32 && f->f_dtype == EOD_F32)
+        st = reconstruct_impl<float>(f, (float *)A_hat, ld_hat, s);
+    else
+        return EOD_EUNSUPPORTED;
+    if (st == EOD_OK && cudaStreamSynchronize(s) != cudaSuccess) st = EOD_ECUDA;
+    return st;
+}
+
+eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const int64_t *n, const int64_t *lda,
+                                  int64_t count, double tol, uint64_t seed, const eod_opts *opts, eod_factors **out,
+                                  eod_status *per_item) {
+    if (!A || !m || !n || !lda || !out || !per_item || count < 1) return EOD_EINVAL;
+    eod_opts o;
+    eod_opts_default(&o);
+    if (opts) o = *opts;
+    eod_status first = EOD_OK;
+    for (int64_t i = 0; i < count; ++i) {
+        eod_opts oi = o;
+        oi.batch_index = (uint64_t)i;
+        out[i] = nullptr;
+        per_item[i] = factor_any(A[i], m[i], n[i], lda[i], tol, seed, &oi, &out[i]);
+        if (per_item[i] != EOD_OK && first == EOD_OK) first = per_item[i];
+    }
+    return first;
+}
+
+eod_status eod_abe_omega(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, uint64_t batch, double *out,
+                         void *stream) {
+    if (n < 1 || ncols < 1 || col0 < 0 || !out) return EOD_EINVAL;
+    if (n > 0xFFFFFFFFLL || col0 + ncols > 0xFFFFFFFFLL || batch > 0xFFFFFFFFull) return EOD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (omega_fill<double>(n, col0, ncols, seed, batch, out, n, s) != cudaSuccess) return EOD_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return EOD_ECUDA;
+    return EOD_OK;
+}
+
+void eod_abe_free(eod_factors *f) {
+    if (!f) return;
+    free_factors_device(f);
+    std::free(f);
+}
+
+const char *eod_status_string(eod_status s) {
+    switch (s) {
+    case EOD_OK: return "ok";
+    case EOD_EINVAL: return "invalid argument";
+    case EOD_ENOMEM: return "out of memory";
+    case EOD_ECUDA: return "CUDA error";
+    case EOD_ENONFINITE: return "matrix holds NaN or Inf";
+    case EOD_ETIMEOUT: return "device wait timed out";
+    case EOD_EPRECISION: return "Cholesky breakdown beyond the shifted fallback";
+    case EOD_EUNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+int64_t eod_abe_storage_entries(int64_t m, int64_t n, int64_t r) { return r * (m + n) + r * (r + 1) / 2; }
+
+double eod_abe_model_flops(int64_t m, int64_t n, int64_t r, int64_t k, int32_t with_err) {
+    const double M = (double)m, N = (double)n, Rr = (double)r, K = (double)k;
+    double f = 2.0 * (2.0 * M * N * Rr + M * Rr * Rr + 2.0 * N * Rr * Rr + 2.0 * Rr * Rr * Rr + 4.0 * M * Rr * K);
+    if (with_err) f += 2.0 * M * N * Rr;
+    return f;
+}
+
+void eod_abe_debug_fail_alloc_after(int32_t n) { g_fail_alloc_after = n > 0 ? n : 0; }
+
+const char *eod_abe_version(void) { return "eod-abe-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

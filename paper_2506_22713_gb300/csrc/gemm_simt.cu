@@ -1,0 +1,230 @@
+// SIMT GEMM for the plain (FP64 / FP32) path: every dense contraction of
+// Alg. 1 and Alg. 2 that is not on the tensor cores — the sketch A*Omega
+// (Alg. 1 step 4), the two block Gram-Schmidt projections Q^T Y and Y - Q S
+// (step 4, applied twice), the Gram matrices of CholQR (step 5), the
+// projection C^T = A^T Q (Alg. 2 step 8), the triangular solves and products
+// of the core (steps 9-11) and the reconstruction Q C with its fused
+// Frobenius error (Sec. 4.1).
+//
+// Tile 64 x 64 x 16, 256 threads, 4 x 4 outputs per thread with the row
+// index fastest across lanes so that column-major stores coalesce.  When the
+// tile grid is smaller than two waves of the 152 SMs the K range is split and
+// the partial tiles are summed by a second kernel in a fixed order.
+#include "common.cuh"
+
+namespace eod {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int F_UPPER_ONLY = 1, F_A_UPPER = 2, F_B_UPPER = 4;
+
+template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB, int EPI, bool SPLIT>
+__global__ void __launch_bounds__(NT)
+gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restrict__ A, int64_t lda,
+                 const TB *__restrict__ B, int64_t ldb, Acc beta, TC *C, int64_t ldc, int64_t kchunk,
+                 Acc *__restrict__ part, int flags, const TC *__restrict__ ref, int64_t ldref,
+                 double *__restrict__ errp)
+{
+    __shared__ Acc As[BK][BM + 1];
+    __shared__ Acc Bs[BK][BN + 1];
+    __shared__ double red[32];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+
+    if ((flags & F_UPPER_ONLY) && m0 > n0 + BN - 1) {
+        if (EPI == EPI_ERR && tid == 0) errp[blockIdx.x + (int64_t)blockIdx.y * gridDim.x] = 0.0;
+        return;
+    }
+    int64_t kb = (int64_t)blockIdx.z * kchunk;
+    int64_t ke = kb + kchunk < K ? kb + kchunk : K;
+    if (flags & F_A_UPPER) kb = kb > m0 ? kb : m0;                // op(A)(i,l) = 0 for l < i
+    if (flags & F_B_UPPER) ke = ke < n0 + BN ? ke : n0 + BN;      // op(B)(l,j) = 0 for l > j
+
+    Acc acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
+
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+        for (int q = 0; q < (BM * BK) / NT; ++q) {
+            const int e = tid + q * NT;
+            int i, kk;
+            if (!TRA) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
+            const int64_t gi = m0 + i, gk = k0 + kk;
+            Acc v = Acc(0);
+            if (gi < M && gk < ke) v = (Acc)(TRA ? A[gk + gi * lda] : A[gi + gk * lda]);
+            As[kk][i] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < (BN * BK) / NT; ++q) {
+            const int e = tid + q * NT;
+            int j, kk;
+            if (!TRB) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+            const int64_t gj = n0 + j, gk = k0 + kk;
+            Acc v = Acc(0);
+            if (gj < N && gk < ke) v = (Acc)(TRB ? B[gj + gk * ldb] : B[gk + gj * ldb]);
+            Bs[kk][j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            Acc a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+
+    if (SPLIT) {
+        Acc *dst = part + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t col = n0 + ty + 16 * j;
+            if (col >= N) continue;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t row = m0 + tx + 16 * i;
+                if (row < M) dst[row + col * M] = acc[i][j];
+            }
+        }
+        return;
+    }
+    double local = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t col = n0 + ty + 16 * j;
+        if (col >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t row = m0 + tx + 16 * i;
+            if (row >= M) continue;
+            Acc v = alpha * acc[i][j];
+            if (EPI == EPI_STORE) {
+                if (beta != Acc(0)) v = fma(beta, (Acc)C[row + col * ldc], v);
+                C[row + col * ldc] = (TC)v;
+            } else {
+                const TC vh = (TC)v;
+                if (C != nullptr) C[row + col * ldc] = vh;
+                const double d = (double)ref[row + col * ldref] - (double)vh;
+                local = fma(d, d, local);
+            }
+        }
+    }
+    if (EPI == EPI_ERR) {
+        const double tot = block_sum(local, red);
+        if (tid == 0) errp[blockIdx.x + (int64_t)blockIdx.y * gridDim.x] = tot;
+    }
+}
+
+template <typename TC, typename Acc>
+__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int S, const Acc *__restrict__ part,
+                                     Acc alpha, Acc beta, TC *C, int64_t ldc, int upper_only)
+{
+    const int64_t total = M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e % M, col = e / M;
+        if (upper_only && (row / BM) * BM > (col / BN) * BN + BN - 1) continue;
+        Acc s = Acc(0);
+        for (int z = 0; z < S; ++z) s += part[(int64_t)z * total + e];
+        Acc v = alpha * s;
+        if (beta != Acc(0)) v = fma(beta, (Acc)C[row + col * ldc], v);
+        C[row + col * ldc] = (TC)v;
+    }
+}
+
+template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB>
+cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, int64_t lda,
+                   const TB *B, int64_t ldb, double beta, TC *C, int64_t ldc, const GemmExtra &x,
+                   Scratch *ws, cudaStream_t s)
+{
+    const int64_t gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
+    const int flags = (x.upper_only ? F_UPPER_ONLY : 0) | (x.a_upper ? F_A_UPPER : 0) |
+                      (x.b_upper ? F_B_UPPER : 0);
+    if (gn > 65535) return cudaErrorInvalidValue;
+    if (x.epilogue == EPI_ERR) {
+        dim3 grid((unsigned)gm, (unsigned)gn, 1);
+        gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_ERR, false><<<grid, NT, 0, s>>>(
+            M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, K > 0 ? K : 1, nullptr, flags,
+            (const TC *)x.ref, x.ldref, x.err_partials);
+        return cudaGetLastError();
+    }
+    int64_t tiles = gm * gn;
+    if (x.upper_only) tiles = (tiles + gm) / 2 + 1;
+    const int64_t target = 2 * kNumSMs;
+    int64_t S = 1;
+    if (tiles < target && K > 4 * BK) {
+        S = (target + tiles - 1) / tiles;
+        int64_t kmax = (K + 4 * BK - 1) / (4 * BK);
+        if (S > kmax) S = kmax;
+        if (S > x.max_split) S = x.max_split;
+    }
+    Acc *part = nullptr;
+    size_t mark = ws ? ws->mark() : 0;
+    while (S > 1) {
+        part = ws ? (Acc *)ws->take(sizeof(Acc) * (size_t)S * (size_t)M * (size_t)N) : nullptr;
+        if (part) break;
+        S /= 2;
+    }
+    int64_t kchunk = K > 0 ? K : 1;
+    if (S > 1) {
+        kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
+        S = (K + kchunk - 1) / kchunk;
+    }
+    dim3 grid((unsigned)gm, (unsigned)gn, (unsigned)S);
+    if (S > 1) {
+        gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, true><<<grid, NT, 0, s>>>(
+            M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, part, flags, nullptr, 0,
+            nullptr);
+        EOD_CUDA_TRY(cudaGetLastError());
+        int64_t total = M * N;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 4 * kNumSMs * 8) blocks = 4 * kNumSMs * 8;
+        splitk_reduce_kernel<TC, Acc><<<blocks, 256, 0, s>>>(M, N, (int)S, part, (Acc)alpha, (Acc)beta,
+                                                             C, ldc, x.upper_only ? 1 : 0);
+        EOD_CUDA_TRY(cudaGetLastError());
+        ws->release(mark);
+        return cudaSuccess;
+    }
+    gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, false><<<grid, NT, 0, s>>>(
+        M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, nullptr, flags, nullptr, 0,
+        nullptr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t gemm_err_ctas(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + BN - 1) / BN); }
+
+template <typename TA, typename TB, typename TC, typename Acc>
+cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const TA *A,
+                 int64_t lda, const TB *B, int64_t ldb, double beta, TC *C, int64_t ldc,
+                 const GemmExtra &x, Scratch *ws, cudaStream_t s)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (!ta && !tb) return launch<TA, TB, TC, Acc, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
+    if (ta && !tb) return launch<TA, TB, TC, Acc, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
+    if (!ta && tb) return launch<TA, TB, TC, Acc, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
+    return launch<TA, TB, TC, Acc, true, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
+}
+
+template cudaError_t gemm<double, double, double, double>(bool, bool, int64_t, int64_t, int64_t, double,
+    const double *, int64_t, const double *, int64_t, double, double *, int64_t, const GemmExtra &,
+    Scratch *, cudaStream_t);
+template cudaError_t gemm<float, float, float, float>(bool, bool, int64_t, int64_t, int64_t, double,
+    const float *, int64_t, const float *, int64_t, double, float *, int64_t, const GemmExtra &,
+    Scratch *, cudaStream_t);
+template cudaError_t gemm<float, float, double, double>(bool, bool, int64_t, int64_t, int64_t, double,
+    const float *, int64_t, const float *, int64_t, double, double *, int64_t, const GemmExtra &,
+    Scratch *, cudaStream_t);
+
+}  // namespace eod

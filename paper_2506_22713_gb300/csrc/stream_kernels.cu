@@ -1,0 +1,212 @@
+// Streaming kernels of the EOD-ABE path: the Gaussian test blocks Omega_j
+// (Alg. 1 step 3), the Frobenius norm of A with its finiteness check (the
+// denominator of RelErr, Sec. 4.1, and eps in relative-tolerance mode), and
+// small copy / scale / fill helpers used between the dense steps.
+#include "common.cuh"
+
+namespace eod {
+namespace {
+
+// ---------------------------------------------------------------- Omega ----
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products, the key advanced by the golden-ratio Weyl
+// constants between rounds.
+__device__ __forceinline__ void philox_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        const uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+// Round a double to the nearest BF16 value (8 significant bits), ties to
+// even, by integer rounding at bit 45 of the binary64 encoding (the carry
+// propagates into the exponent when the mantissa overflows).
+__device__ __forceinline__ double round_bf16_from_f64(double g) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(g);
+    const unsigned long long lsb = (b >> 45) & 1ull;
+    b += 0x00000FFFFFFFFFFFull + lsb;
+    b &= ~0x00001FFFFFFFFFFFull;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ double omega_value(uint64_t seed, uint32_t row, uint32_t col, uint32_t batch) {
+    uint32_t c[4] = {row, col, batch, 0u};
+    philox_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const double u1 = ((double)c[0] + 0.5) * 0x1p-32;
+    const double u2 = ((double)c[1] + 0.5) * 0x1p-32;
+    const double radius = sqrt(-2.0 * log(u1));
+    const double angle = (2.0 * 3.141592653589793) * u2;
+    return round_bf16_from_f64(radius * cos(angle));
+}
+
+template <typename T>
+__global__ void omega_kernel(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, uint32_t batch,
+                             T *out, int64_t ldo) {
+    const int64_t total = n * ncols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % n, c = e / n;
+        out[i + c * ldo] = (T)omega_value(seed, (uint32_t)i, (uint32_t)(col0 + c), batch);
+    }
+}
+
+// ------------------------------------------------------------- norms ----
+template <typename T>
+__global__ void sumsq_kernel(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda,
+                             double *partials, int *flags) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    int bad = 0;
+    const int64_t total = m * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % m, j = e / m;
+        const double v = (double)A[i + j * lda];
+        if (!isfinite(v)) bad = 1;
+        acc = fma(v, v, acc);
+    }
+    const double tot = block_sum(acc, red);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = tot;
+        flags[blockIdx.x] = bad;
+    }
+}
+
+__global__ void finalize_norm_kernel(const double *partials, const int *pflags, int64_t count,
+                                     double *out, int *flag) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    int bad = 0;
+    for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
+        acc += partials[e];
+        if (pflags) bad |= pflags[e];
+    }
+    const double tot = block_sum(acc, red);
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        out[0] = sqrt(tot);
+        if (flag) flag[0] |= bad;
+    }
+}
+
+__global__ void finalize_sqrt_sum_kernel(const double *partials, int64_t count, const double *denom,
+                                         double *out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < count; e += blockDim.x) acc += partials[e];
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) {
+        const double d = denom ? denom[0] : 1.0;
+        out[0] = d > 0.0 ? sqrt(tot) / d : (tot > 0.0 ? INFINITY : 0.0);
+    }
+}
+
+// ------------------------------------------------------------- helpers ----
+template <typename TS, typename TD>
+__global__ void copy_kernel(const TS *__restrict__ src, int64_t lds, TD *__restrict__ dst, int64_t ldd,
+                            int64_t rows, int64_t cols, int transpose) {
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % rows, j = e / rows;
+        // dst(i, j) = src(i, j) or src(j, i)
+        dst[i + j * ldd] = (TD)(transpose ? src[j + i * lds] : src[i + j * lds]);
+    }
+}
+
+template <typename T>
+__global__ void scale_kernel(T *x, int64_t m, const double *norm) {
+    const double inv = 1.0 / norm[0];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        x[e] = (T)((double)x[e] * inv);
+}
+
+template <typename T>
+__global__ void zero_kernel(T *x, int64_t rows, int64_t cols, int64_t ld) {
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x)
+        x[(e % rows) + (e / rows) * ld] = T(0);
+}
+
+inline int grid_for(int64_t total, int per = 256) {
+    int64_t b = (total + per - 1) / per;
+    const int64_t cap = 8LL * kNumSMs * 4;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t omega_fill(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, uint64_t batch, T *out,
+                       int64_t ldo, cudaStream_t s) {
+    if (n <= 0 || ncols <= 0) return cudaSuccess;
+    omega_kernel<T><<<grid_for(n * ncols), 256, 0, s>>>(n, col0, ncols, seed, (uint32_t)batch, out, ldo);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fro_norm(const T *A, int64_t m, int64_t n, int64_t lda, double *out, int *flag, Scratch *ws,
+                     cudaStream_t s) {
+    const int blocks = grid_for(m * n, 512);
+    size_t mark = ws->mark();
+    double *part = (double *)ws->take(sizeof(double) * blocks);
+    int *pf = (int *)ws->take(sizeof(int) * blocks);
+    if (!part || !pf) return cudaErrorMemoryAllocation;
+    sumsq_kernel<T><<<blocks, 512, 0, s>>>(A, m, n, lda, part, pf);
+    EOD_CUDA_TRY(cudaGetLastError());
+    finalize_norm_kernel<<<1, 1024, 0, s>>>(part, pf, blocks, out, flag);
+    EOD_CUDA_TRY(cudaGetLastError());
+    ws->release(mark);
+    return cudaSuccess;
+}
+
+cudaError_t finalize_sqrt_sum(const double *partials, int64_t count, const double *denom, double *out,
+                              cudaStream_t s) {
+    finalize_sqrt_sum_kernel<<<1, 1024, 0, s>>>(partials, count, denom, out);
+    return cudaGetLastError();
+}
+
+template <typename TS, typename TD>
+cudaError_t copy_matrix(const TS *src, int64_t lds, TD *dst, int64_t ldd, int64_t rows, int64_t cols,
+                        bool transpose, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    copy_kernel<TS, TD><<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols, transpose ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t scale_column(T *x, int64_t m, const double *norm, cudaStream_t s) {
+    scale_kernel<T><<<grid_for(m), 256, 0, s>>>(x, m, norm);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fill_zero(T *x, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    zero_kernel<T><<<grid_for(rows * cols), 256, 0, s>>>(x, rows, cols, ld);
+    return cudaGetLastError();
+}
+
+template cudaError_t omega_fill<double>(int64_t, int64_t, int64_t, uint64_t, uint64_t, double *, int64_t, cudaStream_t);
+template cudaError_t omega_fill<float>(int64_t, int64_t, int64_t, uint64_t, uint64_t, float *, int64_t, cudaStream_t);
+template cudaError_t fro_norm<double>(const double *, int64_t, int64_t, int64_t, double *, int *, Scratch *, cudaStream_t);
+template cudaError_t fro_norm<float>(const float *, int64_t, int64_t, int64_t, double *, int *, Scratch *, cudaStream_t);
+template cudaError_t copy_matrix<double, double>(const double *, int64_t, double *, int64_t, int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t copy_matrix<float, float>(const float *, int64_t, float *, int64_t, int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t copy_matrix<double, float>(const double *, int64_t, float *, int64_t, int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t copy_matrix<float, double>(const float *, int64_t, double *, int64_t, int64_t, int64_t, bool, cudaStream_t);
+template cudaError_t scale_column<double>(double *, int64_t, const double *, cudaStream_t);
+template cudaError_t scale_column<float>(float *, int64_t, const double *, cudaStream_t);
+template cudaError_t fill_zero<double>(double *, int64_t, int64_t, int64_t, cudaStream_t);
+template cudaError_t fill_zero<float>(float *, int64_t, int64_t, int64_t, cudaStream_t);
+
+}  // namespace eod

@@ -1,0 +1,98 @@
+"""The C-ABI library: loads, exports what include/*.h declares, and rejects
+bad arguments on the host before any device work (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def eod():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2506_22713_gb300 as eod
+    return eod
+
+
+def _declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names += re.findall(r"EOD_API\s+[\w\s\*]+?\b(eod_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(eod):
+    names = _declared_symbols()
+    assert len(names) >= 12
+    lib = ctypes.CDLL(eod.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(eod.EXPORTED) | set(names)
+
+
+def test_status_strings_and_version(eod):
+    assert eod.status_string(0) == "ok"
+    assert "invalid" in eod.status_string(1)
+    assert eod.eod_abe_version().decode().startswith("eod-abe-gb300")
+
+
+def test_storage_entries_matches_worked_example(eod):
+    # Sec. 1: ranks 50/52/53 of a 220 x 220 RGB image -> 72284 entries
+    assert sum(eod.storage_entries(220, 220, r) for r in (50, 52, 53)) == 72284
+
+
+def test_model_flops_cost_table(eod):
+    # Sec. 3.4: 2mnr + mr^2 + 2nr^2 + 2r^3 + 4mrk multiply-adds (+ mnr for Q C)
+    m, n, r, k = 512, 384, 20, 32
+    ma = 2 * m * n * r + m * r * r + 2 * n * r * r + 2 * r ** 3 + 4 * m * r * k
+    assert eod.model_flops(m, n, r, k, with_err=False) == 2 * ma
+    assert eod.model_flops(m, n, r, k, with_err=True) == 2 * ma + 2 * m * n * r
+
+
+@pytest.mark.parametrize("m,n,lda,tol", [(0, 5, 1, 1e-3), (5, 0, 5, 1e-3), (5, 5, 4, 1e-3), (5, 5, 5, 0.0),
+                                         (5, 5, 5, -1.0), (5, 5, 5, float("nan")), (5, 5, 5, float("inf"))])
+def test_factor_rejects_bad_arguments(eod, m, n, lda, tol):
+    out = ctypes.POINTER(eod.EodFactors)()
+    dummy = ctypes.c_void_p(0x1000)  # never dereferenced: validation fails first
+    st = eod.eod_abe_factor(dummy, m, n, lda, tol, 1, ctypes.byref(out))
+    assert st == eod.EOD_EINVAL
+    assert not out
+
+
+def test_factor_rejects_null_and_bad_options(eod):
+    out = ctypes.POINTER(eod.EodFactors)()
+    assert eod.eod_abe_factor(None, 4, 4, 4, 1e-3, 1, ctypes.byref(out)) == eod.EOD_EINVAL
+    dummy = ctypes.c_void_p(0x1000)
+    for field, val in [("power_iters", 1), ("a_dtype", 7), ("precision", 9), ("tol_mode", 3), ("block_k", 129),
+                       ("block_k", -1)]:
+        o = eod.EodOpts()
+        eod.eod_opts_default(ctypes.byref(o))
+        setattr(o, field, val)
+        st = eod.eod_abe_factor_ex(dummy, 4, 4, 4, 1e-3, 1, ctypes.byref(o), ctypes.byref(out))
+        assert st == eod.EOD_EINVAL, field
+    assert eod.eod_abe_factor_ex(dummy, 4, 4, 4, 1e-3, 1, None, None) == eod.EOD_EINVAL
+
+
+def test_omega_and_batched_reject_bad_arguments(eod):
+    assert eod.eod_abe_omega(0, 0, 1, 1, 0, ctypes.c_void_p(0x1000), None) == eod.EOD_EINVAL
+    assert eod.eod_abe_omega(4, -1, 1, 1, 0, ctypes.c_void_p(0x1000), None) == eod.EOD_EINVAL
+    assert eod.eod_abe_omega(4, 0, 1, 1, 0, None, None) == eod.EOD_EINVAL
+    assert eod.eod_abe_omega(1 << 33, 0, 1, 1, 0, ctypes.c_void_p(0x1000), None) == eod.EOD_EINVAL
+    assert eod.eod_abe_factor_batched(None, None, None, None, 0, 1e-3, 1, None, None, None) == eod.EOD_EINVAL
+
+
+def test_opts_default_layout(eod):
+    o = eod.EodOpts()
+    eod.eod_opts_default(ctypes.byref(o))
+    assert (o.a_dtype, o.precision, o.tol_mode, o.block_k, o.power_iters, o.compute_err) == (0, 0, 0, 0, 0, 1)
+    assert ctypes.sizeof(eod.EodOpts) == 40
+    assert ctypes.sizeof(eod.EodFactors) == 8 * 3 + 4 * 2 + 8 * 5 + 8 + 8 + 8 * 4 + 8 * 3
+
+
+def test_free_null_is_noop(eod):
+    eod.eod_abe_free(None)
