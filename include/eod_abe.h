@@ -190,6 +190,22 @@ EOD_API double eod_abe_model_flops(int64_t m, int64_t n, int64_t r, int64_t k, i
  * device were out of memory; n <= 0 clears the hook.  Host-side only. */
 EOD_API void eod_abe_debug_fail_alloc_after(int32_t n);
 
+/* Measurement hooks (no counterpart in the paper; they support the
+ * benchmark's roofline figures).
+ * eod_abe_debug_profile(1) clears and starts CUDA-event timing of every
+ * kernel launch, grouped by kind: 0 SIMT GEMM, 1 one-CTA Cholesky / rank
+ * test, 2 Omega generation, 3 streaming (norms, copies, splitting),
+ * 4 tcgen05 tensor-core GEMM; eod_abe_debug_profile(0) stops it and clears.
+ * eod_abe_debug_profile_read() waits for the recorded events of one kind and
+ * returns the launch count, the summed device time (ms) and the summed
+ * algorithmic flops and bytes of those launches; EOD_EINVAL for an unknown
+ * kind or NULL outputs.  eod_abe_debug_launch_count() is the number of
+ * kernels the library has launched since it was loaded. */
+EOD_API void eod_abe_debug_profile(int32_t enable);
+EOD_API eod_status eod_abe_debug_profile_read(int32_t kind, int64_t *launches, double *total_ms,
+                                              double *total_flops, double *total_bytes);
+EOD_API int64_t eod_abe_debug_launch_count(void);
+
 /* Build identification (static string). */
 EOD_API const char *eod_abe_version(void);
 

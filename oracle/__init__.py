@@ -55,7 +55,7 @@ def configure(lib):
     lib.orc_fro_norm.restype = ctypes.c_double
     lib.orc_basis_ext.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
-                                  _f64p, _i64p, _f64p, _i64p]
+                                  _f64p, _i64p, _f64p, _i64p, ctypes.c_int64]
     lib.orc_basis_ext.restype = ctypes.c_int
     lib.orc_eod_abe.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
@@ -145,8 +145,9 @@ def fro_norm(A) -> float:
     return lib.orc_fro_norm(A.shape[0], A.shape[1], _ptr(A), A.shape[0])
 
 
-def basis_ext(A, eps: float, k: int = 32, seed: int = 0, batch: int = 0):
-    """Alg. 1: returns (Q (m x r), tdiag) for the absolute threshold eps."""
+def basis_ext(A, eps: float, k: int = 32, seed: int = 0, batch: int = 0, max_blocks: int = 0):
+    """Alg. 1: returns (Q (m x r), tdiag) for the absolute threshold eps.
+    max_blocks > 0 stops after that many blocks (a bounded timing sample)."""
     lib = _load()
     A = _colmajor(A)
     m, n = A.shape
@@ -156,7 +157,7 @@ def basis_ext(A, eps: float, k: int = 32, seed: int = 0, batch: int = 0):
     r = ctypes.c_int64(0)
     nt = ctypes.c_int64(0)
     st = lib.orc_basis_ext(_ptr(A), m, n, m, eps, k, seed, batch, _ptr(Q), ctypes.byref(r),
-                           _ptr(td), ctypes.byref(nt))
+                           _ptr(td), ctypes.byref(nt), int(max_blocks))
     if st:
         raise MemoryError("oracle allocation failed")
     return Q[:, : r.value].copy(order="F"), td[: nt.value].copy()

@@ -232,14 +232,16 @@ double orc_fro_norm(int64_t m, int64_t n, const double *A, int64_t lda)
 /*                                                                           */
 /* Q: m x cap (ld m) receives the basis; tdiag (cap entries) receives every  */
 /* computed diagonal entry of the T_j in order; *ntd their count; *r_out the */
-/* detected rank.  Returns 0, or 2 on allocation failure.                    */
+/* detected rank.  max_blocks > 0 stops after that many blocks (a bounded    */
+/* sample of the work for timing; 0 = run to the end).  Returns 0, or 2 on   */
+/* allocation failure.                                                       */
 /* ------------------------------------------------------------------------ */
 int orc_basis_ext(const double *A, int64_t m, int64_t n, int64_t lda, double eps,
                   int64_t k, uint64_t seed, uint64_t batch,
-                  double *Q, int64_t *r_out, double *tdiag, int64_t *ntd)
+                  double *Q, int64_t *r_out, double *tdiag, int64_t *ntd, int64_t max_blocks)
 {
     const int64_t cap = (m < n) ? m : n;
-    int64_t kept = 0, nt = 0;
+    int64_t kept = 0, nt = 0, blocks = 0;
     double *Om = (double *)malloc(sizeof(double) * (size_t)n * (size_t)k);
     double *Y = (double *)malloc(sizeof(double) * (size_t)m * (size_t)k);
     double *S = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)k);
@@ -250,8 +252,9 @@ int orc_basis_ext(const double *A, int64_t m, int64_t n, int64_t lda, double eps
         return 2;
     }
     int stop = 0;
-    while (!stop && kept < cap) {
+    while (!stop && kept < cap && (max_blocks <= 0 || blocks < max_blocks)) {
         int64_t f = (k < cap - kept) ? k : (cap - kept);
+        ++blocks;
         /* step 3: Omega_j, n x f */
         orc_omega(n, kept, f, seed, batch, Om);
         /* step 4: Y_j = A Omega_j, then Y_j <- (I - Q Q^T) Y_j, twice */
@@ -313,7 +316,7 @@ int orc_eod_abe(const double *A, int64_t m, int64_t n, int64_t lda, double tol,
     double norm_a = orc_fro_norm(m, n, A, lda);
     double eps = (tol_mode == 1) ? tol * norm_a : tol;
     int64_t r = 0;
-    int st = orc_basis_ext(A, m, n, lda, eps, k, seed, batch, Q, &r, tdiag, ntd);
+    int st = orc_basis_ext(A, m, n, lda, eps, k, seed, batch, Q, &r, tdiag, ntd, 0);
     if (st) return st;
     *r_out = r;
     res[1] = norm_a;

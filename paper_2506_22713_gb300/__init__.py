@@ -29,7 +29,8 @@ EXPORTED = [
     "eod_opts_default", "eod_abe_factor", "eod_abe_factor_ex", "eod_abe_factor_host",
     "eod_abe_reconstruct", "eod_abe_factor_batched", "eod_abe_omega", "eod_abe_free",
     "eod_status_string", "eod_abe_storage_entries", "eod_abe_model_flops",
-    "eod_abe_debug_fail_alloc_after", "eod_abe_version",
+    "eod_abe_debug_fail_alloc_after", "eod_abe_version", "eod_abe_debug_profile",
+    "eod_abe_debug_profile_read", "eod_abe_debug_launch_count",
 ]
 
 
@@ -100,6 +101,13 @@ def _load() -> ctypes.CDLL:
     lib.eod_abe_model_flops.restype = F64
     lib.eod_abe_debug_fail_alloc_after.argtypes = [I32]
     lib.eod_abe_debug_fail_alloc_after.restype = None
+    lib.eod_abe_debug_profile.argtypes = [I32]
+    lib.eod_abe_debug_profile.restype = None
+    lib.eod_abe_debug_profile_read.argtypes = [I32, ctypes.POINTER(I64), ctypes.POINTER(F64), ctypes.POINTER(F64),
+                                               ctypes.POINTER(F64)]
+    lib.eod_abe_debug_profile_read.restype = I32
+    lib.eod_abe_debug_launch_count.argtypes = []
+    lib.eod_abe_debug_launch_count.restype = I64
     lib.eod_abe_version.argtypes = []
     lib.eod_abe_version.restype = ctypes.c_char_p
     return lib
@@ -121,6 +129,22 @@ eod_abe_storage_entries = _lib.eod_abe_storage_entries
 eod_abe_model_flops = _lib.eod_abe_model_flops
 eod_abe_debug_fail_alloc_after = _lib.eod_abe_debug_fail_alloc_after
 eod_abe_version = _lib.eod_abe_version
+eod_abe_debug_profile = _lib.eod_abe_debug_profile
+eod_abe_debug_profile_read = _lib.eod_abe_debug_profile_read
+eod_abe_debug_launch_count = _lib.eod_abe_debug_launch_count
+
+PROF_GEMM_SIMT, PROF_CHOL, PROF_OMEGA, PROF_STREAM, PROF_TC_GEMM = range(5)
+
+
+def profile_read(kind: int) -> dict:
+    """Launch count, device ms, algorithmic flops and bytes of one kernel kind
+    since eod_abe_debug_profile(1)."""
+    n = ctypes.c_int64(0)
+    ms, fl, by = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    st = _lib.eod_abe_debug_profile_read(kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(by))
+    if st != EOD_OK:
+        raise EodError(st, "eod_abe_debug_profile_read")
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
 
 
 def status_string(status: int) -> str:

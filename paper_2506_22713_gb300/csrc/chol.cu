@@ -18,6 +18,7 @@
 // The rho guard (1e-10) also keeps every accepted panel well enough
 // conditioned for CholQR2 to reach orthogonality at the unit roundoff.
 #include "common.cuh"
+#include "instrument.cuh"
 
 namespace eod {
 namespace {
@@ -121,17 +122,21 @@ cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double e
                                           (int)(sizeof(double) * (128 * 128 + 256))));
         attr_set = true;
     }
+    ProfScope prof(PROF_CHOL, (double)w * w * w / 3.0, sizeof(double) * 2.0 * w * w, s);
+    count_launch();
     chol_small_kernel<<<1, 256, smem, s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R, Rinv, ldr, info);
     return cudaGetLastError();
 }
 
 cudaError_t tdiag_product(const double *R1, const double *R2, int64_t ldr, const int *p_dev, double *tdiag,
                           cudaStream_t s) {
+    count_launch();
     tdiag_kernel<<<1, 128, 0, s>>>(R1, R2, ldr, p_dev, tdiag);
     return cudaGetLastError();
 }
 
 cudaError_t trace_sum(const double *G, int64_t ldg, int64_t p, double *out, cudaStream_t s) {
+    count_launch();
     trace_kernel<<<1, 1024, 0, s>>>(G, ldg, p, out);
     return cudaGetLastError();
 }

@@ -11,6 +11,7 @@
 // tile grid is smaller than two waves of the 152 SMs the K range is split and
 // the partial tiles are summed by a second kernel in a fixed order.
 #include "common.cuh"
+#include "instrument.cuh"
 
 namespace eod {
 namespace {
@@ -151,7 +152,16 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
     const int flags = (x.upper_only ? F_UPPER_ONLY : 0) | (x.a_upper ? F_A_UPPER : 0) |
                       (x.b_upper ? F_B_UPPER : 0);
     if (gn > 65535) return cudaErrorInvalidValue;
+    double frac = 1.0;
+    if (x.upper_only) frac *= 0.5;
+    if (x.a_upper && x.b_upper) frac /= 6.0;
+    else if (x.a_upper || x.b_upper) frac *= 0.5;
+    const double flops = 2.0 * (double)M * (double)N * (double)K * frac;
+    double bytes = (double)sizeof(TA) * M * K + (double)sizeof(TB) * K * N + (double)sizeof(TC) * M * N;
+    if (beta != 0.0 || x.epilogue == EPI_ERR) bytes += (double)sizeof(TC) * M * N;
+    ProfScope prof(PROF_GEMM_SIMT, flops, bytes, s);
     if (x.epilogue == EPI_ERR) {
+        count_launch();
         dim3 grid((unsigned)gm, (unsigned)gn, 1);
         gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_ERR, false><<<grid, NT, 0, s>>>(
             M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, K > 0 ? K : 1, nullptr, flags,
@@ -182,6 +192,7 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
     }
     dim3 grid((unsigned)gm, (unsigned)gn, (unsigned)S);
     if (S > 1) {
+        count_launch(2);
         gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, true><<<grid, NT, 0, s>>>(
             M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, part, flags, nullptr, 0,
             nullptr);
@@ -195,6 +206,7 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
         ws->release(mark);
         return cudaSuccess;
     }
+    count_launch();
     gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, false><<<grid, NT, 0, s>>>(
         M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, nullptr, flags, nullptr, 0,
         nullptr);

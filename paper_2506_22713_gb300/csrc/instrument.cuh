@@ -1,0 +1,31 @@
+// Launch counting and per-kind CUDA-event timing (see instrument.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace eod {
+
+// kernel kinds, as reported by eod_abe_debug_profile_read()
+enum ProfKind {
+    PROF_GEMM_SIMT = 0,   // SIMT GEMM (plain path contractions), incl. its split-K reduction
+    PROF_CHOL = 1,        // one-CTA Cholesky / rank test
+    PROF_OMEGA = 2,       // Gaussian test blocks
+    PROF_STREAM = 3,      // norms, copies, scaling, splitting
+    PROF_TC_GEMM = 4,     // tcgen05 tensor-core contractions (mixed path)
+    PROF_KINDS = 5
+};
+
+void count_launch(int n = 1);
+
+class ProfScope {
+  public:
+    ProfScope(int kind, double flops, double bytes, cudaStream_t s);
+    ~ProfScope();
+    ProfScope(const ProfScope &) = delete;
+    ProfScope &operator=(const ProfScope &) = delete;
+
+  private:
+    cudaStream_t s_;
+    int rec_;
+};
+
+}  // namespace eod

@@ -3,6 +3,7 @@
 // denominator of RelErr, Sec. 4.1, and eps in relative-tolerance mode), and
 // small copy / scale / fill helpers used between the dense steps.
 #include "common.cuh"
+#include "instrument.cuh"
 
 namespace eod {
 namespace {
@@ -149,6 +150,8 @@ template <typename T>
 cudaError_t omega_fill(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, uint64_t batch, T *out,
                        int64_t ldo, cudaStream_t s) {
     if (n <= 0 || ncols <= 0) return cudaSuccess;
+    ProfScope prof(PROF_OMEGA, 0.0, (double)sizeof(T) * n * ncols, s);
+    count_launch();
     omega_kernel<T><<<grid_for(n * ncols), 256, 0, s>>>(n, col0, ncols, seed, (uint32_t)batch, out, ldo);
     return cudaGetLastError();
 }
@@ -161,6 +164,8 @@ cudaError_t fro_norm(const T *A, int64_t m, int64_t n, int64_t lda, double *out,
     double *part = (double *)ws->take(sizeof(double) * blocks);
     int *pf = (int *)ws->take(sizeof(int) * blocks);
     if (!part || !pf) return cudaErrorMemoryAllocation;
+    ProfScope prof(PROF_STREAM, 2.0 * m * n, (double)sizeof(T) * m * n, s);
+    count_launch(2);
     sumsq_kernel<T><<<blocks, 512, 0, s>>>(A, m, n, lda, part, pf);
     EOD_CUDA_TRY(cudaGetLastError());
     finalize_norm_kernel<<<1, 1024, 0, s>>>(part, pf, blocks, out, flag);
@@ -171,6 +176,7 @@ cudaError_t fro_norm(const T *A, int64_t m, int64_t n, int64_t lda, double *out,
 
 cudaError_t finalize_sqrt_sum(const double *partials, int64_t count, const double *denom, double *out,
                               cudaStream_t s) {
+    count_launch();
     finalize_sqrt_sum_kernel<<<1, 1024, 0, s>>>(partials, count, denom, out);
     return cudaGetLastError();
 }
@@ -179,12 +185,15 @@ template <typename TS, typename TD>
 cudaError_t copy_matrix(const TS *src, int64_t lds, TD *dst, int64_t ldd, int64_t rows, int64_t cols,
                         bool transpose, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
+    ProfScope prof(PROF_STREAM, 0.0, (double)(sizeof(TS) + sizeof(TD)) * rows * cols, s);
+    count_launch();
     copy_kernel<TS, TD><<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols, transpose ? 1 : 0);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t scale_column(T *x, int64_t m, const double *norm, cudaStream_t s) {
+    count_launch();
     scale_kernel<T><<<grid_for(m), 256, 0, s>>>(x, m, norm);
     return cudaGetLastError();
 }
@@ -192,6 +201,7 @@ cudaError_t scale_column(T *x, int64_t m, const double *norm, cudaStream_t s) {
 template <typename T>
 cudaError_t fill_zero(T *x, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
+    count_launch();
     zero_kernel<T><<<grid_for(rows * cols), 256, 0, s>>>(x, rows, cols, ld);
     return cudaGetLastError();
 }
