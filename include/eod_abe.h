@@ -206,6 +206,38 @@ EOD_API eod_status eod_abe_debug_profile_read(int32_t kind, int64_t *launches, d
                                               double *total_flops, double *total_bytes);
 EOD_API int64_t eod_abe_debug_launch_count(void);
 
+/* ||A||_F of a device matrix without allocating anything: no cudaMalloc,
+ * no cudaFree and no allocating library call, for callers that cannot
+ * allocate device memory (code running while another framework owns the
+ * device allocator, real-time pipelines that forbid allocation after
+ * start-up, or threads recording work for later replay).  The paper has no
+ * counterpart; it is the S0 reduction of eod_abe_factor run on a fixed
+ * scratch area.
+ *
+ * A: device matrix, m x n, column-major, ld lda >= m, type dtype (EOD_F64 or
+ * EOD_F32).  norm_out: device pointer to one double, receives ||A||_F
+ * (FP64 accumulation, the same reduction order as eod_abe_factor's norm_a).
+ * nonfinite_out: device pointer to one int32, receives 1 if A holds a NaN
+ * or an infinity, else 0 (it is cleared by the call).  stream: cudaStream_t.
+ * The call only enqueues work and returns; read the outputs after
+ * synchronising the stream.
+ *
+ * Scratch: the per-block partial sums live in a static device array of
+ * 58,368 bytes (4864 partial sums and flags) that every GPU loading this
+ * library keeps until the process exits.  The first call on each device
+ * looks the array's device address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the array, which keeps the last call's partials: calls that
+ * overlap on the GPU (different streams, or different host threads on the
+ * same device) race on it and must be serialised by the caller.
+ *
+ * Errors: EOD_EINVAL for NULL pointers, m < 1, n < 1, lda < m, an unknown
+ * dtype, m or n above 2^31 - 1, or m*n above 2^40 elements (the largest
+ * input this entry point accepts); EOD_ECUDA if a launch fails;
+ * EOD_EUNSUPPORTED for a device ordinal of 64 or more. */
+EOD_API eod_status eod_abe_fro_norm_noalloc(const void *A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                                            double *norm_out, int32_t *nonfinite_out, void *stream);
+
 /* Build identification (static string). */
 EOD_API const char *eod_abe_version(void);
 

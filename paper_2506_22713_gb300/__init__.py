@@ -30,7 +30,7 @@ EXPORTED = [
     "eod_abe_reconstruct", "eod_abe_factor_batched", "eod_abe_omega", "eod_abe_free",
     "eod_status_string", "eod_abe_storage_entries", "eod_abe_model_flops",
     "eod_abe_debug_fail_alloc_after", "eod_abe_version", "eod_abe_debug_profile",
-    "eod_abe_debug_profile_read", "eod_abe_debug_launch_count",
+    "eod_abe_debug_profile_read", "eod_abe_debug_launch_count", "eod_abe_fro_norm_noalloc",
 ]
 
 
@@ -108,6 +108,8 @@ def _load() -> ctypes.CDLL:
     lib.eod_abe_debug_profile_read.restype = I32
     lib.eod_abe_debug_launch_count.argtypes = []
     lib.eod_abe_debug_launch_count.restype = I64
+    lib.eod_abe_fro_norm_noalloc.argtypes = [P, I64, I64, I64, I32, P, P, P]
+    lib.eod_abe_fro_norm_noalloc.restype = I32
     lib.eod_abe_version.argtypes = []
     lib.eod_abe_version.restype = ctypes.c_char_p
     return lib
@@ -132,6 +134,7 @@ eod_abe_version = _lib.eod_abe_version
 eod_abe_debug_profile = _lib.eod_abe_debug_profile
 eod_abe_debug_profile_read = _lib.eod_abe_debug_profile_read
 eod_abe_debug_launch_count = _lib.eod_abe_debug_launch_count
+eod_abe_fro_norm_noalloc = _lib.eod_abe_fro_norm_noalloc
 
 PROF_GEMM_SIMT, PROF_CHOL, PROF_OMEGA, PROF_STREAM, PROF_TC_GEMM = range(5)
 

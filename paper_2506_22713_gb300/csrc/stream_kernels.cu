@@ -5,6 +5,8 @@
 #include "common.cuh"
 #include "instrument.cuh"
 
+#include <mutex>
+
 namespace eod {
 namespace {
 
@@ -136,9 +138,11 @@ __global__ void zero_kernel(T *x, int64_t rows, int64_t cols, int64_t ld) {
         x[(e % rows) + (e / rows) * ld] = T(0);
 }
 
+constexpr int64_t kGridCap = 8LL * kNumSMs * 4;   // most blocks any streaming launch uses
+
 inline int grid_for(int64_t total, int per = 256) {
     int64_t b = (total + per - 1) / per;
-    const int64_t cap = 8LL * kNumSMs * 4;
+    const int64_t cap = kGridCap;
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
@@ -220,3 +224,79 @@ template cudaError_t fill_zero<double>(double *, int64_t, int64_t, int64_t, cuda
 template cudaError_t fill_zero<float>(float *, int64_t, int64_t, int64_t, cudaStream_t);
 
 }  // namespace eod
+
+// ===========================================================================
+// Allocation-free Frobenius norm (eod_abe_fro_norm_noalloc).
+//
+// Some callers cannot allocate device memory at all: code that runs while
+// another framework owns the device allocator, real-time pipelines that
+// forbid allocation after start-up, or a host thread that is recording work
+// for later replay.  For them the per-block partial sums and non-finite flags
+// of the norm reduction live in this fixed device array instead of the
+// per-call workspace.  Every GPU that loads the library holds it until the
+// process exits.
+// ===========================================================================
+namespace eod {
+namespace {
+
+constexpr int64_t kNoAllocMaxBlocks = kGridCap;                 // 4864 partials
+constexpr int64_t kNoAllocMaxElements = (int64_t)1 << 40;       // largest m*n accepted
+constexpr size_t kNoAllocScratchBytes = (size_t)kNoAllocMaxBlocks * (sizeof(double) + sizeof(int));
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device ordinal, looked up once per
+// device (with that device current) on the first call made on it.
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};
+
+eod_status noalloc_scratch(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
+    if (dev < 0 || dev >= 64) return EOD_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) { cudaGetLastError(); return EOD_ECUDA; }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return EOD_OK;
+}
+
+template <typename T>
+eod_status fro_norm_noalloc(const T *A, int64_t m, int64_t n, int64_t lda, double *norm_out, int *flag_out,
+                            cudaStream_t s) {
+    const int blocks = grid_for(m * n, 512);
+    if (blocks > kNoAllocMaxBlocks) return EOD_EINVAL;
+    void *base = nullptr;
+    eod_status st = noalloc_scratch(&base);
+    if (st != EOD_OK) return st;
+    double *part = (double *)base;
+    int *pf = (int *)((char *)base + sizeof(double) * kNoAllocMaxBlocks);
+    // the flag is OR-ed by the finalize kernel: clear it first; the partials
+    // are all rewritten by this call before they are read
+    if (cudaMemsetAsync(flag_out, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
+    ProfScope prof(PROF_STREAM, 2.0 * m * n, (double)sizeof(T) * m * n, s);
+    count_launch(2);
+    sumsq_kernel<T><<<blocks, 512, 0, s>>>(A, m, n, lda, part, pf);
+    if (cudaGetLastError() != cudaSuccess) return EOD_ECUDA;
+    finalize_norm_kernel<<<1, 1024, 0, s>>>(part, pf, blocks, norm_out, flag_out);
+    if (cudaGetLastError() != cudaSuccess) return EOD_ECUDA;
+    return EOD_OK;
+}
+
+}  // namespace
+}  // namespace eod
+
+extern "C" eod_status eod_abe_fro_norm_noalloc(const void *A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
+                                               double *norm_out, int32_t *nonfinite_out, void *stream) {
+    using namespace eod;
+    if (!A || !norm_out || !nonfinite_out || m < 1 || n < 1 || lda < m) return EOD_EINVAL;
+    if (m > 0x7FFFFFFFLL || n > 0x7FFFFFFFLL || m * n > kNoAllocMaxElements) return EOD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == EOD_F64) return fro_norm_noalloc<double>((const double *)A, m, n, lda, norm_out, (int *)nonfinite_out, s);
+    if (dtype == EOD_F32) return fro_norm_noalloc<float>((const float *)A, m, n, lda, norm_out, (int *)nonfinite_out, s);
+    return EOD_EINVAL;
+}
