@@ -206,6 +206,22 @@ EOD_API eod_status eod_abe_debug_profile_read(int32_t kind, int64_t *launches, d
                                               double *total_flops, double *total_bytes);
 EOD_API int64_t eod_abe_debug_launch_count(void);
 
+/* Test hook (no counterpart in the paper): one tcgen05 tensor-core
+ * contraction of the mixed path on FP32 device inputs, split into BF16
+ * hi/lo parts inside the call.  All matrices column-major.
+ *   form 0 (sketch):          D (M x N) = X Y, X M x K (ld ldx), Y K x N
+ *                             (ld ldy) holding BF16-exact values; X is read
+ *                             M-contiguous as in A Omega.
+ *   form 1 (projection):      D (M x N) = X^T Y, X K x M, Y K x N.
+ *   form 2 (reconstruction):  *err_out (device double) = ||D - X Y^T||_F
+ *                             with X M x K, Y N x K and D the M x N
+ *                             reference (ld ldd); D is not written.
+ * Returns after synchronising `stream`; EOD_ETIMEOUT if a bounded device
+ * wait ran out, EOD_EINVAL for bad sizes or leading dimensions. */
+EOD_API eod_status eod_abe_debug_tc_gemm(int32_t form, int64_t M, int64_t N, int64_t K, const float *X,
+                                         int64_t ldx, const float *Y, int64_t ldy, float *D, int64_t ldd,
+                                         double *err_out, void *stream);
+
 /* ||A||_F of a device matrix without allocating anything: no cudaMalloc,
  * no cudaFree and no allocating library call, for callers that cannot
  * allocate device memory (code running while another framework owns the

@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/eod_abe.h"
 
 namespace eod {
@@ -69,6 +71,43 @@ struct Scratch {
     }
     size_t mark() const { return used; }
     void release(size_t m) { used = m; }
+};
+
+// --------------------------------------------------------------------------
+// Stream-ordered device allocations owned by one call; freed on the stream
+// when the call returns unless handed over with keep().
+// --------------------------------------------------------------------------
+extern int g_fail_alloc_after;   // test hook: n-th allocation from now fails
+
+struct Arena {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    explicit Arena(cudaStream_t st) : s(st) {}
+    template <typename T>
+    eod_status get(T **p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        if (g_fail_alloc_after > 0) {
+            if (--g_fail_alloc_after == 0) return EOD_ENOMEM;
+        }
+        void *q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, sizeof(T) * count, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? EOD_ENOMEM : EOD_ECUDA;
+        }
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return EOD_OK;
+    }
+    void keep(void *p) {
+        for (auto &q : ptrs)
+            if (q == p) q = nullptr;
+    }
+    ~Arena() {
+        for (void *q : ptrs)
+            if (q) cudaFreeAsync(q, s);
+    }
 };
 
 // --------------------------------------------------------------------------

@@ -26,39 +26,7 @@
 
 namespace eod {
 
-static int g_fail_alloc_after = 0;
-
-// Stream-ordered device allocations owned by one call.
-struct Arena {
-    cudaStream_t s;
-    std::vector<void *> ptrs;
-    explicit Arena(cudaStream_t st) : s(st) {}
-    template <typename T>
-    eod_status get(T **p, size_t count) {
-        *p = nullptr;
-        if (count == 0) count = 1;
-        if (g_fail_alloc_after > 0) {
-            if (--g_fail_alloc_after == 0) return EOD_ENOMEM;
-        }
-        void *q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, sizeof(T) * count, s);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return e == cudaErrorMemoryAllocation ? EOD_ENOMEM : EOD_ECUDA;
-        }
-        ptrs.push_back(q);
-        *p = (T *)q;
-        return EOD_OK;
-    }
-    void keep(void *p) {  // ownership moves to the caller's factors
-        for (auto &q : ptrs)
-            if (q == p) q = nullptr;
-    }
-    ~Arena() {
-        for (void *q : ptrs)
-            if (q) cudaFreeAsync(q, s);
-    }
-};
+int g_fail_alloc_after = 0;
 
 #define EOD_TRY(...)                                    \
     do {                                                 \
@@ -283,7 +251,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     F->block_k = k;
 
     MixedOps<T> mx;
-    if (mixed) EOD_TRY(mx.prepare(A, m, n, lda, ar, s));
+    if (mixed) EOD_TRY(mx.prepare(A, m, n, lda, k, ar, &ws, s));
 
     // ---- Alg. 1 ----
     const double eps2 = eps * eps;
@@ -464,6 +432,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     }
     EOD_CU(cudaStreamSynchronize(s));
     F->rel_err = o.compute_err ? hm.val[0] : -1.0;
+    if (mixed) EOD_TRY(mx.check(s));
 
     F->U = U; ar.keep(U);
     F->V = V; ar.keep(V);

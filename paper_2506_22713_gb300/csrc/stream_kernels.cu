@@ -46,6 +46,9 @@ __device__ __forceinline__ double omega_value(uint64_t seed, uint32_t row, uint3
     return round_bf16_from_f64(radius * cos(angle));
 }
 
+template <typename T> __device__ __forceinline__ T from_f64(double x) { return (T)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+
 template <typename T>
 __global__ void omega_kernel(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, uint32_t batch,
                              T *out, int64_t ldo) {
@@ -53,7 +56,7 @@ __global__ void omega_kernel(int64_t n, int64_t col0, int64_t ncols, uint64_t se
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e % n, c = e / n;
-        out[i + c * ldo] = (T)omega_value(seed, (uint32_t)i, (uint32_t)(col0 + c), batch);
+        out[i + c * ldo] = from_f64<T>(omega_value(seed, (uint32_t)i, (uint32_t)(col0 + c), batch));
     }
 }
 
@@ -212,6 +215,8 @@ cudaError_t fill_zero(T *x, int64_t rows, int64_t cols, int64_t ld, cudaStream_t
 
 template cudaError_t omega_fill<double>(int64_t, int64_t, int64_t, uint64_t, uint64_t, double *, int64_t, cudaStream_t);
 template cudaError_t omega_fill<float>(int64_t, int64_t, int64_t, uint64_t, uint64_t, float *, int64_t, cudaStream_t);
+template cudaError_t omega_fill<__nv_bfloat16>(int64_t, int64_t, int64_t, uint64_t, uint64_t, __nv_bfloat16 *, int64_t,
+                                               cudaStream_t);
 template cudaError_t fro_norm<double>(const double *, int64_t, int64_t, int64_t, double *, int *, Scratch *, cudaStream_t);
 template cudaError_t fro_norm<float>(const float *, int64_t, int64_t, int64_t, double *, int *, Scratch *, cudaStream_t);
 template cudaError_t copy_matrix<double, double>(const double *, int64_t, double *, int64_t, int64_t, int64_t, bool, cudaStream_t);

@@ -1,0 +1,527 @@
+// Tensor-core contractions of the mixed path on sm_103a: tcgen05.mma
+// (kind::f16, BF16 operands, FP32 accumulation in TMEM) fed by TMA.
+//
+//   sketch          Y   = (A_hi + A_lo) Omega         Alg. 1 step 4
+//   projection      C^T = A_hi^T Q_hi + A_hi^T Q_lo + A_lo^T Q_hi    Alg. 2 step 8
+//   reconstruction  sum (A - Q C)^2 over a tile       Sec. 4.1 RelErr, with
+//                   Q C = Q_hi C_hi + Q_hi C_lo + Q_lo C_hi
+//
+// A FP32 matrix X is split as X_hi = bf16(X), X_lo = bf16(X - X_hi) (round
+// to nearest even); the dropped X_lo Y_lo term and the split's own residual
+// are about 2^-16 relative.  Omega is BF16-exact, so the sketch needs two
+// products only.
+//
+// One CTA computes a 128 x BN tile of D.  Warp 0 issues TMA loads into a
+// ring of shared-memory stages (128-byte swizzle), warp 1 allocates TMEM and
+// one of its threads issues the MMAs (4 per 64-wide K block), warps 2-5 read
+// the accumulator back with tcgen05.ld (warp w owns TMEM lanes 32*(w%4) ..)
+// and run the epilogue.  A tile is "pairs" of (A operand, B operand) tensor
+// maps accumulated into the same TMEM columns, interleaved per K block so a
+// re-read A tile hits L2.  Every mbarrier wait is bounded; a wait that runs
+// out sets an error flag the host turns into EOD_ETIMEOUT, and the CTA still
+// releases its TMEM and exits.
+#include "common.cuh"
+#include "instrument.cuh"
+#include "tc_gemm.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+namespace eod {
+namespace tc {
+
+constexpr int BM = 128;           // MMA M (one CTA, cta_group::1)
+constexpr int BK = 64;            // K per stage: 64 BF16 = one 128-byte swizzle row
+constexpr int UMMA_K = 16;        // K per tcgen05.mma (kind::f16)
+constexpr int NTHREADS = 192;
+constexpr long long kWaitBudget = 4000000000LL;   // ~2 s of SM clock per wait
+
+// ------------------------------------------------------------------ PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok;
+}
+// true when the phase with the given parity completed; false after the budget
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitBudget) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (16-byte units), descriptor version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// Instruction descriptor, kind::f16: FP32 D, BF16 A and B, majorness, N, M.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------- kernel ----
+struct Maps {
+    CUtensorMap a[3];
+    CUtensorMap b[3];
+};
+
+struct Params {
+    int64_t M, N;          // output size
+    int64_t kblocks;       // K blocks (of 64) in the whole K range
+    int64_t kblocks_per_split;
+    int npairs;
+    float *D;              // EPI_STORE: output (or split partial base), column-major
+    int64_t ldd;
+    int64_t split_stride;  // elements between split partials (0: no split)
+    const float *R;        // EPI_ERR: reference
+    int64_t ldr;
+    double *errp;          // EPI_ERR: one partial per CTA
+    int *err_flag;         // timeout flag
+};
+
+template <bool A_MN, int BN_, int EPI>
+struct Cfg {
+    static constexpr int A_BYTES = BM * BK * 2;          // 16 KB
+    static constexpr int B_BYTES = BN_ * BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (BN_ >= 256) ? 4 : (BN_ >= 128 ? 6 : 8);
+    static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr uint32_t TMEM_COLS = BN_ < 32 ? 32 : BN_;
+};
+
+template <bool A_MN, int BN_, int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ Maps maps, Params p) {
+    using C = Cfg<A_MN, BN_, EPI>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + C::STAGES * C::STAGE);
+    uint64_t *empty = full + C::STAGES;
+    uint64_t *tmem_full = empty + C::STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(tmem_full + 1);
+    int *abort_sh = (int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN_;
+    const int64_t kb0 = (int64_t)blockIdx.z * p.kblocks_per_split;
+    int64_t kb1 = kb0 + p.kblocks_per_split;
+    if (kb1 > p.kblocks) kb1 = p.kblocks;
+    const int64_t iters = (kb1 > kb0 ? kb1 - kb0 : 0) * p.npairs;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tmem_full, 1);
+        *abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        for (int64_t it = 0; it < iters; ++it) {
+            const int s = (int)(it % C::STAGES);
+            const uint32_t round = (uint32_t)(it / C::STAGES);
+            if (it >= C::STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) {
+                atomicExch(p.err_flag, 1);
+                *abort_sh = 1;
+                break;
+            }
+            if (*(volatile int *)abort_sh) break;
+            const int pair = (int)(it % p.npairs);
+            const int64_t kb = kb0 + it / p.npairs;
+            uint8_t *sa = smem + s * C::STAGE;
+            uint8_t *sb = sa + C::A_BYTES;
+            mbar_expect_tx(&full[s], C::STAGE);
+            const int k_el = (int)(kb * BK);
+            if (A_MN) {
+                // A stored M-contiguous: two 64 (M) x 64 (K) boxes
+                tma_load_2d(sa, &maps.a[pair], &full[s], (int)m0, k_el);
+                tma_load_2d(sa + BM * BK, &maps.a[pair], &full[s], (int)m0 + 64, k_el);
+            } else {
+                tma_load_2d(sa, &maps.a[pair], &full[s], k_el, (int)m0);
+            }
+            tma_load_2d(sb, &maps.b[pair], &full[s], k_el, (int)n0);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idesc = idesc_bf16(BM, BN_, A_MN, false);
+        bool ok = true;
+        for (int64_t it = 0; it < iters; ++it) {
+            const int s = (int)(it % C::STAGES);
+            const uint32_t round = (uint32_t)(it / C::STAGES);
+            if (!mbar_wait(&full[s], round & 1)) {
+                atomicExch(p.err_flag, 1);
+                *abort_sh = 1;
+                ok = false;
+                break;
+            }
+            if (*(volatile int *)abort_sh) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * C::STAGE);
+            const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                uint64_t ad, bd;
+                if (A_MN) ad = sdesc(sa + kk * (UMMA_K * 128), BM * BK, 1024);   // LBO: next 64-row M block
+                else ad = sdesc(sa + kk * (UMMA_K * 2), 16, 1024);
+                bd = sdesc(sb + kk * (UMMA_K * 2), 16, 1024);
+                umma_bf16(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(&empty[s]);
+        }
+        (void)ok;
+        umma_commit(tmem_full);   // completes once every MMA issued above has finished
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;   // TMEM lane quarter this warp may access
+        const bool got = __all_sync(0xffffffffu, mbar_wait(tmem_full, 0) ? 1 : 0) != 0;
+        if (!got) atomicExch(p.err_flag, 1);
+        tc_fence_after();
+        const int64_t row = m0 + 32 * q + lane;
+        double local = 0.0;
+        if (got && iters > 0) {
+#pragma unroll 1
+            for (int c = 0; c < BN_; c += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+                if (row < p.M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t col = n0 + c + j;
+                        if (col < p.N) {
+                            if (EPI == EPI_STORE) {
+                                p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = v[j];
+                            } else {
+                                const double d = (double)p.R[row + col * p.ldr] - (double)v[j];
+                                local = fma(d, d, local);
+                            }
+                        }
+                    }
+                }
+            }
+        } else if (EPI == EPI_STORE && iters == 0 && row < p.M) {
+            for (int c = 0; c < BN_; ++c) {
+                const int64_t col = n0 + c;
+                if (col < p.N) p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = 0.0f;
+            }
+        }
+        if (EPI == EPI_ERR) {
+            local = warp_sum(local);
+            __shared__ double red[4];
+            if (lane == 0) red[q] = local;
+            asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
+            if (warp == 2 && lane == 0)
+                p.errp[blockIdx.x + (int64_t)blockIdx.y * gridDim.x] = red[0] + red[1] + red[2] + red[3];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+__global__ void split_reduce_kernel(const float *__restrict__ part, int64_t M, int64_t N, int S, float *D,
+                                    int64_t ldd) {
+    const int64_t total = M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < S; ++z) s += part[(int64_t)z * total + e];
+        D[(e % M) + (e / M) * ldd] = s;
+    }
+}
+
+// --------------------------------------------------------- split kernels ----
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// X (rows x cols, ldx, FP32) -> X_hi, X_lo (same shape, ld ldo), with the
+// Frobenius partial sums and the non-finite flag of X (the S0 pass).
+__global__ void split_norm_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo, int64_t ldo,
+                                  double *partials, int *flags) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    int bad = 0;
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % rows, j = e / rows;
+        const float x = X[i + j * ldx];
+        if (!isfinite(x)) bad = 1;
+        acc = fma((double)x, (double)x, acc);
+        __nv_bfloat16 h, l;
+        split_bf16(x, h, l);
+        hi[i + j * ldo] = h;
+        lo[i + j * ldo] = l;
+    }
+    if (partials) {
+        const double tot = block_sum(acc, red);
+        bad = __syncthreads_or(bad);
+        if (threadIdx.x == 0) {
+            partials[blockIdx.x] = tot;
+            flags[blockIdx.x] = bad;
+        }
+    }
+}
+
+// Xt_hi/lo (cols x rows, ld ldt) = split(X^T), X rows x cols (ldx), FP32.
+__global__ void split_transpose_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                       __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo, int64_t ldt) {
+    __shared__ float tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t i = i0 + threadIdx.x, j = j0 + dy;
+        tile[dy][threadIdx.x] = (i < rows && j < cols) ? X[i + j * ldx] : 0.f;
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t j = j0 + threadIdx.x, i = i0 + dy;   // output (j, i) = X(i, j)
+        if (i < rows && j < cols) {
+            __nv_bfloat16 h, l;
+            split_bf16(tile[threadIdx.x][dy], h, l);
+            hi[j + i * ldt] = h;
+            lo[j + i * ldt] = l;
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side ----
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D BF16 map: inner extent `inner` (contiguous), `outer` rows of stride
+// ld elements, box box_in x box_out, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_in,
+              uint32_t box_out) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    if (((uintptr_t)base & 15) || ((ld * 2) & 15)) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld * 2};
+    cuuint32_t box[2] = {box_in, box_out};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <bool A_MN, int BN_, int EPI>
+cudaError_t launch_tc(const Maps &maps, Params p, int splits, cudaStream_t s) {
+    using C = Cfg<A_MN, BN_, EPI>;
+    static bool attr = false;
+    if (!attr) {
+        EOD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<A_MN, BN_, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          C::SMEM));
+        attr = true;
+    }
+    dim3 grid((unsigned)((p.M + BM - 1) / BM), (unsigned)((p.N + BN_ - 1) / BN_), (unsigned)splits);
+    count_launch();
+    tc_gemm_kernel<A_MN, BN_, EPI><<<grid, NTHREADS, C::SMEM, s>>>(maps, p);
+    return cudaGetLastError();
+}
+
+template <bool A_MN, int EPI>
+cudaError_t launch_bn(int bn, const Maps &maps, const Params &p, int splits, cudaStream_t s) {
+    switch (bn) {
+    case 32: return launch_tc<A_MN, 32, EPI>(maps, p, splits, s);
+    case 64: return launch_tc<A_MN, 64, EPI>(maps, p, splits, s);
+    case 128: return launch_tc<A_MN, 128, EPI>(maps, p, splits, s);
+    default: return launch_tc<A_MN, 256, EPI>(maps, p, splits, s);
+    }
+}
+
+int pick_bn(int64_t N) {
+    if (N <= 32) return 32;
+    if (N <= 64) return 64;
+    if (N <= 128) return 128;
+    return 256;
+}
+
+}  // namespace tc
+
+// Runs one tensor-core contraction (see tc_gemm.cuh).
+cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s) {
+    using namespace tc;
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    const int bn = g.bn > 0 ? g.bn : pick_bn(g.N);
+    Maps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    for (int i = 0; i < g.npairs; ++i) {
+        const TcOperand &a = g.a[i], &b = g.b[i];
+        bool ok = g.a_mn_major ? make_map(&maps.a[i], a.ptr, a.inner, a.outer, a.ld, 64, 64)
+                               : make_map(&maps.a[i], a.ptr, a.inner, a.outer, a.ld, 64, BM);
+        ok = ok && make_map(&maps.b[i], b.ptr, b.inner, b.outer, b.ld, 64, (uint32_t)bn);
+        if (!ok) return cudaErrorInvalidValue;
+    }
+    Params p;
+    p.M = g.M;
+    p.N = g.N;
+    p.kblocks = (g.K + BK - 1) / BK;
+    p.npairs = g.npairs;
+    p.err_flag = g.err_flag;
+    p.R = g.ref;
+    p.ldr = g.ldref;
+    p.errp = g.err_partials;
+    const int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + bn - 1) / bn);
+    int splits = 1;
+    if (g.epilogue == EPI_STORE && tiles < kNumSMs && p.kblocks >= 8) {
+        splits = (int)((kNumSMs + tiles - 1) / tiles);
+        if (splits > p.kblocks / 4) splits = (int)(p.kblocks / 4);
+        if (splits > 8) splits = 8;
+        if (splits < 1) splits = 1;
+    }
+    float *part = nullptr;
+    size_t mark = ws ? ws->mark() : 0;
+    if (splits > 1) {
+        part = ws ? (float *)ws->take(sizeof(float) * (size_t)splits * g.M * g.N) : nullptr;
+        if (!part) splits = 1;
+    }
+    p.kblocks_per_split = (p.kblocks + splits - 1) / splits;
+    const double flops = 2.0 * g.M * g.N * g.K * g.npairs;
+    const double bytes = 2.0 * g.npairs * ((double)g.M * g.K + (double)g.K * g.N) +
+                         (g.epilogue == EPI_ERR ? 4.0 * g.M * g.N : 4.0 * g.M * g.N);
+    ProfScope prof(PROF_TC_GEMM, flops, bytes, s);
+    if (splits > 1) {
+        p.D = part;
+        p.ldd = g.M;
+        p.split_stride = g.M * g.N;
+    } else {
+        p.D = g.D;
+        p.ldd = g.ldd;
+        p.split_stride = 0;
+    }
+    cudaError_t e;
+    if (g.epilogue == EPI_ERR)
+        e = g.a_mn_major ? launch_bn<true, EPI_ERR>(bn, maps, p, 1, s) : launch_bn<false, EPI_ERR>(bn, maps, p, 1, s);
+    else
+        e = g.a_mn_major ? launch_bn<true, EPI_STORE>(bn, maps, p, splits, s)
+                         : launch_bn<false, EPI_STORE>(bn, maps, p, splits, s);
+    if (e != cudaSuccess) return e;
+    if (splits > 1) {
+        int blocks = (int)std::min<int64_t>((g.M * g.N + 255) / 256, 4 * kNumSMs * 8);
+        count_launch();
+        split_reduce_kernel<<<blocks, 256, 0, s>>>(part, g.M, g.N, splits, g.D, g.ldd);
+        EOD_CUDA_TRY(cudaGetLastError());
+        ws->release(mark);
+    }
+    return cudaSuccess;
+}
+
+int64_t tc_gemm_err_ctas(int64_t M, int64_t N, int bn) {
+    if (bn <= 0) bn = tc::pick_bn(N);
+    return ((M + tc::BM - 1) / tc::BM) * ((N + bn - 1) / bn);
+}
+
+cudaError_t split_norm(const float *X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16 *hi,
+                       __nv_bfloat16 *lo, int64_t ldo, double *partials, int *flags, int blocks, cudaStream_t s) {
+    ProfScope prof(PROF_STREAM, 2.0 * rows * cols, 8.0 * rows * cols, s);
+    count_launch();
+    tc::split_norm_kernel<<<blocks, 512, 0, s>>>(X, rows, cols, ldx, hi, lo, ldo, partials, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t split_transpose(const float *X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16 *hi,
+                            __nv_bfloat16 *lo, int64_t ldt, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    ProfScope prof(PROF_STREAM, 0.0, 8.0 * rows * cols, s);
+    count_launch();
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+    tc::split_transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(X, rows, cols, ldx, hi, lo, ldt);
+    return cudaGetLastError();
+}
+
+}  // namespace eod
