@@ -40,6 +40,15 @@ BLOCK_K = 64
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 # FP32 (FFMA) peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]) * 1e3, float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 1.9e6, 6800.0, "fallback"
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -50,6 +59,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-compare", action="store_true", help="skip the mixed-vs-plain comparison workloads")
     return p.parse_args()
 
 
@@ -277,6 +287,10 @@ def run_ours(args):
                                 "ms_per_step": t32 / max(2, args.steps // 2)}},
         "clocks": clk,
     }
+    if not args.no_compare:
+        comp, troof = compare_forms(eod, 3, 1, flush)
+        out["mixed_vs_plain"] = comp
+        out["roofline_tensor"] = troof
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, sample, el = oracle_sample(A_np, w.tol * float(np.linalg.norm(A_np)), 15.0)
         out["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
@@ -286,6 +300,70 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def compare_forms(eod, steps, warmup, flush):
+    """Mixed (BF16 split on tcgen05) against the plain FP64 path on the same
+    inputs: the image-like 2048^2 matrix, the 8192^2 harmonic matrix and the
+    262144 x 224 hyperspectral matrix.  Returns a list of result dicts and
+    the tensor-core kernel's roofline over the mixed runs."""
+    import numpy as np
+    import torch
+    import workloads as W
+
+    bf16_peak, _, src = _measured_peaks()
+    out, tc_fl, tc_ms, tc_n = [], 0.0, 0.0, 0
+    cases = [("image-like 2048x2048 tol 1e-3 rel", lambda: W.image_like(), 64),
+             ("harmonic 8192x8192 rank-400 1/i + noise 1e-6, tol 0.0128 rel", lambda: W.harmonic(), 64),
+             ("hyperspectral 262144x224, 12 endmembers, 30 dB, tol 0.047 rel", lambda: W.hyperspectral(), 16)]
+    for name, make, k in cases:
+        w = make()
+        A64 = torch.from_numpy(np.asfortranarray(w.A.astype(np.float64))).cuda()
+        A32 = torch.from_numpy(np.asfortranarray(w.A.astype(np.float32))).cuda()
+        del w.A
+        m, n = A64.shape
+        res = {}
+        for form, A, prec in (("plain_f64", A64, "plain"), ("plain_f32", A32, "plain"), ("mixed_bf16", A32, "mixed")):
+            for _ in range(warmup):
+                f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
+                f.close()
+            torch.cuda.synchronize()
+            if prec == "mixed":
+                eod.eod_abe_debug_profile(1)
+            tot = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
+                e1.record()
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+                r, rel = f.rank, f.rel_err
+                f.close()
+            if prec == "mixed":
+                pr = eod.profile_read(eod.PROF_TC_GEMM)
+                eod.eod_abe_debug_profile(0)
+                tc_fl += pr["flops"]
+                tc_ms += pr["ms"]
+                tc_n += pr["launches"]
+            ms = tot / steps
+            res[form] = {"gflops": eod.model_flops(m, n, r, k, True) / (ms / 1e3) / 1e9, "ms": ms, "rank": r,
+                         "rel_err": rel}
+        base = res["plain_f64"]
+        for form, v in res.items():
+            v["rank_equal_f64"] = v["rank"] == base["rank"]
+            v["d_rel_err_vs_f64"] = abs(v["rel_err"] - base["rel_err"])
+        out.append({"workload": name, "m": m, "n": n, "k": k, "forms": res,
+                    "mixed_speedup_vs_f64": base["ms"] / res["mixed_bf16"]["ms"]})
+        del A64, A32
+        torch.cuda.empty_cache()
+    ach = tc_fl / (tc_ms / 1e3) / 1e9 if tc_ms > 0 else None
+    roof = {"bound": "tensor", "kernel": "tc_gemm (tcgen05 kind::f16, BF16 split pairs)", "achieved": ach,
+            "peak": bf16_peak, "unit": "GFLOP/s", "frac": (ach / bf16_peak) if ach else None,
+            "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)", "launches": tc_n,
+            "flops_per_launch": tc_fl / tc_n if tc_n else None, "traffic": None}
+    return out, roof
 
 
 # ---------------------------------------------------------- reference arm --

@@ -23,26 +23,32 @@
 namespace eod {
 namespace {
 
-__global__ void chol_small_kernel(const double *__restrict__ G, int64_t ldg, int w, int decide,
-                                  double eps2, double delta_coef, double rho, double shift,
-                                  double *__restrict__ R, double *__restrict__ Rinv, int64_t ldr,
-                                  int *info) {
+__global__ void __launch_bounds__(256) chol_small_kernel(const double *__restrict__ G, int64_t ldg, int w,
+                                                         int decide, double eps2, double delta_coef, double rho,
+                                                         double shift, double *__restrict__ R, int64_t ldr,
+                                                         int *info) {
+    // L = R^T (lower triangle, column-major): column j of L is row j of R and
+    // is contiguous, so the rank-1 trailing update reads it without conflicts.
     extern __shared__ double sh[];
-    double *S = sh;              // w x w: R in the upper triangle, X = R^{-1} transposed below it
+    double *S = sh;              // w x w, lower triangle
     double *g0 = sh + w * w;     // original diagonal
-    double *xd = g0 + w;         // diagonal of R^{-1}
     __shared__ int p_sh, code_sh, go_sh;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double rinv_sh;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
 
-    for (int e = tid; e < w * w; e += nt) {
-        const int i = e % w, j = e / w;
-        S[e] = (i <= j) ? G[i + (int64_t)j * ldg] + (i == j ? shift : 0.0) : 0.0;
-    }
-    for (int j = tid; j < w; j += nt) g0[j] = G[j + (int64_t)j * ldg] + shift;
+    // S(i, c) = G(c, i) for i >= c (G's upper triangle, transposed)
+    for (int c = ty; c < w; c += 16)
+        for (int i = tx; i < w; i += 16)
+            S[i + c * w] = (i >= c) ? G[c + (int64_t)i * ldg] + (i == c ? shift : 0.0) : 0.0;
+    for (int j = tid; j < w; j += blockDim.x) g0[j] = G[j + (int64_t)j * ldg] + shift;
     if (tid == 0) { p_sh = w; code_sh = CHOL_ALL; }
     __syncthreads();
 
+    double rinv_prev = 0.0;
     for (int j = 0; j < w; ++j) {
+        // phase 1: thread 0 decides pivot j while every thread finishes
+        // column j-1 of L (scaled by the previous pivot's 1/L(j-1,j-1))
         if (tid == 0) {
             const double d = S[j + j * w];
             int keep;
@@ -55,43 +61,77 @@ __global__ void chol_small_kernel(const double *__restrict__ G, int64_t ldg, int
                 keep = (d > 0.0 && isfinite(d)) ? 1 : 0;
                 if (!keep) code_sh = CHOL_FAIL;
             }
-            if (keep) S[j + j * w] = sqrt(d);
-            else p_sh = j;
+            if (keep) {
+                const double ri = rsqrt(d);
+                S[j + j * w] = d * ri;
+                rinv_sh = ri;
+            } else {
+                p_sh = j;
+            }
             go_sh = keep;
         }
+        if (j > 0)
+            for (int i = j + tid; i < w; i += blockDim.x) S[i + (j - 1) * w] *= rinv_prev;
         __syncthreads();
         if (!go_sh) break;
-        const double rjj = S[j + j * w];
-        for (int l = j + 1 + tid; l < w; l += nt) S[j + l * w] /= rjj;
-        __syncthreads();
-        const int rem = w - j - 1;
-        for (int e = tid; e < rem * rem; e += nt) {
-            const int ii = j + 1 + e % rem, ll = j + 1 + e / rem;
-            if (ii <= ll) S[ii + ll * w] = fma(-S[j + ii * w], S[j + ll * w], S[ii + ll * w]);
+        const double rinv = rinv_sh;
+        // phase 2: trailing update S(ii, ll) -= L(ii, j) L(ll, j), j < ll <= ii,
+        // from the still unscaled column j times 1/L(j,j)
+        for (int ll = j + 1 + ty; ll < w; ll += 16) {
+            const double lj = S[ll + j * w] * rinv;
+            for (int ii = ll + tx; ii < w; ii += 16) S[ii + ll * w] = fma(-S[ii + j * w] * rinv, lj, S[ii + ll * w]);
         }
         __syncthreads();
+        rinv_prev = rinv;
     }
     const int p = p_sh;
-
-    // X = R^{-1}, row by row from the bottom: X(i,c) = -sum_{l=i+1..c} R(i,l) X(l,c) / R(i,i).
-    // X(i,c), i < c, lives at S[c + i*w] (below the diagonal); X(i,i) in xd[i].
-    for (int i = tid; i < p; i += nt) xd[i] = 1.0 / S[i + i * w];
-    __syncthreads();
-    for (int i = p - 2; i >= 0; --i) {
-        const double rii = S[i + i * w];
-        for (int c = i + 1 + tid; c < p; c += nt) {
-            double acc = S[i + c * w] * xd[c];
-            for (int l = i + 1; l < c; ++l) acc = fma(S[i + l * w], S[c + l * w], acc);
-            S[c + i * w] = -acc / rii;
-        }
-        __syncthreads();
-    }
-    for (int e = tid; e < p * p; e += nt) {
-        const int i = e % p, c = e / p;
-        R[i + (int64_t)c * ldr] = (i <= c) ? S[i + c * w] : 0.0;
-        Rinv[i + (int64_t)c * ldr] = (i < c) ? S[c + i * w] : (i == c ? xd[i] : 0.0);
-    }
+    for (int c = ty; c < p; c += 16)
+        for (int i = tx; i < p; i += 16) R[i + (int64_t)c * ldr] = (i <= c) ? S[c + i * w] : 0.0;
     if (tid == 0) { info[0] = p; info[1] = code_sh; }
+}
+
+// X = R^{-1} for upper-triangular R (p x p, ld ldr), one warp per column:
+// column c solves R x = e_c from the bottom, x_j = b_j / R(j,j), then
+// b_i -= x_j R(i,j) for i < j, with b spread over the lanes.
+__global__ void __launch_bounds__(128) tri_inverse_kernel(const double *__restrict__ R, int64_t ldr, int p,
+                                                          const int *p_dev, double *__restrict__ X,
+                                                          int64_t ldx) {
+    __shared__ double rd[128];
+    if (p_dev) p = *p_dev;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) rd[j] = 1.0 / R[j + (int64_t)j * ldr];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (c >= p) return;
+    constexpr int PER = 4;                      // p <= 128: lane holds b_i for i = lane + 32 t
+    const int tmax = c >> 5;
+    double b[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) b[t] = (lane + 32 * t == c) ? 1.0 : 0.0;
+    for (int j = c; j >= 0; --j) {
+        const int owner = j & 31, slot = j >> 5;
+        double bj = 0.0;
+#pragma unroll
+        for (int t = 0; t < PER; ++t)
+            if (t == slot) bj = b[t];
+        bj = __shfl_sync(0xffffffffu, bj, owner);
+        const double xj = bj * rd[j];
+        if (lane == owner) {
+#pragma unroll
+            for (int t = 0; t < PER; ++t)
+                if (t == slot) b[t] = xj;
+        }
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+            const int i = lane + 32 * t;
+            if (t <= tmax && i < j) b[t] = fma(-xj, R[i + (int64_t)j * ldr], b[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const int i = lane + 32 * t;
+        if (i < p) X[i + (int64_t)c * ldx] = (i <= c) ? b[t] : 0.0;
+    }
 }
 
 __global__ void tdiag_kernel(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
@@ -115,17 +155,27 @@ cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double e
                        double rho, double shift, double *R, double *Rinv, int64_t ldr, int *info,
                        cudaStream_t s) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * ((size_t)w * w + 2 * (size_t)w);
+    const size_t smem = sizeof(double) * ((size_t)w * w + (size_t)w);
     static bool attr_set = false;
     if (!attr_set) {
         EOD_CUDA_TRY(cudaFuncSetAttribute(chol_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(sizeof(double) * (128 * 128 + 256))));
+                                          (int)(sizeof(double) * (128 * 128 + 128))));
         attr_set = true;
     }
-    ProfScope prof(PROF_CHOL, (double)w * w * w / 3.0, sizeof(double) * 2.0 * w * w, s);
-    count_launch();
-    chol_small_kernel<<<1, 256, smem, s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R, Rinv, ldr, info);
-    return cudaGetLastError();
+    {
+        ProfScope prof(PROF_CHOL, (double)w * w * w / 3.0, sizeof(double) * 2.0 * w * w, s);
+        count_launch();
+        chol_small_kernel<<<1, 256, smem, s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R, ldr, info);
+        EOD_CUDA_TRY(cudaGetLastError());
+    }
+    if (Rinv) {
+        // the factored order p is read on the device (info[0])
+        ProfScope prof(PROF_CHOL, (double)w * w * w / 3.0, sizeof(double) * 2.0 * w * w, s);
+        count_launch();
+        tri_inverse_kernel<<<(w + 3) / 4, 128, 0, s>>>(R, ldr, w, info, Rinv, ldr);
+        EOD_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
 }
 
 cudaError_t tdiag_product(const double *R1, const double *R2, int64_t ldr, const int *p_dev, double *tdiag,

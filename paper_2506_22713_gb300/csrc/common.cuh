@@ -161,6 +161,12 @@ cudaError_t scale_column(T *x, int64_t m, const double *inv_norm_src, cudaStream
 template <typename T>
 cudaError_t fill_zero(T *x, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s);
 
+// G (w x w, upper triangle, FP64, ld ldg) = Y^T Y for a tall panel Y (m x w,
+// w <= 128); FP64 accumulation of the exact products (gram.cu).
+template <typename T>
+cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, int64_t ldg, Scratch *ws,
+                        cudaStream_t s);
+
 // --------------------------------------------------------------------------
 // Small dense factorisations (one CTA)
 // --------------------------------------------------------------------------

@@ -160,7 +160,8 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
     int passes = 2;
     double shift = 0.0;
     for (int pass = 0; pass < passes; ++pass) {
-        EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
+        if (p <= 128) EOD_CU(gram_skinny<T>(W, rows, (int)p, ldw, w.G, p, ws, s));
+        else EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
         double *Rpass = (pass == 0) ? Rout : w.Rp + kNB * kNB;  // pass factor storage
         eod_status st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
         if (st == EOD_EPRECISION && pass == 0 && shift == 0.0) {
@@ -171,7 +172,8 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
             const double u = std::is_same<T, float>::value ? kU32 : kU64;
             shift = 11.0 * ((double)rows * p + (double)p * (p + 1)) * u * hm.val[0];
             passes = 3;
-            EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
+            if (p <= 128) EOD_CU(gram_skinny<T>(W, rows, (int)p, ldw, w.G, p, ws, s));
+            else EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
             st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
         }
         if (st != EOD_OK) return st;
@@ -285,7 +287,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 EOD_CU((gemm<T, T, T, T>(false, false, m, wdt, kept, -1.0, Qb, m, S, cap, 1.0, Yc, m, ex, &ws, s)));
             }
             // step 5 (pass 1) + steps 6-11: Gram, Cholesky with the rank test
-            EOD_CU((gemm<T, T, double, double>(true, false, wdt, wdt, m, 1.0, Yc, m, Yc, m, 0.0, G, k, sym, &ws, s)));
+            EOD_CU(gram_skinny<T>(Yc, m, (int)wdt, m, G, k, &ws, s));
             EOD_CU(chol_small(G, k, (int)wdt, 1, eps2, delta_coef, Traits<T>::rho, 0.0, R1, R1i, k, info, s));
             EOD_CU(cudaMemcpyAsync(hm.info, info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
             EOD_CU(cudaStreamSynchronize(s));
@@ -298,7 +300,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                     Ri = RinvT;
                 }
                 EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, Yc, m, Ri, k, 0.0, T1, m, bup, &ws, s)));
-                EOD_CU((gemm<T, T, double, double>(true, false, p, p, m, 1.0, T1, m, T1, m, 0.0, G, k, sym, &ws, s)));
+                EOD_CU(gram_skinny<T>(T1, m, p, m, G, k, &ws, s));
                 EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, R2i, k, info, s));
                 const T *Ri2 = (const T *)R2i;
                 if (!std::is_same<T, double>::value) {
