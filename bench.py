@@ -52,6 +52,35 @@ def _measured_peaks():
 L2_BYTES = 129 * 1024 * 1024
 
 
+PROFILE_CASES = {
+    "image2048_f64": ("image_like", {}, "f64", "plain", 64),
+    "image2048_mixed": ("image_like", {}, "f32", "mixed", 64),
+    "harmonic8192_mixed": ("harmonic", {}, "f32", "mixed", 64),
+    "hyperspectral_mixed": ("hyperspectral", {}, "f32", "mixed", 16),
+}
+
+
+def run_profile_case(name):
+    """One warm-up and one factorisation of a named workload, nothing timed:
+    the command ncu captures (NVTX ranges eod.norm, eod.basis_ext_block,
+    eod.projection, eod.reconstruction_error, eod.core select the phase)."""
+    import numpy as np
+    import torch
+
+    import paper_2506_22713_gb300 as eod
+    import workloads as W
+
+    gen, kw, dt, prec, k = PROFILE_CASES[name]
+    w = W.by_name(gen, **kw)
+    A = torch.from_numpy(np.asfortranarray(w.A.astype(np.float64 if dt == "f64" else np.float32))).cuda()
+    for _ in range(2):
+        f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
+        r, rel = f.rank, f.rel_err
+        f.close()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "rank": r, "rel_err": rel}))
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -60,6 +89,8 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the mixed-vs-plain comparison workloads")
+    p.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
+                   help="run one warm-up and one factorisation of a named workload (for ncu) and exit")
     return p.parse_args()
 
 
@@ -407,6 +438,9 @@ def run_reference(args):
 
 def main():
     args = _args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

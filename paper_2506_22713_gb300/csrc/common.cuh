@@ -167,6 +167,11 @@ template <typename T>
 cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, int64_t ldg, Scratch *ws,
                         cudaStream_t s);
 
+// Upper triangle of G (p x p, FP64, ld ldg) = W^T W for FP32 W (rows x p,
+// any p): exact products and TwoSum accumulation in FP32, FP64 per tile.
+cudaError_t gram_tiled_f32(const float *W, int64_t rows, int64_t p, int64_t ldw, double *G, int64_t ldg,
+                           Scratch *ws, cudaStream_t s);
+
 // --------------------------------------------------------------------------
 // Small dense factorisations (one CTA)
 // --------------------------------------------------------------------------

@@ -16,6 +16,7 @@
 // device.
 #include "common.cuh"
 #include "tc_gemm.cuh"
+#include "instrument.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -147,6 +148,17 @@ static eod_status trsm_right(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, in
     return EOD_OK;
 }
 
+// G (p x p, upper, FP64) = W^T W: the skinny kernel for p <= 128, else a
+// tiled one (FP64 DFMA for FP64 data, exact-product FP32 sums for FP32 data).
+template <typename T>
+static eod_status gram_full(const T *W, int64_t rows, int64_t p, int64_t ldw, double *G, const GemmExtra &sym,
+                            Scratch *ws, cudaStream_t s) {
+    if (p <= 128) EOD_CU(gram_skinny<T>(W, rows, (int)p, ldw, G, p, ws, s));
+    else if (std::is_same<T, float>::value) EOD_CU(gram_tiled_f32((const float *)W, rows, p, ldw, G, p, ws, s));
+    else EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, G, p, sym, ws, s)));
+    return EOD_OK;
+}
+
 // CholQR2 (shifted CholQR3 when the first Cholesky breaks down; Fukaya,
 // Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SISC 2020): W (rows x p) is
 // replaced by its orthonormal factor and Rout (p x p, ld p) by R with
@@ -160,8 +172,7 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
     int passes = 2;
     double shift = 0.0;
     for (int pass = 0; pass < passes; ++pass) {
-        if (p <= 128) EOD_CU(gram_skinny<T>(W, rows, (int)p, ldw, w.G, p, ws, s));
-        else EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
+        EOD_TRY(gram_full(W, rows, p, ldw, w.G, sym, ws, s));
         double *Rpass = (pass == 0) ? Rout : w.Rp + kNB * kNB;  // pass factor storage
         eod_status st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
         if (st == EOD_EPRECISION && pass == 0 && shift == 0.0) {
@@ -172,8 +183,7 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
             const double u = std::is_same<T, float>::value ? kU32 : kU64;
             shift = 11.0 * ((double)rows * p + (double)p * (p + 1)) * u * hm.val[0];
             passes = 3;
-            if (p <= 128) EOD_CU(gram_skinny<T>(W, rows, (int)p, ldw, w.G, p, ws, s));
-            else EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, w.G, p, sym, ws, s)));
+            EOD_TRY(gram_full(W, rows, p, ldw, w.G, sym, ws, s));
             st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
         }
         if (st != EOD_OK) return st;
@@ -240,12 +250,15 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     double *d_norm = dsc, *d_t = dsc + 1, *d_err = dsc + 2;
 
     // ---- S0: ||A||_F and finiteness ----
-    EOD_CU(cudaMemsetAsync(iflag, 0, sizeof(int) * 4, s));
-    EOD_CU(fro_norm<T>(A, m, n, lda, d_norm, iflag, &ws, s));
-    EOD_CU(cudaMemcpyAsync(hm.val, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
-    EOD_CU(cudaMemcpyAsync(hm.flag, iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    EOD_CU(cudaStreamSynchronize(s));
-    if (hm.flag[0]) return EOD_ENONFINITE;
+    {
+        Phase ph_norm("eod.norm");
+        EOD_CU(cudaMemsetAsync(iflag, 0, sizeof(int) * 4, s));
+        EOD_CU(fro_norm<T>(A, m, n, lda, d_norm, iflag, &ws, s));
+        EOD_CU(cudaMemcpyAsync(hm.val, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        EOD_CU(cudaMemcpyAsync(hm.flag, iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        EOD_CU(cudaStreamSynchronize(s));
+        if (hm.flag[0]) return EOD_ENONFINITE;
+    }
     const double norm_a = hm.val[0];
     const double eps = (o.tol_mode == EOD_TOL_REL_FRO) ? tol * norm_a : tol;
     F->norm_a = norm_a;
@@ -271,6 +284,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
         const int64_t f = std::min(k, cap - kept);
         ++blocks;
         // steps 3-4: Omega_j and Y = A Omega_j
+        Phase ph_block("eod.basis_ext_block");
         if (mixed) {
             EOD_TRY(mx.sketch(kept, f, seed, o.batch_index, Y, m, s));
         } else {
@@ -387,14 +401,18 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(ar.get(&Rt, (size_t)r * r));
     EOD_TRY(ar.get(&D, (size_t)r * r));
     EOD_TRY(ar.get(&Rc, (size_t)r * r));
-    if (mixed) {
-        EOD_TRY(mx.project(Qb, r, Ct, s));
-    } else {
-        EOD_CU((gemm<T, T, T, T>(true, false, n, r, m, 1.0, A, lda, Qb, m, 0.0, Ct, n, ex, &ws, s)));
+    {
+        Phase ph("eod.projection");
+        if (mixed) {
+            EOD_TRY(mx.project(Qb, r, Ct, s));
+        } else {
+            EOD_CU((gemm<T, T, T, T>(true, false, n, r, m, 1.0, A, lda, Qb, m, 0.0, Ct, n, ex, &ws, s)));
+        }
     }
 
     // ---- reconstruction error: || A - Q C ||_F / ||A||_F ----
     if (o.compute_err) {
+        Phase ph("eod.reconstruction_error");
         if (mixed) {
             EOD_TRY(mx.recon_error(Qb, r, Ct, d_norm, d_err, s));
         } else {
@@ -423,6 +441,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kNB) * kNB));
     EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kNB));
     EOD_TRY(ar.get(&cw.info, (size_t)2 * nblk));
+    Phase ph_core("eod.core");
     EOD_CU((copy_matrix<T, T>(Ct, n, V, n, n, r, false, s)));
     EOD_TRY(cholqr2(cw, V, n, n, r, Rc, hm, &ws, s));                 // C^T = V R
     EOD_CU((copy_matrix<double, T>(Rc, r, Rt, r, r, r, true, s)));    // R^T

@@ -14,6 +14,8 @@
 #include "common.cuh"
 #include "instrument.cuh"
 
+#include <algorithm>
+
 namespace eod {
 namespace {
 
@@ -157,7 +159,112 @@ __global__ void gram_reduce_kernel(const double *__restrict__ part, int nparts, 
     }
 }
 
+// Upper triangle of G = W^T W for FP32 W (rows x p, any p), 64 x 64 tiles of
+// G, 256 threads with 4 x 4 outputs each, the exact-product / TwoSum
+// accumulation of GramAcc<float>; the row range is split over gridDim.z and
+// each split writes its FP64 partial tile (or G itself when unsplit).
+constexpr int TBM = 64, TBK = 16;
+
+__global__ void __launch_bounds__(GT) gram_tiled_f32_kernel(const float *__restrict__ W, int64_t rows, int64_t p,
+                                                             int64_t ldw, int64_t rows_per_split,
+                                                             double *__restrict__ out, int64_t ldo,
+                                                             int64_t split_stride) {
+    __shared__ float As[TBK][TBM + 1];
+    __shared__ float Bs[TBK][TBM + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * TBM, n0 = (int64_t)blockIdx.y * TBM;
+    if (m0 > n0 + TBM - 1) return;                     // strictly below the diagonal
+    const int64_t kb = (int64_t)blockIdx.z * rows_per_split;
+    const int64_t ke = kb + rows_per_split < rows ? kb + rows_per_split : rows;
+    GramAcc<float> acc[4][4];
+    for (int64_t k0 = kb; k0 < ke; k0 += TBK) {
+#pragma unroll
+        for (int q = 0; q < (TBM * TBK) / GT; ++q) {
+            const int e = tid + q * GT;
+            const int kk = e % TBK, i = e / TBK;
+            const int64_t gk = k0 + kk;
+            As[kk][i] = (gk < ke && m0 + i < p) ? W[gk + (m0 + i) * ldw] : 0.f;
+            Bs[kk][i] = (gk < ke && n0 + i < p) ? W[gk + (n0 + i) * ldw] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TBK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j].add(a[i], b[j]);
+        }
+        __syncthreads();
+    }
+    double *dst = out + (int64_t)blockIdx.z * split_stride;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t col = n0 + ty + 16 * j;
+        if (col >= p) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t row = m0 + tx + 16 * i;
+            if (row < p) dst[row + col * ldo] = acc[i][j].value();
+        }
+    }
+}
+
+__global__ void gram_split_reduce_kernel(const double *__restrict__ part, int S, int64_t p, double *G, int64_t ldg) {
+    const int64_t total = p * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % p, j = e / p;
+        if ((i / TBM) * TBM > (j / TBM) * TBM + TBM - 1) continue;
+        double s = 0.0;
+        for (int z = 0; z < S; ++z) s += part[(int64_t)z * total + e];
+        G[i + j * ldg] = s;
+    }
+}
+
 }  // namespace
+
+cudaError_t gram_tiled_f32(const float *W, int64_t rows, int64_t p, int64_t ldw, double *G, int64_t ldg,
+                           Scratch *ws, cudaStream_t s) {
+    if (p < 1 || rows < 1) return cudaSuccess;
+    const int64_t gt = (p + TBM - 1) / TBM;
+    const int64_t tiles = gt * (gt + 1) / 2;
+    int64_t S = 1;
+    if (tiles < 2 * kNumSMs) {
+        S = (2 * kNumSMs + tiles - 1) / tiles;
+        const int64_t smax = (rows + 4 * TBK - 1) / (4 * TBK);
+        if (S > smax) S = smax;
+        if (S < 1) S = 1;
+    }
+    size_t mark = ws->mark();
+    double *part = nullptr;
+    while (S > 1) {
+        part = (double *)ws->take(sizeof(double) * (size_t)S * p * p);
+        if (part) break;
+        S /= 2;
+    }
+    const int64_t rows_per = ((rows + S - 1) / S + TBK - 1) / TBK * TBK;
+    S = (rows + rows_per - 1) / rows_per;
+    ProfScope prof(PROF_GEMM_SIMT, (double)rows * p * (p + 1), 4.0 * rows * p, s);
+    dim3 grid((unsigned)gt, (unsigned)gt, (unsigned)S);
+    if (S > 1) {
+        count_launch(2);
+        gram_tiled_f32_kernel<<<grid, GT, 0, s>>>(W, rows, p, ldw, rows_per, part, p, p * p);
+        EOD_CUDA_TRY(cudaGetLastError());
+        const int blocks = (int)std::min<int64_t>((p * p + 255) / 256, 4 * kNumSMs * 4);
+        gram_split_reduce_kernel<<<blocks, 256, 0, s>>>(part, (int)S, p, G, ldg);
+        EOD_CUDA_TRY(cudaGetLastError());
+        ws->release(mark);
+    } else {
+        count_launch();
+        gram_tiled_f32_kernel<<<grid, GT, 0, s>>>(W, rows, p, ldw, rows_per, G, ldg, 0);
+        EOD_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
 
 template <typename T>
 cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, int64_t ldg, Scratch *ws,

@@ -1,6 +1,7 @@
 // Launch counting and per-kind CUDA-event timing (see instrument.cu).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace eod {
 
@@ -26,6 +27,16 @@ class ProfScope {
   private:
     cudaStream_t s_;
     int rec_;
+};
+
+// NVTX range for one phase of the method (visible to nsys / ncu --nvtx);
+// names are "eod.<phase>".
+class Phase {
+  public:
+    explicit Phase(const char *name) { nvtxRangePushA(name); }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase &) = delete;
+    Phase &operator=(const Phase &) = delete;
 };
 
 }  // namespace eod

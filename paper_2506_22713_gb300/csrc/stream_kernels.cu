@@ -36,14 +36,42 @@ __device__ __forceinline__ double round_bf16_from_f64(double g) {
     return __longlong_as_double((long long)b);
 }
 
-__device__ __forceinline__ double omega_value(uint64_t seed, uint32_t row, uint32_t col, uint32_t batch) {
-    uint32_t c[4] = {row, col, batch, 0u};
-    philox_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-    const double u1 = ((double)c[0] + 0.5) * 0x1p-32;
-    const double u2 = ((double)c[1] + 0.5) * 0x1p-32;
+// The draw in FP64 from the two Philox words (the definition of Omega).
+__device__ __forceinline__ double omega_value_f64(uint32_t x0, uint32_t x1) {
+    const double u1 = ((double)x0 + 0.5) * 0x1p-32;
+    const double u2 = ((double)x1 + 0.5) * 0x1p-32;
     const double radius = sqrt(-2.0 * log(u1));
     const double angle = (2.0 * 3.141592653589793) * u2;
     return round_bf16_from_f64(radius * cos(angle));
+}
+
+// The same draw evaluated in FP32 when that provably gives the same BF16
+// value.  u1, u2 and the transcendental functions are taken in FP32 (logf /
+// log1pf / sqrtf / cospif, each within a few ulp); -2 ln u1 is formed from
+// 1 - u1 through log1pf when u1 >= 1/2, so its relative error stays at a few
+// 2^-24 everywhere.  Their combined error in g is below (13/|cos| + 6) float
+// ulps of g; if no BF16 rounding midpoint lies within twice that distance of
+// the FP32 result, both roundings agree and the FP32 value is returned,
+// otherwise the FP64 formula decides.
+__device__ __forceinline__ double omega_value_fast(uint64_t seed, uint32_t row, uint32_t col, uint32_t batch) {
+    uint32_t c[4] = {row, col, batch, 0u};
+    philox_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t x0 = c[0], x1 = c[1];
+    float L;
+    if (x0 < 0x80000000u) {
+        const float u1 = ((float)x0 + 0.5f) * 0x1p-32f;
+        L = -2.f * logf(u1);
+    } else {
+        const float v = ((float)(0xFFFFFFFFu - x0) + 0.5f) * 0x1p-32f;
+        L = -2.f * log1pf(-v);
+    }
+    const float cs = cospif(2.f * (((float)x1 + 0.5f) * 0x1p-32f));
+    const float g = sqrtf(L) * cs;
+    const int low = (int)(__float_as_uint(g) & 0xFFFFu);
+    const float guard = 26.f / fabsf(cs) + 12.f;
+    if (fabsf((float)(low - 0x8000)) > guard && isfinite(g))
+        return (double)__bfloat162float(__float2bfloat16_rn(g));
+    return omega_value_f64(x0, x1);
 }
 
 template <typename T> __device__ __forceinline__ T from_f64(double x) { return (T)x; }
@@ -56,7 +84,7 @@ __global__ void omega_kernel(int64_t n, int64_t col0, int64_t ncols, uint64_t se
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e % n, c = e / n;
-        out[i + c * ldo] = from_f64<T>(omega_value(seed, (uint32_t)i, (uint32_t)(col0 + c), batch));
+        out[i + c * ldo] = from_f64<T>(omega_value_fast(seed, (uint32_t)i, (uint32_t)(col0 + c), batch));
     }
 }
 

@@ -261,17 +261,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
                 if (row < p.M) {
+                    if (EPI == EPI_STORE) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t col = n0 + c + j;
-                        if (col < p.N) {
-                            if (EPI == EPI_STORE) {
-                                p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = v[j];
-                            } else {
-                                const double d = (double)p.R[row + col * p.ldr] - (double)v[j];
-                                local = fma(d, d, local);
+                        for (int j = 0; j < 16; ++j) {
+                            const int64_t col = n0 + c + j;
+                            if (col < p.N) p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = v[j];
+                        }
+                    } else {
+                        // residual in FP32 (the difference of two FP32 values), squares
+                        // summed in FP32 over the 16 columns, FP64 across chunks
+                        float part = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int64_t col = n0 + c + j;
+                            if (col < p.N) {
+                                const float d = p.R[row + col * p.ldr] - v[j];
+                                part = fmaf(d, d, part);
                             }
                         }
+                        local += (double)part;
                     }
                 }
             }

@@ -53,6 +53,14 @@ def test_omega_bit_exact(eod, n, col0, ncols, seed, batch):
     assert np.array_equal(got, ref)
 
 
+def test_omega_bit_exact_large(eod):
+    """Four million entries: the FP32 fast path with its FP64 fallback must
+    agree with the oracle's FP64 draw on every one."""
+    got = eod.omega(1 << 20, 123, 4, 0xDEADBEEF12345, 3).cpu().numpy()
+    ref = oracle.omega(1 << 20, 123, 4, 0xDEADBEEF12345, 3)
+    assert np.array_equal(got, ref)
+
+
 # ------------------------------------------------------- exact rank (c1) --
 @pytest.mark.parametrize("k", [32, 1, 7, 64])
 def test_exact_rank_512x384(eod, k):
