@@ -151,11 +151,16 @@ EOD_API eod_status eod_abe_reconstruct(const eod_factors *f, void *A_hat, int64_
 
 /* Factors `count` independent matrices (the per-image use of Sec. 4.1) in
  * one call.  A, m, n, lda, out and per_item are HOST arrays of length count;
- * A[i] is a device pointer.  Item i draws Omega with batch_index = i.  Every
- * item gets its own status in per_item[i] and, on EOD_OK, its own factors in
- * out[i] (free each with eod_abe_free).  Returns EOD_OK if every item
- * succeeded, else the first failing item's status; EOD_EINVAL for count < 1
- * or NULL arrays. */
+ * A[i] is a device pointer.  Item i draws Omega with batch_index = i, so its
+ * result equals a single eod_abe_factor_ex call with that batch_index.  The
+ * items run concurrently on a pool of worker threads, each with its own
+ * non-blocking stream (8 by default; the environment variable
+ * EOD_BATCH_STREAMS overrides), largest m*n*min(m,n) first; the workers wait
+ * for the work already queued on opts->stream.  Every item gets its own
+ * status in per_item[i] and, on EOD_OK, its own factors in out[i] (free each
+ * with eod_abe_free).  Returns EOD_OK if every item succeeded, else the
+ * status of the lowest-index failing item; EOD_EINVAL for count < 1 or NULL
+ * arrays. */
 EOD_API eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const int64_t *n,
                                   const int64_t *lda, int64_t count, double tol, uint64_t seed,
                                   const eod_opts *opts, eod_factors **out, eod_status *per_item);

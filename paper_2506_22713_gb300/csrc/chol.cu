@@ -156,12 +156,7 @@ cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double e
                        cudaStream_t s) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
     const size_t smem = sizeof(double) * ((size_t)w * w + (size_t)w);
-    static bool attr_set = false;
-    if (!attr_set) {
-        EOD_CUDA_TRY(cudaFuncSetAttribute(chol_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(sizeof(double) * (128 * 128 + 128))));
-        attr_set = true;
-    }
+    EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)(sizeof(double) * (128 * 128 + 128))));
     {
         ProfScope prof(PROF_CHOL, (double)w * w * w / 3.0, sizeof(double) * 2.0 * w * w, s);
         count_launch();

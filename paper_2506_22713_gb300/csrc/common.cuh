@@ -6,6 +6,9 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/eod_abe.h"
@@ -21,6 +24,26 @@ namespace eod {
 constexpr double kU64 = 1.1102230246251565e-16;   // 2^-53, unit roundoff of binary64
 constexpr double kU32 = 5.9604644775390625e-08;   // 2^-24, unit roundoff of binary32
 constexpr int kNumSMs = 152;
+
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device)
+// (thread-safe; a failed attempt is retried by the next caller).
+inline cudaError_t set_smem_once_ptr(const void *kernel, int bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &d : done)
+        if (d.first == kernel && d.second == dev) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.emplace_back(kernel, dev);
+    return e;
+}
+template <typename K>
+inline cudaError_t set_smem_once(K kernel, int bytes) {
+    return set_smem_once_ptr((const void *)kernel, bytes);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -23,6 +23,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 namespace eod {
@@ -667,14 +669,60 @@ eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const 
     eod_opts o;
     eod_opts_default(&o);
     if (opts) o = *opts;
-    eod_status first = EOD_OK;
     for (int64_t i = 0; i < count; ++i) {
-        eod_opts oi = o;
-        oi.batch_index = (uint64_t)i;
         out[i] = nullptr;
-        per_item[i] = factor_any(A[i], m[i], n[i], lda[i], tol, seed, &oi, &out[i]);
-        if (per_item[i] != EOD_OK && first == EOD_OK) first = per_item[i];
+        per_item[i] = EOD_EINVAL;
     }
+    // longest first: the rank is unknown, so m * n * min(m, n) stands in for the cost
+    std::vector<int64_t> order((size_t)count);
+    for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        const double ca = (double)m[a] * n[a] * std::min(m[a], n[a]);
+        const double cb = (double)m[b] * n[b] * std::min(m[b], n[b]);
+        return ca > cb;
+    });
+    int workers = 8;
+    if (const char *env = std::getenv("EOD_BATCH_STREAMS")) workers = std::max(1, std::atoi(env));
+    if (workers > count) workers = (int)count;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
+    // work already queued on the caller's stream (for example the matrices
+    // themselves) must finish before any worker stream reads it
+    cudaStream_t caller = (cudaStream_t)o.stream;
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, caller) != cudaSuccess) {
+        cudaGetLastError();
+        if (ready) cudaEventDestroy(ready);
+        return EOD_ECUDA;
+    }
+    std::atomic<int64_t> next{0};
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        cudaStream_t st = nullptr;
+        const bool own = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+        if (!own) { cudaGetLastError(); st = caller; }
+        cudaStreamWaitEvent(st, ready, 0);
+        for (;;) {
+            const int64_t j = next.fetch_add(1);
+            if (j >= count) break;
+            const int64_t i = order[(size_t)j];
+            eod_opts oi = o;
+            oi.batch_index = (uint64_t)i;
+            oi.stream = st;
+            per_item[i] = factor_any(A[i], m[i], n[i], lda[i], tol, seed, &oi, &out[i]);
+        }
+        cudaStreamSynchronize(st);
+        if (own) cudaStreamDestroy(st);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+    work();
+    for (auto &t : pool) t.join();
+    cudaEventDestroy(ready);
+    eod_status first = EOD_OK;
+    for (int64_t i = 0; i < count; ++i)
+        if (per_item[i] != EOD_OK) { first = per_item[i]; break; }
     return first;
 }
 

@@ -281,12 +281,7 @@ cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, in
     if (!part) return cudaErrorMemoryAllocation;
     size_t smem = sizeof(T) * (size_t)GR * (w + 1);
     if (smem < sizeof(double) * GT * 16) smem = sizeof(double) * GT * 16;   // room for the row-group sums
-    static bool attr = false;
-    if (!attr) {
-        EOD_CUDA_TRY(cudaFuncSetAttribute(gram_partial_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(sizeof(double) * GR * 129)));
-        attr = true;
-    }
+    EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T>, (int)(sizeof(double) * GR * 129)));
     ProfScope prof(PROF_GEMM_SIMT, (double)m * w * (w + 1), (double)sizeof(T) * m * w, s);
     count_launch(2);
     gram_partial_kernel<T><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);

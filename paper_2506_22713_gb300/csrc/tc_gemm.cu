@@ -410,12 +410,7 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, 
 template <bool A_MN, int BN_, int EPI>
 cudaError_t launch_tc(const Maps &maps, Params p, int splits, cudaStream_t s) {
     using C = Cfg<A_MN, BN_, EPI>;
-    static bool attr = false;
-    if (!attr) {
-        EOD_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<A_MN, BN_, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          C::SMEM));
-        attr = true;
-    }
+    EOD_CUDA_TRY(set_smem_once(tc_gemm_kernel<A_MN, BN_, EPI>, C::SMEM));
     dim3 grid((unsigned)((p.M + BM - 1) / BM), (unsigned)((p.N + BN_ - 1) / BN_), (unsigned)splits);
     count_launch();
     tc_gemm_kernel<A_MN, BN_, EPI><<<grid, NTHREADS, C::SMEM, s>>>(maps, p);
