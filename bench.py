@@ -174,9 +174,9 @@ def _traffic_for(kind_name, source_files):
             h.update(fh.read())
     digest = h.hexdigest()[:16]
     for line in open(path):
-        parts = line.split()
+        parts = line.split(None, 3)
         if len(parts) >= 3 and not line.startswith("#") and parts[0] == kind_name and parts[1] == digest:
-            return float(parts[2])
+            return float(parts[2]), (parts[3].strip() if len(parts) > 3 else "")
     return None
 
 
@@ -279,7 +279,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the SIMT FP64 GEMM)
     achieved = prof["flops"] / (prof["ms"] / 1e3) / 1e9 if prof and prof["ms"] > 0 else None
-    traffic = _traffic_for("gemm_simt_f64", ["paper_2506_22713_gb300/csrc/gemm_simt.cu"])
+    tr = _traffic_for("gemm_simt_f64", ["paper_2506_22713_gb300/csrc/gemm_simt.cu"])
+    traffic = tr[0] if tr else None
     per_launch = (prof["flops"] / prof["launches"]) if prof and prof["launches"] else None
     roofline = {
         "bound": "alu",
@@ -290,6 +291,8 @@ def run_ours(args):
         "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
         "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz",
         "traffic": traffic,
+        "traffic_launch": (tr[1] + "; algorithmic bytes of that launch 100302848 (A, Q read, C^T written)")
+        if tr else None,
         "launches": prof["launches"] if prof else None,
         "flops_per_launch": per_launch,
         "share_of_step": (prof["ms"] / total_ms) if prof else None,
@@ -322,6 +325,7 @@ def run_ours(args):
         comp, troof = compare_forms(eod, 3, 1, flush)
         out["mixed_vs_plain"] = comp
         out["roofline_tensor"] = troof
+        out["batched_mixed_vs_plain"] = compare_batched(eod, 1, 1)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, sample, el = oracle_sample(A_np, w.tol * float(np.linalg.norm(A_np)), 15.0)
         out["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
@@ -395,6 +399,50 @@ def compare_forms(eod, steps, warmup, flush):
             "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)", "launches": tc_n,
             "flops_per_launch": tc_fl / tc_n if tc_n else None, "traffic": None}
     return out, roof
+
+
+def compare_batched(eod, steps, warmup):
+    """Factorisations per second of the 256-matrix pixel batch, mixed against
+    plain FP64, as stated (clipped to [0, 255], tol 1e-3 relative) and
+    unclipped (same tolerance)."""
+    import numpy as np
+    import torch
+    import workloads as W
+
+    out = []
+    for name, clip, tol in (("pixel batch 256 (m,n~U[256,2048], r~U[8,128]), clipped [0,255], tol 1e-3 rel", True, 1e-3),
+                            ("pixel batch 256, unclipped (no noise tail from clipping), tol 1e-3 rel", False, 1e-3)):
+        w = W.pixel_batch(clip=clip, tol=tol)
+        sets = {"plain_f64": ([torch.from_numpy(np.asfortranarray(a.astype(np.float64))).cuda() for a in w.A], "plain"),
+                "mixed_bf16": ([torch.from_numpy(a).cuda() for a in w.A], "mixed")}
+        res = {}
+        ranks = {}
+        rels = {}
+        for form, (mats, prec) in sets.items():
+            for _ in range(warmup):
+                r, st = eod.factor_batched(mats, tol, w.seed, block_k=32, tol_mode="rel", precision=prec)
+                del r
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                r, st = eod.factor_batched(mats, tol, w.seed, block_k=32, tol_mode="rel", precision=prec)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / steps
+            ranks[form] = [x.rank for x in r]
+            rels[form] = [x.rel_err for x in r]
+            flops = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, 32, True) for a, x in zip(w.A, r))
+            res[form] = {"fact_per_s": len(mats) / dt, "ms_per_batch": dt * 1e3, "gflops": flops / dt / 1e9,
+                         "statuses_ok": all(x == 0 for x in st),
+                         "rank_mean": float(np.mean(ranks[form])), "rank_max": int(np.max(ranks[form]))}
+            del r
+        eq = sum(a == b for a, b in zip(ranks["mixed_bf16"], ranks["plain_f64"]))
+        drel = max(abs(a - b) for a, b in zip(rels["mixed_bf16"], rels["plain_f64"]))
+        out.append({"workload": name, "forms": res, "mixed_rank_equal_f64": f"{eq}/{len(ranks['plain_f64'])}",
+                    "mixed_max_d_rel_err_vs_f64": drel,
+                    "mixed_speedup_vs_f64": res["mixed_bf16"]["fact_per_s"] / res["plain_f64"]["fact_per_s"]})
+        del sets
+        torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------- reference arm --

@@ -48,8 +48,10 @@ typedef enum {
     EOD_ENONFINITE = 4,    /* A holds a NaN or an infinity */
     EOD_ETIMEOUT = 5,      /* a bounded device-side wait gave up (kernel returned
                               an error flag instead of waiting forever) */
-    EOD_EPRECISION = 6,    /* a Cholesky factorisation broke down beyond the
-                              shifted fallback's reach */
+    EOD_EPRECISION = 6,    /* eps is below what FP32 data can resolve
+                              (eps < 1e-5 ||A||_F with EOD_F32 storage or on
+                              the mixed path), or a Cholesky factorisation
+                              broke down beyond the shifted fallback's reach */
     EOD_EUNSUPPORTED = 7   /* valid request this build does not support */
 } eod_status;
 
@@ -60,8 +62,9 @@ typedef enum {
                               (FP64 DFMA for EOD_F64, FP32 FFMA for EOD_F32);
                               Gram/Cholesky/rank test/core in FP64 */
     EOD_MIXED_BF16 = 1     /* sketch, projection and reconstruction on tcgen05
-                              tensor cores with A split as A_hi + A_lo (BF16,
-                              round to nearest even) and FP32 accumulation;
+                              tensor cores with FP32 accumulation: A split into
+                              three BF16 terms for the sketch (exact for FP32
+                              data), two for the projection and the error;
                               Gram/Cholesky/rank test/core in FP64 */
 } eod_precision;
 

@@ -65,6 +65,10 @@ struct HostMirror {
     ~HostMirror() { if (info) cudaFreeHost(info); }
 };
 
+// smallest eps / ||A||_F the FP32-data paths accept (see factor_impl)
+constexpr double kMixedFloor = 1e-5;
+constexpr double kF32Floor = 1e-5;
+
 template <typename T> struct Traits;
 template <> struct Traits<double> { static constexpr int dtype = EOD_F64; static constexpr double rho = 1e-10; };
 template <> struct Traits<float> { static constexpr int dtype = EOD_F32; static constexpr double rho = 1e-6; };
@@ -263,6 +267,13 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     }
     const double norm_a = hm.val[0];
     const double eps = (o.tol_mode == EOD_TOL_REL_FRO) ? tol * norm_a : tol;
+    // Below these thresholds the sketch's own rounding (FP32 accumulation,
+    // and the BF16 split on the mixed path) reaches the size of |T(l,l)|, so
+    // the rank test could not be decided: refuse instead of guessing.
+    if (std::is_same<T, float>::value && norm_a > 0.0) {
+        const double floor_rel = mixed ? kMixedFloor : kF32Floor;
+        if (eps < floor_rel * norm_a) return EOD_EPRECISION;
+    }
     F->norm_a = norm_a;
     F->eps = eps;
     F->block_k = k;

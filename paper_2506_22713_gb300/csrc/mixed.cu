@@ -10,9 +10,11 @@
 //  * projection (Alg. 2 step 8): C^T = A^T Q.
 //  * reconstruction error (Sec. 4.1): sum (A - Q C)^2, never storing Q C.
 //
-// A is split once into BF16 A_hi + A_lo; Q and C are split before their
-// products.  Deflation, CholQR, the rank test and the core stay on the FP32
-// SIMT / FP64 kernels of the plain path.
+// A is split once into BF16 A_hi + A_lo + A_3 (exact for FP32 data; the
+// sketch uses all three terms, the projection and the error the first two);
+// Q and C are split into two terms before their products.  Deflation,
+// CholQR, the rank test and the core stay on the FP32 SIMT / FP64 kernels of
+// the plain path.
 #include "common.cuh"
 #include "instrument.cuh"
 #include "tc_gemm.cuh"
@@ -54,9 +56,10 @@ eod_status MixedOps<float>::prepare(const float *A_, int64_t m_, int64_t n_, int
     ldn8 = round_up(n, 8);
     MX_ST(ar->get(&Ahi, (size_t)ldm8 * n));
     MX_ST(ar->get(&Alo, (size_t)ldm8 * n));
+    MX_ST(ar->get(&A3, (size_t)ldm8 * n));
     MX_ST(ar->get(&err_flag, 1));
     MX_TRY(cudaMemsetAsync(err_flag, 0, sizeof(int), s));
-    MX_TRY(split_norm(A, m, n, lda, Ahi, Alo, ldm8, nullptr, nullptr, stream_blocks(m * n), s));
+    MX_TRY(split_norm(A, m, n, lda, Ahi, Alo, ldm8, nullptr, nullptr, stream_blocks(m * n), s, A3));
     win_cap = std::min<int64_t>(cap, 1024);
     next_w = std::min<int64_t>(std::max<int64_t>(2 * k, 64), win_cap);
     MX_ST(ar->get(&Yw, (size_t)m * win_cap));
@@ -77,11 +80,13 @@ eod_status MixedOps<float>::sketch(int64_t col0, int64_t f, uint64_t seed, uint6
         g.N = w;
         g.K = n;
         g.a_mn_major = true;
-        g.npairs = 2;
+        g.npairs = 3;
         g.a[0] = {Ahi, m, n, ldm8};
         g.a[1] = {Alo, m, n, ldm8};
+        g.a[2] = {A3, m, n, ldm8};
         g.b[0] = {Om, n, w, ldn8};
         g.b[1] = g.b[0];
+        g.b[2] = g.b[0];
         g.D = Yw;
         g.ldd = m;
         g.err_flag = err_flag;
@@ -183,20 +188,23 @@ extern "C" eod_status eod_abe_debug_tc_gemm(int32_t form, int64_t M, int64_t N, 
         // D (M x N) = split(X) * bf16(Y): X is M x K (ld ldx), Y is K x N with BF16-exact values
         if (!D || ldx < M || ldy < K || ldd < M) return EOD_EINVAL;
         const int64_t lm = round_up(M, 8), lk = round_up(K, 8);
-        __nv_bfloat16 *xh, *xl, *yh, *yl;
+        __nv_bfloat16 *xh, *xl, *x3, *yh, *yl;
         MX_ST(ar.get(&xh, (size_t)lm * K));
         MX_ST(ar.get(&xl, (size_t)lm * K));
+        MX_ST(ar.get(&x3, (size_t)lm * K));
         MX_ST(ar.get(&yh, (size_t)lk * N));
         MX_ST(ar.get(&yl, (size_t)lk * N));
-        MX_TRY(split_norm(X, M, K, ldx, xh, xl, lm, nullptr, nullptr, 1024, s));
+        MX_TRY(split_norm(X, M, K, ldx, xh, xl, lm, nullptr, nullptr, 1024, s, x3));
         MX_TRY(split_norm(Y, K, N, ldy, yh, yl, lk, nullptr, nullptr, 1024, s));
         g.M = M; g.N = N; g.K = K;
         g.a_mn_major = true;
-        g.npairs = 2;
+        g.npairs = 3;
         g.a[0] = {xh, M, K, lm};
         g.a[1] = {xl, M, K, lm};
+        g.a[2] = {x3, M, K, lm};
         g.b[0] = {yh, K, N, lk};
         g.b[1] = g.b[0];
+        g.b[2] = g.b[0];
         g.D = D;
         g.ldd = ldd;
     } else if (form == 1) {

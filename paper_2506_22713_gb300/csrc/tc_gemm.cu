@@ -1,15 +1,16 @@
 // Tensor-core contractions of the mixed path on sm_103a: tcgen05.mma
 // (kind::f16, BF16 operands, FP32 accumulation in TMEM) fed by TMA.
 //
-//   sketch          Y   = (A_hi + A_lo) Omega         Alg. 1 step 4
+//   sketch          Y   = (A_hi + A_lo + A_3) Omega   Alg. 1 step 4
 //   projection      C^T = A_hi^T Q_hi + A_hi^T Q_lo + A_lo^T Q_hi    Alg. 2 step 8
 //   reconstruction  sum (A - Q C)^2 over a tile       Sec. 4.1 RelErr, with
 //                   Q C = Q_hi C_hi + Q_hi C_lo + Q_lo C_hi
 //
 // A FP32 matrix X is split as X_hi = bf16(X), X_lo = bf16(X - X_hi) (round
 // to nearest even); the dropped X_lo Y_lo term and the split's own residual
-// are about 2^-16 relative.  Omega is BF16-exact, so the sketch needs two
-// products only.
+// are about 2^-16 relative.  For the sketch A gets a third term A_3 =
+// bf16(A - A_hi - A_lo), which makes the split exact for FP32 data; Omega is
+// BF16-exact, so the sketch is then as accurate as an FP32 GEMM.
 //
 // One CTA computes a 128 x BN tile of D.  Warp 0 issues TMA loads into a
 // ring of shared-memory stages (128-byte swizzle), warp 1 allocates TMEM and
@@ -323,11 +324,13 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// X (rows x cols, ldx, FP32) -> X_hi, X_lo (same shape, ld ldo), with the
-// Frobenius partial sums and the non-finite flag of X (the S0 pass).
+// X (rows x cols, ldx, FP32) -> X_hi, X_lo (same shape, ld ldo) and, when
+// x3 != nullptr, X_3 = bf16(X - X_hi - X_lo), so that X_hi + X_lo + X_3 == X
+// exactly for normal FP32 values (three 8-bit significands); with partials
+// != nullptr also the S0 sums of squares and non-finite flags per block.
 __global__ void split_norm_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
-                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo, int64_t ldo,
-                                  double *partials, int *flags) {
+                                  __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+                                  __nv_bfloat16 *__restrict__ x3, int64_t ldo, double *partials, int *flags) {
     __shared__ double red[32];
     double acc = 0.0;
     int bad = 0;
@@ -341,6 +344,7 @@ __global__ void split_norm_kernel(const float *__restrict__ X, int64_t rows, int
         split_bf16(x, h, l);
         hi[i + j * ldo] = h;
         lo[i + j * ldo] = l;
+        if (x3) x3[i + j * ldo] = __float2bfloat16_rn((x - __bfloat162float(h)) - __bfloat162float(l));
     }
     if (partials) {
         const double tot = block_sum(acc, red);
@@ -510,10 +514,11 @@ int64_t tc_gemm_err_ctas(int64_t M, int64_t N, int bn) {
 }
 
 cudaError_t split_norm(const float *X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16 *hi,
-                       __nv_bfloat16 *lo, int64_t ldo, double *partials, int *flags, int blocks, cudaStream_t s) {
-    ProfScope prof(PROF_STREAM, 2.0 * rows * cols, 8.0 * rows * cols, s);
+                       __nv_bfloat16 *lo, int64_t ldo, double *partials, int *flags, int blocks, cudaStream_t s,
+                       __nv_bfloat16 *x3) {
+    ProfScope prof(PROF_STREAM, 2.0 * rows * cols, (x3 ? 10.0 : 8.0) * rows * cols, s);
     count_launch();
-    tc::split_norm_kernel<<<blocks, 512, 0, s>>>(X, rows, cols, ldx, hi, lo, ldo, partials, flags);
+    tc::split_norm_kernel<<<blocks, 512, 0, s>>>(X, rows, cols, ldx, hi, lo, x3, ldo, partials, flags);
     return cudaGetLastError();
 }
 

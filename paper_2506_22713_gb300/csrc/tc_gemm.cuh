@@ -39,11 +39,13 @@ struct TcGemmDesc {
 cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s);
 int64_t tc_gemm_err_ctas(int64_t M, int64_t N, int bn);
 
-// X (rows x cols, FP32) -> X_hi = bf16(X), X_lo = bf16(X - X_hi), same
-// layout with ld ldo; with partials != nullptr also the S0 sums of squares
-// and non-finite flags per block (blocks entries each).
+// X (rows x cols, FP32) -> X_hi = bf16(X), X_lo = bf16(X - X_hi) and, when
+// x3 is given, X_3 = bf16(X - X_hi - X_lo) (then X_hi + X_lo + X_3 == X),
+// same layout with ld ldo; with partials != nullptr also the S0 sums of
+// squares and non-finite flags per block (blocks entries each).
 cudaError_t split_norm(const float *X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16 *hi,
-                       __nv_bfloat16 *lo, int64_t ldo, double *partials, int *flags, int blocks, cudaStream_t s);
+                       __nv_bfloat16 *lo, int64_t ldo, double *partials, int *flags, int blocks, cudaStream_t s,
+                       __nv_bfloat16 *x3 = nullptr);
 // Xt_hi / Xt_lo (cols x rows, ld ldt) = split of X^T.
 cudaError_t split_transpose(const float *X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16 *hi,
                             __nv_bfloat16 *lo, int64_t ldt, cudaStream_t s);
@@ -72,7 +74,7 @@ struct MixedOps<float> {
     Scratch *ws = nullptr;
     const float *A = nullptr;
     int64_t m = 0, n = 0, lda = 0, cap = 0, k = 0, ldm8 = 0, ldn8 = 0;
-    __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr;
+    __nv_bfloat16 *Ahi = nullptr, *Alo = nullptr, *A3 = nullptr;
     // sketch window: Yw holds A Omega for global columns win_c0 .. win_c0 + win_w - 1
     float *Yw = nullptr;
     __nv_bfloat16 *Om = nullptr;
