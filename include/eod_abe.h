@@ -203,7 +203,8 @@ EOD_API void eod_abe_debug_fail_alloc_after(int32_t n);
  * eod_abe_debug_profile(1) clears and starts CUDA-event timing of every
  * kernel launch, grouped by kind: 0 SIMT GEMM, 1 one-CTA Cholesky / rank
  * test, 2 Omega generation, 3 streaming (norms, copies, splitting),
- * 4 tcgen05 tensor-core GEMM; eod_abe_debug_profile(0) stops it and clears.
+ * 4 tcgen05 tensor-core GEMM (mixed path), 5 FP64 GEMM emulated on tcgen05
+ * (plain FP64 path); eod_abe_debug_profile(0) stops it and clears.
  * eod_abe_debug_profile_read() waits for the recorded events of one kind and
  * returns the launch count, the summed device time (ms) and the summed
  * algorithmic flops and bytes of those launches; EOD_EINVAL for an unknown
@@ -261,6 +262,17 @@ EOD_API eod_status eod_abe_debug_tc_gemm(int32_t form, int64_t M, int64_t N, int
  * EOD_EUNSUPPORTED for a device ordinal of 64 or more. */
 EOD_API eod_status eod_abe_fro_norm_noalloc(const void *A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
                                             double *norm_out, int32_t *nonfinite_out, void *stream);
+
+/* Test hook (no counterpart in the paper): one FP64 GEMM C = alpha op(A)
+ * op(B) + beta C on device matrices, column-major, op(X) = X^T when the
+ * matching flag is nonzero; mode 0 runs the SIMT DFMA kernel, mode 1 the FP64
+ * emulation on tcgen05 tensor cores that the plain FP64 path uses for large
+ * products (exact BF16 slices, FP64 accumulation).  Returns after
+ * synchronising `stream`; EOD_EINVAL for bad sizes or leading dimensions,
+ * EOD_ETIMEOUT if a bounded device wait ran out. */
+EOD_API eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,
+                                          double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
+                                          double beta, double *C, int64_t ldc, void *stream);
 
 /* Build identification (static string). */
 EOD_API const char *eod_abe_version(void);

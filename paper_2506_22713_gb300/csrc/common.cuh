@@ -85,6 +85,7 @@ template <typename T> __device__ __forceinline__ double to_f64(T x) { return (do
 struct Scratch {
     char *base = nullptr;
     size_t size = 0, used = 0, high = 0;
+    int *err_flag = nullptr;   // device flag set by a kernel whose bounded wait ran out
     void *take(size_t bytes) {
         size_t off = (used + 255) & ~size_t(255);
         if (off + bytes > size) return nullptr;
@@ -158,8 +159,35 @@ cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
                  const TA *A, int64_t lda, const TB *B, int64_t ldb, double beta, TC *C,
                  int64_t ldc, const GemmExtra &x, Scratch *ws, cudaStream_t s);
 
-// number of CTAs the EPI_ERR form of gemm() launches for an M x N output
+// most CTAs (partials) the EPI_ERR form of gemm() writes for an M x N output;
+// clear that many before the call (the emulated FP64 path writes fewer)
 int64_t gemm_err_ctas(int64_t M, int64_t N);
+
+// FP64 GEMM emulated on tcgen05 tensor cores (oz_gemm.cu); same contract as
+// gemm<double,...> except that the triangular / upper-only hints are ignored
+cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                    const double *B, int64_t ldb, double beta, double *C, int64_t ldc, const GemmExtra &x,
+                    int *err_flag, cudaStream_t s);
+// Pre-sliced operand of oz_gemm_ops: 8 BF16 slices of op(X) as rows x K
+// (K contiguous, leading dimension ldk, slices slice_stride elements apart)
+// with a per-row exponent array e, or e == nullptr and one fixed exponent.
+struct OzOperand {
+    const void *q = nullptr;   // __nv_bfloat16 slices
+    const int *e = nullptr;
+    int e_fixed = 0;
+    int64_t ldk = 0, slice_stride = 0;
+};
+cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64_t N, int64_t K, double alpha,
+                        double beta, double *C, int64_t ldc, const GemmExtra &x, int *err_flag, cudaStream_t s);
+// slices of op(X) (rows x K, X(r, k) at X[r*sr + k*sk]) into q (ld ldk, slices
+// slice_stride apart); per-row exponents into e, or the fixed exponent when e
+// is null (every |X| must then be below 2^fixed_e)
+cudaError_t oz_slice(const double *X, int64_t rows, int64_t K, int64_t sr, int64_t sk, void *q, int *e,
+                     int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s);
+constexpr int kOzSlices = 8;
+
+// whether gemm<double,...> sends an M x N x K product to oz_gemm
+bool fp64_use_emulated(int64_t M, int64_t N, int64_t K);
 
 // --------------------------------------------------------------------------
 // Streaming kernels

@@ -65,6 +65,8 @@ struct HostMirror {
     ~HostMirror() { if (info) cudaFreeHost(info); }
 };
 
+inline int64_t round_up8(int64_t x) { return (x + 7) / 8 * 8; }
+
 // smallest eps / ||A||_F the FP32-data paths accept (see factor_impl)
 constexpr double kMixedFloor = 1e-5;
 constexpr double kF32Floor = 1e-5;
@@ -218,6 +220,19 @@ struct Result {
     std::vector<double> tdiag;
 };
 
+// Slices kept for the plain FP64 path's tensor-core contractions: A in both
+// orientations (sliced once), the basis Q in both orientations (extended as
+// columns are appended: per-column exponents for Q^T, the fixed exponent 1
+// for Q, whose entries are at most 1 in magnitude), and a buffer for the
+// small operand of each product.
+struct OzCache {
+    bool on = false;
+    void *Arow = nullptr, *Acol = nullptr, *Qc = nullptr, *Qr = nullptr, *Bt = nullptr;
+    int *eArow = nullptr, *eAcol = nullptr, *eQc = nullptr, *eBt = nullptr;
+    int64_t m = 0, m8 = 0, n8 = 0, cap8 = 0, bt_elems = 0;
+    OzOperand arow() const { return {Arow, eArow, 0, n8, m * n8}; }
+};
+
 template <typename T>
 static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
                               const eod_opts &o, cudaStream_t s, Arena &ar, eod_factors *F) {
@@ -234,6 +249,8 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     const size_t ws_bytes = (size_t)48 << 20;
     EOD_TRY(ar.get((char **)&ws.base, ws_bytes));
     ws.size = ws_bytes;
+    EOD_TRY(ar.get(&ws.err_flag, 1));
+    EOD_CU(cudaMemsetAsync(ws.err_flag, 0, sizeof(int), s));
 
     T *Qb, *Om, *Y, *S, *T1, *RinvT;
     double *G, *R1, *R1i, *R2, *R2i, *tdiag_d, *dsc;
@@ -281,6 +298,44 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     MixedOps<T> mx;
     if (mixed) EOD_TRY(mx.prepare(A, m, n, lda, k, ar, &ws, s));
 
+    OzCache oz;
+    oz.on = std::is_same<T, double>::value && fp64_use_emulated(m, k, n);
+    if (oz.on) {
+        oz.m = m;
+        oz.m8 = round_up8(m);
+        oz.n8 = round_up8(n);
+        oz.cap8 = round_up8(cap);
+        oz.bt_elems = (int64_t)kOzSlices * k * std::max(oz.m8, std::max(oz.n8, oz.cap8));
+        EOD_TRY(ar.get((uint16_t **)&oz.Arow, (size_t)kOzSlices * m * oz.n8));
+        EOD_TRY(ar.get((uint16_t **)&oz.Acol, (size_t)kOzSlices * n * oz.m8));
+        EOD_TRY(ar.get((uint16_t **)&oz.Qc, (size_t)kOzSlices * cap * oz.m8));
+        EOD_TRY(ar.get((uint16_t **)&oz.Qr, (size_t)kOzSlices * m * oz.cap8));
+        EOD_TRY(ar.get((uint16_t **)&oz.Bt, (size_t)oz.bt_elems));
+        EOD_TRY(ar.get(&oz.eArow, (size_t)m));
+        EOD_TRY(ar.get(&oz.eAcol, (size_t)n));
+        EOD_TRY(ar.get(&oz.eQc, (size_t)cap));
+        EOD_TRY(ar.get(&oz.eBt, (size_t)std::max(m, n)));
+        const double *Ad = (const double *)A;
+        // op(A) = A: rows i, K = n;  op(A) = A^T: rows = columns of A, K = m
+        EOD_CU(oz_slice(Ad, m, n, 1, lda, oz.Arow, oz.eArow, 0, oz.n8, m * oz.n8, s));
+        EOD_CU(oz_slice(Ad, n, m, lda, 1, oz.Acol, oz.eAcol, 0, oz.m8, n * oz.m8, s));
+    }
+    // append columns c0 .. c0+cnt-1 of the basis to the sliced copies
+    auto oz_append = [&](int64_t c0, int64_t cnt) -> cudaError_t {
+        if (!oz.on || cnt <= 0) return cudaSuccess;
+        const double *Qd = (const double *)Qb;
+        cudaError_t e = oz_slice(Qd + c0 * m, cnt, m, m, 1, (uint16_t *)oz.Qc + c0 * oz.m8, oz.eQc + c0, 0, oz.m8,
+                                 cap * oz.m8, s);
+        if (e != cudaSuccess) return e;
+        return oz_slice(Qd + c0 * m, m, cnt, 1, m, (uint16_t *)oz.Qr + c0, nullptr, 1, oz.cap8, m * oz.cap8, s);
+    };
+    // slices of a small B operand (rows x K, X(r, k) at X[r*sr + k*sk]) into oz.Bt
+    auto oz_small = [&](const T *X, int64_t rows, int64_t K, int64_t sr, int64_t sk, OzOperand &out) -> cudaError_t {
+        const int64_t ldk = round_up8(K);
+        out = {oz.Bt, oz.eBt, 0, ldk, rows * ldk};
+        return oz_slice((const double *)X, rows, K, sr, sk, oz.Bt, oz.eBt, 0, ldk, rows * ldk, s);
+    };
+
     // ---- Alg. 1 ----
     const double eps2 = eps * eps;
     const double delta_coef = 64.0 * ((double)k + std::sqrt((double)m)) * kU64;
@@ -302,7 +357,13 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
             EOD_TRY(mx.sketch(kept, f, seed, o.batch_index, Y, m, s));
         } else {
             EOD_CU(omega_fill<T>(n, kept, f, seed, o.batch_index, Om, n, s));
-            EOD_CU((gemm<T, T, T, T>(false, false, m, f, n, 1.0, A, lda, Om, n, 0.0, Y, m, ex, &ws, s)));
+            if (oz.on) {
+                OzOperand bo;
+                EOD_CU(oz_small(Om, f, n, n, 1, bo));
+                EOD_CU(oz_gemm_ops(oz.arow(), bo, m, f, n, 1.0, 0.0, (double *)Y, m, ex, ws.err_flag, s));
+            } else {
+                EOD_CU((gemm<T, T, T, T>(false, false, m, f, n, 1.0, A, lda, Om, n, 0.0, Y, m, ex, &ws, s)));
+            }
         }
         int64_t cur = 0;
         while (!stop && cur < f) {
@@ -310,8 +371,22 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
             const int64_t wdt = f - cur;
             // step 4: Y <- (I - Q Q^T) Y, twice
             for (int pass = 0; pass < 2 && kept > 0; ++pass) {
-                EOD_CU((gemm<T, T, T, T>(true, false, kept, wdt, m, 1.0, Qb, m, Yc, m, 0.0, S, cap, ex, &ws, s)));
-                EOD_CU((gemm<T, T, T, T>(false, false, m, wdt, kept, -1.0, Qb, m, S, cap, 1.0, Yc, m, ex, &ws, s)));
+                if (oz.on && fp64_use_emulated(kept, wdt, m)) {
+                    OzOperand bo;
+                    EOD_CU(oz_small(Yc, wdt, m, m, 1, bo));
+                    const OzOperand qc{oz.Qc, oz.eQc, 0, oz.m8, cap * oz.m8};
+                    EOD_CU(oz_gemm_ops(qc, bo, kept, wdt, m, 1.0, 0.0, (double *)S, cap, ex, ws.err_flag, s));
+                } else {
+                    EOD_CU((gemm<T, T, T, T>(true, false, kept, wdt, m, 1.0, Qb, m, Yc, m, 0.0, S, cap, ex, &ws, s)));
+                }
+                if (oz.on && fp64_use_emulated(m, wdt, kept)) {
+                    OzOperand bo;
+                    EOD_CU(oz_small(S, wdt, kept, cap, 1, bo));
+                    const OzOperand qr{oz.Qr, nullptr, 1, oz.cap8, m * oz.cap8};
+                    EOD_CU(oz_gemm_ops(qr, bo, m, wdt, kept, -1.0, 1.0, (double *)Yc, m, ex, ws.err_flag, s));
+                } else {
+                    EOD_CU((gemm<T, T, T, T>(false, false, m, wdt, kept, -1.0, Qb, m, S, cap, 1.0, Yc, m, ex, &ws, s)));
+                }
             }
             // step 5 (pass 1) + steps 6-11: Gram, Cholesky with the rank test
             EOD_CU(gram_skinny<T>(Yc, m, (int)wdt, m, G, k, &ws, s));
@@ -342,6 +417,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 EOD_CU(cudaStreamSynchronize(s));
                 if (hm.info[0] != p || hm.info[1] != CHOL_ALL) return EOD_EPRECISION;
                 for (int j = 0; j < p; ++j) tdiag.push_back(td[j]);
+                EOD_CU(oz_append(kept, p));
                 kept += p;
             }
             if (code == CHOL_ALL) {
@@ -378,6 +454,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 } else {
                     EOD_CU(scale_column<T>(z, m, d_t, s));
                     EOD_CU((copy_matrix<T, T>(z, m, Qb + kept * m, m, m, 1, false, s)));
+                    EOD_CU(oz_append(kept, 1));
                     kept += 1;
                     cur += p + 1;
                 }
@@ -419,7 +496,13 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
         if (mixed) {
             EOD_TRY(mx.project(Qb, r, Ct, s));
         } else {
-            EOD_CU((gemm<T, T, T, T>(true, false, n, r, m, 1.0, A, lda, Qb, m, 0.0, Ct, n, ex, &ws, s)));
+            if (oz.on) {
+                const OzOperand acol{oz.Acol, oz.eAcol, 0, oz.m8, n * oz.m8};
+                const OzOperand qc{oz.Qc, oz.eQc, 0, oz.m8, cap * oz.m8};
+                EOD_CU(oz_gemm_ops(acol, qc, n, r, m, 1.0, 0.0, (double *)Ct, n, ex, ws.err_flag, s));
+            } else {
+                EOD_CU((gemm<T, T, T, T>(true, false, n, r, m, 1.0, A, lda, Qb, m, 0.0, Ct, n, ex, &ws, s)));
+            }
         }
     }
 
@@ -432,12 +515,26 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
             const int64_t nct = gemm_err_ctas(m, n);
             double *part;
             EOD_TRY(ar.get(&part, (size_t)nct));
+            EOD_CU(cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nct, s));
             GemmExtra ee;
             ee.epilogue = EPI_ERR;
             ee.ref = A;
             ee.ldref = lda;
             ee.err_partials = part;
-            EOD_CU((gemm<T, T, T, T>(false, true, m, n, r, 1.0, Qb, m, Ct, n, 0.0, (T *)nullptr, m, ee, &ws, s)));
+            if (oz.on && fp64_use_emulated(m, n, r)) {
+                // B operand (C^T)^T: rows = rows of C^T (n), K = r
+                const int64_t r8 = round_up8(r);
+                uint16_t *cts;
+                int *ects;
+                EOD_TRY(ar.get(&cts, (size_t)kOzSlices * n * r8));
+                EOD_TRY(ar.get(&ects, (size_t)n));
+                EOD_CU(oz_slice((const double *)Ct, n, r, 1, n, cts, ects, 0, r8, n * r8, s));
+                const OzOperand qr{oz.Qr, nullptr, 1, oz.cap8, m * oz.cap8};
+                const OzOperand cto{cts, ects, 0, r8, n * r8};
+                EOD_CU(oz_gemm_ops(qr, cto, m, n, r, 1.0, 0.0, nullptr, m, ee, ws.err_flag, s));
+            } else {
+                EOD_CU((gemm<T, T, T, T>(false, true, m, n, r, 1.0, Qb, m, Ct, n, 0.0, (T *)nullptr, m, ee, &ws, s)));
+            }
             EOD_CU(finalize_sqrt_sum(part, nct, d_norm, d_err, s));
         }
     }
@@ -459,7 +556,19 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(cholqr2(cw, V, n, n, r, Rc, hm, &ws, s));                 // C^T = V R
     EOD_CU((copy_matrix<double, T>(Rc, r, Rt, r, r, r, true, s)));    // R^T
     EOD_TRY(cholqr2(cw, Rt, r, r, r, D, hm, &ws, s));                 // R^T = Qh D
-    EOD_CU((gemm<T, T, T, T>(false, false, m, r, r, 1.0, Qb, m, Rt, r, 0.0, U, m, ex, &ws, s)));  // U = Q Qh
+    if (oz.on && fp64_use_emulated(m, r, r)) {   // U = Q Qh
+        const int64_t r8 = round_up8(r);
+        uint16_t *qhs;
+        int *eqh;
+        EOD_TRY(ar.get(&qhs, (size_t)kOzSlices * r * r8));
+        EOD_TRY(ar.get(&eqh, (size_t)r));
+        EOD_CU(oz_slice((const double *)Rt, r, r, r, 1, qhs, eqh, 0, r8, r * r8, s));
+        const OzOperand qr{oz.Qr, nullptr, 1, oz.cap8, m * oz.cap8};
+        const OzOperand qho{qhs, eqh, 0, r8, r * r8};
+        EOD_CU(oz_gemm_ops(qr, qho, m, r, r, 1.0, 0.0, (double *)U, m, ex, ws.err_flag, s));
+    } else {
+        EOD_CU((gemm<T, T, T, T>(false, false, m, r, r, 1.0, Qb, m, Rt, r, 0.0, U, m, ex, &ws, s)));
+    }
 
     if (o.compute_err) {
         EOD_CU(cudaMemcpyAsync(hm.val, d_err, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -467,6 +576,9 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_CU(cudaStreamSynchronize(s));
     F->rel_err = o.compute_err ? hm.val[0] : -1.0;
     if (mixed) EOD_TRY(mx.check(s));
+    EOD_CU(cudaMemcpyAsync(hm.flag, ws.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EOD_CU(cudaStreamSynchronize(s));
+    if (hm.flag[0]) return EOD_ETIMEOUT;
 
     F->U = U; ar.keep(U);
     F->V = V; ar.keep(V);

@@ -13,6 +13,11 @@
 #include "common.cuh"
 #include "instrument.cuh"
 
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <type_traits>
+
 namespace eod {
 namespace {
 
@@ -217,12 +222,31 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
 
 int64_t gemm_err_ctas(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N + BN - 1) / BN); }
 
+// Large FP64 products go to the tensor-core emulation (oz_gemm.cu) unless
+// EOD_FP64_GEMM=simt; products below 2^25 multiply-adds stay on the SIMT
+// kernel, whose launch and slicing overheads are smaller there.
+bool fp64_use_emulated(int64_t M, int64_t N, int64_t K) {
+    static const int mode = [] {
+        const char *v = std::getenv("EOD_FP64_GEMM");
+        if (v && std::strcmp(v, "simt") == 0) return 0;
+        if (v && std::strcmp(v, "emulated") == 0) return 2;
+        return 1;
+    }();
+    if (mode == 0) return false;
+    if (mode == 2) return M >= 1 && N >= 1 && K >= 1;
+    return (double)M * (double)N * (double)K >= 33554432.0 && M >= 128 && N >= 64 && K >= 128;
+}
+
 template <typename TA, typename TB, typename TC, typename Acc>
 cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const TA *A,
                  int64_t lda, const TB *B, int64_t ldb, double beta, TC *C, int64_t ldc,
                  const GemmExtra &x, Scratch *ws, cudaStream_t s)
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
+    if (std::is_same<TA, double>::value && std::is_same<TB, double>::value && std::is_same<TC, double>::value &&
+        ws && ws->err_flag && K > 0 && fp64_use_emulated(M, N, K))
+        return oz_gemm(ta, tb, M, N, K, alpha, (const double *)A, lda, (const double *)B, ldb, beta, (double *)C,
+                       ldc, x, ws->err_flag, s);
     if (!ta && !tb) return launch<TA, TB, TC, Acc, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
     if (ta && !tb) return launch<TA, TB, TC, Acc, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
     if (!ta && tb) return launch<TA, TB, TC, Acc, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
@@ -240,3 +264,42 @@ template cudaError_t gemm<float, float, double, double>(bool, bool, int64_t, int
     Scratch *, cudaStream_t);
 
 }  // namespace eod
+
+// ---------------------------------------------------------------------------
+// Test hook: one FP64 GEMM through the SIMT kernel (mode 0) or the tensor-core
+// emulation (mode 1), C = alpha op(A) op(B) + beta C, device pointers.
+// ---------------------------------------------------------------------------
+extern "C" eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,
+                                             double alpha, const double *A, int64_t lda, const double *B,
+                                             int64_t ldb, double beta, double *C, int64_t ldc, void *stream) {
+    using namespace eod;
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || ldc < M) return EOD_EINVAL;
+    if (lda < (ta ? K : M) || ldb < (tb ? N : K)) return EOD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    GemmExtra x;
+    cudaError_t e;
+    if (mode == 1) {
+        int *flag = nullptr;
+        if (cudaMallocAsync((void **)&flag, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
+        cudaMemsetAsync(flag, 0, sizeof(int), s);
+        e = oz_gemm(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, flag, s);
+        int h = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(flag, s);
+        if (e != cudaSuccess) {
+            std::fprintf(stderr, "eod_abe_debug_f64_gemm: %s\n", cudaGetErrorString(e));
+            cudaGetLastError();
+            return EOD_ECUDA;
+        }
+        return h ? EOD_ETIMEOUT : EOD_OK;
+    }
+    Scratch ws;
+    if (cudaMallocAsync((void **)&ws.base, (size_t)48 << 20, s) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
+    ws.size = (size_t)48 << 20;
+    e = gemm<double, double, double, double>(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, &ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(ws.base, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
+    return EOD_OK;
+}

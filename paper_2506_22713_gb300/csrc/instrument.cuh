@@ -12,7 +12,8 @@ enum ProfKind {
     PROF_OMEGA = 2,       // Gaussian test blocks
     PROF_STREAM = 3,      // norms, copies, scaling, splitting
     PROF_TC_GEMM = 4,     // tcgen05 tensor-core contractions (mixed path)
-    PROF_KINDS = 5
+    PROF_OZ_GEMM = 5,     // FP64 contractions emulated on tcgen05 (plain FP64 path)
+    PROF_KINDS = 6
 };
 
 void count_launch(int n = 1);

@@ -1,0 +1,503 @@
+// FP64 GEMM emulated on tcgen05 BF16 tensor cores (exact slicing in the
+// manner of Ozaki, Ogita and Oishi's error-free splitting), used by the plain
+// FP64 path for its large contractions.
+//
+// Each row i of op(A) (and each column j of op(B)) is scaled by a power of
+// two 2^-e so that its entries lie in (-1, 1), then cut into S = 8 integer
+// slices (exact BF16 values): q_0 in [-64, 64] (6 bits + rounding), q_1..q_7
+// in [-64, 64] (7 bits each):
+//     a = 2^e * sum_s q_s 2^(-6 - 7s),   truncation below 2^(e-56).
+// Products of slices are integers of magnitude <= 2^12.  Pairs (s, t) with
+// s + t <= 7 are grouped by g = s + t (weight 2^(-12 - 7g)); group g holds
+// g + 1 <= 8 pairs, so over a K chunk of 448 every group sum stays below
+// 8 * 448 * 2^12 < 2^24 and the tensor core's FP32 accumulation is exact.
+// After each chunk the epilogue warps read the eight group sums from TMEM as
+// integers, merge groups 0-3 and 4-7 exactly in int64 (each below 2^46), and
+// add the two merged values, scaled, into FP64 registers.  The dropped pairs
+// (s + t > 7) weigh at most 2^-68 of the row / column scales.  The result
+// equals an FP64 GEMM to within the slicing truncation (about 2^-56 of the
+// row / column maxima per term), accumulated in FP64.
+//
+// CTA tile 128 x 64; a K block of 64 stages all eight B slices (64 KB) and
+// streams the eight A slices through a 4-deep ring; TMEM holds 8 x 64 FP32
+// group accumulators (all 512 columns).  Warp 0: TMA producer, warp 1: MMA
+// issuer, warps 2-9: drain and epilogue (two per TMEM lane quarter, 32
+// columns each).  All waits are bounded (EOD_ETIMEOUT
+// on expiry).
+#include "common.cuh"
+#include "instrument.cuh"
+#include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace eod {
+namespace oz {
+
+using namespace eod::tc;
+
+constexpr int NS = kOzSlices;         // slices per operand (8)
+constexpr int NG = 8;                 // weight groups g = s + t, pairs with s + t <= 7
+constexpr int BM = 128, BN = 64, BK = 64;
+constexpr int KCH = 7;                // K blocks per exact chunk (448)
+constexpr int UMMA_K = 16;            // K per tcgen05.mma kind::f16
+constexpr int ASTAGES = 4, BSTAGES = 2;
+constexpr int A_TILE = BM * BK * 2;   // 16 KB
+constexpr int B_TILE = BN * BK * 2;   // 8 KB
+constexpr int B_SET = NS * B_TILE;    // 64 KB
+constexpr int SMEM = BSTAGES * B_SET + ASTAGES * A_TILE + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 512;   // 8 x 64 used
+constexpr int NTHREADS = 320;        // producer, MMA issuer, 8 drain warps
+constexpr int ECOLS = BN / 2;         // columns per drain warp
+
+struct Maps {
+    CUtensorMap a[NS];
+    CUtensorMap b[NS];
+};
+
+struct Params {
+    int64_t M, N;
+    int64_t kblocks, kb_per_split;
+    const int *ea, *eb;       // row exponents of op(A), column exponents of op(B) (or null:
+    int ea_fixed, eb_fixed;   // then every row / column uses the fixed exponent)
+    double alpha, beta;
+    double *C;                // output (or split partials when split_stride > 0)
+    int64_t ldc, split_stride;
+    const double *R;          // EPI_ERR reference
+    int64_t ldr;
+    double *errp;
+    int *err_flag;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_constant__ Maps maps, Params p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *bbuf = smem;                                 // BSTAGES x 7 B slices
+    uint8_t *abuf = smem + BSTAGES * B_SET;                // ASTAGES A slices
+    uint64_t *fullB = (uint64_t *)(abuf + ASTAGES * A_TILE);
+    uint64_t *emptyB = fullB + BSTAGES;
+    uint64_t *fullA = emptyB + BSTAGES;
+    uint64_t *emptyA = fullA + ASTAGES;
+    uint64_t *tmem_full = emptyA + ASTAGES;
+    uint64_t *tmem_empty = tmem_full + 1;
+    uint32_t *tmem_slot = (uint32_t *)(tmem_empty + 1);
+    int *abort_sh = (int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    const int64_t kb0 = (int64_t)blockIdx.z * p.kb_per_split;
+    int64_t kb1 = kb0 + p.kb_per_split;
+    if (kb1 > p.kblocks) kb1 = p.kblocks;
+    const int64_t nkb = kb1 > kb0 ? kb1 - kb0 : 0;
+    const int64_t nchunks = (nkb + KCH - 1) / KCH;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < BSTAGES; ++i) { mbar_init(&fullB[i], 1); mbar_init(&emptyB[i], 1); }
+        for (int i = 0; i < ASTAGES; ++i) { mbar_init(&fullA[i], 1); mbar_init(&emptyA[i], 1); }
+        mbar_init(tmem_full, 1);
+        mbar_init(tmem_empty, 256);
+        *abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        int64_t ib = 0, ia = 0;
+        bool ok = true;
+        for (int64_t kb = kb0; kb < kb1 && ok; ++kb) {
+            const int sb = (int)(ib % BSTAGES);
+            if (ib >= BSTAGES && !mbar_wait(&emptyB[sb], (uint32_t)((ib / BSTAGES - 1) & 1))) { ok = false; break; }
+            if (*(volatile int *)abort_sh) { ok = false; break; }
+            mbar_expect_tx(&fullB[sb], B_SET);
+            for (int t = 0; t < NS; ++t)
+                tma_load_2d(bbuf + sb * B_SET + t * B_TILE, &maps.b[t], &fullB[sb], (int)(kb * BK), (int)n0);
+            ++ib;
+            for (int s = 0; s < NS; ++s) {
+                const int sa = (int)(ia % ASTAGES);
+                if (ia >= ASTAGES && !mbar_wait(&emptyA[sa], (uint32_t)((ia / ASTAGES - 1) & 1))) { ok = false; break; }
+                mbar_expect_tx(&fullA[sa], A_TILE);
+                tma_load_2d(abuf + sa * A_TILE, &maps.a[s], &fullA[sa], (int)(kb * BK), (int)m0);
+                ++ia;
+            }
+        }
+        if (!ok) { atomicExch(p.err_flag, 1); *abort_sh = 1; }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        constexpr uint32_t idesc = idesc_bf16(BM, BN, false, false);
+        int64_t ib = 0, ia = 0;
+        bool ok = true;
+        bool init[NG];
+        for (int64_t q = 0; q < nkb && ok; ++q) {
+            if (q % KCH == 0) {
+                const int64_t chunk = q / KCH;
+                if (chunk > 0 && !mbar_wait(tmem_empty, (uint32_t)((chunk - 1) & 1))) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int g = 0; g < NG; ++g) init[g] = false;
+            }
+            const int sb = (int)(ib % BSTAGES);
+            if (!mbar_wait(&fullB[sb], (uint32_t)((ib / BSTAGES) & 1))) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t bbase = smem_u32(bbuf + sb * B_SET);
+            for (int s = 0; s < NS; ++s) {
+                const int sa = (int)(ia % ASTAGES);
+                if (!mbar_wait(&fullA[sa], (uint32_t)((ia / ASTAGES) & 1))) { ok = false; break; }
+                if (*(volatile int *)abort_sh) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t abase = smem_u32(abuf + sa * A_TILE);
+                for (int t = 0; t + s < NG; ++t) {
+                    const int g = s + t;
+#pragma unroll
+                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                        const uint64_t ad = sdesc(abase + kk * (UMMA_K * 2), 16, 1024);
+                        const uint64_t bd = sdesc(bbase + t * B_TILE + kk * (UMMA_K * 2), 16, 1024);
+                        umma_bf16(tmem + (uint32_t)(g * BN), ad, bd, idesc, (init[g] || kk > 0) ? 1u : 0u);
+                    }
+                    init[g] = true;
+                }
+                umma_commit(&emptyA[sa]);
+                ++ia;
+            }
+            if (!ok) break;
+            umma_commit(&emptyB[sb]);
+            ++ib;
+            if (q % KCH == KCH - 1 || q == nkb - 1) umma_commit(tmem_full);
+        }
+        if (!ok) {
+            atomicExch(p.err_flag, 1);
+            *abort_sh = 1;
+            umma_commit(tmem_full);   // release the epilogue once the MMAs already issued finish
+        }
+    } else if (warp >= 2) {
+        // ---------------- drain + epilogue ----------------
+        const int qtr = warp & 3;                 // TMEM lane quarter this warp may read
+        const int c0 = ((warp - 2) >> 2) * ECOLS; // its half of the 64 columns
+        const int64_t row = m0 + 32 * qtr + lane;
+        double acc[ECOLS];
+#pragma unroll
+        for (int j = 0; j < ECOLS; ++j) acc[j] = 0.0;
+        bool ok = true;
+        // weights of the merged groups 0-3 and 4-7: 2^(-12 - 7*3), 2^(-12 - 7*7)
+        const double w_hi = __longlong_as_double((long long)(1023 - 33) << 52);
+        const double w_lo = __longlong_as_double((long long)(1023 - 61) << 52);
+        for (int64_t c = 0; c < nchunks; ++c) {
+            ok = __all_sync(0xffffffffu, mbar_wait(tmem_full, (uint32_t)(c & 1)) ? 1 : 0) != 0;
+            if (!ok || *(volatile int *)abort_sh) { ok = false; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int cc = 0; cc < ECOLS; cc += 8) {
+                long long hi[8], lo[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    float v[8];
+                    tmem_ld8(tmem + ((uint32_t)(32 * qtr) << 16) + (uint32_t)(g * BN + c0 + cc), v);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const long long iv = (long long)__float2int_rn(v[j]);   // exact: |v| <= 2^24
+                        if (g < 4) hi[j] = hi[j] * 128 + iv;
+                        else lo[j] = lo[j] * 128 + iv;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    acc[cc + j] = fma((double)lo[j], w_lo, fma((double)hi[j], w_hi, acc[cc + j]));
+            }
+            tc_fence_before();
+            mbar_arrive(tmem_empty);
+        }
+        if (!ok) atomicExch(p.err_flag, 1);
+        double local = 0.0;
+        if (row < p.M) {
+            const int ei = p.ea ? max(p.ea[row], -1100) : p.ea_fixed;
+#pragma unroll
+            for (int j = 0; j < ECOLS; ++j) {
+                const int64_t col = n0 + c0 + j;
+                if (col < p.N) {
+                    const double val = ldexp(acc[j], ei + (p.eb ? max(p.eb[col], -1100) : p.eb_fixed));
+                    if (EPI == EPI_STORE) {
+                        if (p.split_stride > 0) {
+                            p.C[(int64_t)blockIdx.z * p.split_stride + row + col * p.M] = val;
+                        } else {
+                            double out = p.alpha * val;
+                            if (p.beta != 0.0) out = fma(p.beta, p.C[row + col * p.ldc], out);
+                            p.C[row + col * p.ldc] = out;
+                        }
+                    } else {
+                        const double d = p.R[row + col * p.ldr] - p.alpha * val;
+                        local = fma(d, d, local);
+                    }
+                }
+            }
+        }
+        if (EPI == EPI_ERR) {
+            local = warp_sum(local);
+            __shared__ double red[8];
+            if (lane == 0) red[warp - 2] = local;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (warp == 2 && lane == 0) {
+                double t = 0.0;
+                for (int i = 0; i < 8; ++i) t += red[i];
+                p.errp[blockIdx.x + (int64_t)blockIdx.y * gridDim.x] = t;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// e[r] = exponent of max_k |X(r, k)| (frexp convention: max < 2^e), by
+// atomicMax over blocks that each cover 32 rows x a K range; rows that stay
+// all zero keep the sentinel value (< -1100) the caller stored.
+__global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+                              int64_t kper, int *e) {
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int64_t kb = (int64_t)blockIdx.y * kper;
+    int64_t ke = kb + kper;
+    if (ke > K) ke = K;
+    double mx = 0.0;
+    if (sk == 1) {
+        // K contiguous: lanes along k, warps over rows
+        for (int rr = ty; rr < 32; rr += 8) {
+            const int64_t r = r0 + rr;
+            double m = 0.0;
+            if (r < R)
+                for (int64_t k = kb + tx; k < ke; k += 32) m = fmax(m, fabs(X[r * sr + k]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (tx == 0 && r < R && m > 0.0) {
+                int ex;
+                frexp(m, &ex);
+                atomicMax(&e[r], ex);
+            }
+        }
+        return;
+    }
+    // rows contiguous: lanes along rows, warps split the K range
+    const int64_t r = r0 + tx;
+    if (r < R)
+        for (int64_t k = kb + ty; k < ke; k += 8) mx = fmax(mx, fabs(X[r + k * sk]));
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && r < R) {
+        double m = red[0][tx];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) m = fmax(m, red[i][tx]);
+        if (m > 0.0) {
+            int ex;
+            frexp(m, &ex);
+            atomicMax(&e[r], ex);
+        }
+    }
+}
+
+// out[s][r * ldk + k] = slice s of X(r, k) 2^-e[r]; 32 x 32 tiles through
+// shared memory so reads follow X's contiguous axis and writes follow k.
+__global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+                             const int *__restrict__ e, int fixed_e, __nv_bfloat16 *__restrict__ out, int64_t ldk,
+                             int64_t slice_stride) {
+    __shared__ double tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int i = ty; i < 32; i += 8) {
+        int64_t r, k;
+        if (sk == 1) { r = r0 + i; k = k0 + tx; } else { r = r0 + tx; k = k0 + i; }
+        const double v = (r < R && k < K) ? X[r * sr + k * sk] : 0.0;
+        if (sk == 1) tile[i][tx] = v; else tile[tx][i] = v;   // tile[r - r0][k - k0]
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int64_t r = r0 + i, k = k0 + tx;
+        if (r >= R || k >= K) continue;
+        const int er = e ? e[r] : fixed_e;
+        double t = er < -1100 ? 0.0 : ldexp(tile[i][tx], -er) * 64.0;   // exact: |t| < 64
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double q = rint(t);                   // integer in [-64, 64]
+            out[s * slice_stride + r * ldk + k] = __double2bfloat16(q);
+            t = (t - q) * 128.0;                        // exact, |t| <= 64
+        }
+    }
+}
+
+__global__ void split_sum_kernel(const double *__restrict__ part, int S, int64_t M, int64_t N, double alpha,
+                                 double beta, double *C, int64_t ldc) {
+    const int64_t total = M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int z = 0; z < S; ++z) sum += part[(int64_t)z * total + e];
+        const int64_t i = e % M, j = e / M;
+        double out = alpha * sum;
+        if (beta != 0.0) out = fma(beta, C[i + j * ldc], out);
+        C[i + j * ldc] = out;
+    }
+}
+
+struct Slices {
+    __nv_bfloat16 *q = nullptr;
+    int *e = nullptr;
+    int64_t R = 0, ldk = 0;
+};
+
+cudaError_t slice_into(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, __nv_bfloat16 *q, int *e,
+                       int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s) {
+    if (R <= 0 || K <= 0) return cudaSuccess;
+    if (e) {
+        count_launch();
+        // every exponent starts at a large negative sentinel (bytes 0x80)
+        EOD_CUDA_TRY(cudaMemsetAsync(e, 0x80, sizeof(int) * (size_t)R, s));
+        const int64_t rblocks = (R + 31) / 32;
+        int64_t ksplit = (4 * kNumSMs + rblocks - 1) / rblocks;
+        const int64_t kmax = (K + 255) / 256;
+        if (ksplit > kmax) ksplit = kmax;
+        if (ksplit < 1) ksplit = 1;
+        const int64_t kper = (K + ksplit - 1) / ksplit;
+        rowexp_kernel<<<dim3((unsigned)rblocks, (unsigned)ksplit), 256, 0, s>>>(X, R, K, sr, sk, kper, e);
+        EOD_CUDA_TRY(cudaGetLastError());
+    }
+    count_launch();
+    dim3 grid((unsigned)((K + 31) / 32), (unsigned)((R + 31) / 32));
+    slice_kernel<<<grid, dim3(32, 8), 0, s>>>(X, R, K, sr, sk, e, fixed_e, q, ldk, slice_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t make_slices(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, Slices &sl, cudaStream_t s) {
+    sl.R = R;
+    sl.ldk = round_up(K, 8);
+    EOD_CUDA_TRY(cudaMallocAsync((void **)&sl.q, sizeof(__nv_bfloat16) * (size_t)NS * R * sl.ldk, s));
+    EOD_CUDA_TRY(cudaMallocAsync((void **)&sl.e, sizeof(int) * (size_t)R, s));
+    return slice_into(X, R, K, sr, sk, sl.q, sl.e, 0, sl.ldk, R * sl.ldk, s);
+}
+
+void free_slices(Slices &sl, cudaStream_t s) {
+    if (sl.q) cudaFreeAsync(sl.q, s);
+    if (sl.e) cudaFreeAsync(sl.e, s);
+    sl.q = nullptr;
+    sl.e = nullptr;
+}
+
+}  // namespace oz
+
+// Slices of op(X) as `rows` x K with K contiguous (see oz_gemm.cu header).
+cudaError_t oz_slice(const double *X, int64_t rows, int64_t K, int64_t sr, int64_t sk, void *q, int *e,
+                     int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s) {
+    return oz::slice_into(X, rows, K, sr, sk, (__nv_bfloat16 *)q, e, fixed_e, ldk, slice_stride, s);
+}
+
+cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64_t N, int64_t K, double alpha,
+                        double beta, double *C, int64_t ldc, const GemmExtra &x, int *err_flag, cudaStream_t s) {
+    using namespace oz;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    Maps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    for (int i = 0; i < NS; ++i) {
+        const __nv_bfloat16 *qa = (const __nv_bfloat16 *)A.q, *qb = (const __nv_bfloat16 *)B.q;
+        if (!make_map(&maps.a[i], qa + (size_t)i * A.slice_stride, K, M, A.ldk, BK, BM) ||
+            !make_map(&maps.b[i], qb + (size_t)i * B.slice_stride, K, N, B.ldk, BK, BN))
+            return cudaErrorInvalidValue;
+    }
+    // exponents: a fixed exponent is passed as a one-entry array by the caller
+    Params p;
+    std::memset(&p, 0, sizeof(p));
+    p.M = M;
+    p.N = N;
+    p.kblocks = (K + BK - 1) / BK;
+    p.ea = A.e;
+    p.eb = B.e;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.err_flag = err_flag;
+    p.R = (const double *)x.ref;
+    p.ldr = x.ldref;
+    p.errp = x.err_partials;
+    p.ea_fixed = A.e_fixed;
+    p.eb_fixed = B.e_fixed;
+    const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    int64_t splits = 1;
+    if (x.epilogue == EPI_STORE && tiles < kNumSMs) {
+        splits = (kNumSMs + tiles - 1) / tiles;
+        const int64_t chunks = (p.kblocks + KCH - 1) / KCH;
+        if (splits > chunks) splits = chunks;
+        if (splits < 1) splits = 1;
+    }
+    const int64_t chunks_per = ((p.kblocks + KCH - 1) / KCH + splits - 1) / splits;
+    p.kb_per_split = chunks_per * KCH;
+    splits = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;
+    if (splits < 1) splits = 1;
+    double *part = nullptr;
+    e = set_smem_once(oz_gemm_kernel<EPI_STORE>, SMEM);
+    if (e == cudaSuccess) e = set_smem_once(oz_gemm_kernel<EPI_ERR>, SMEM);
+    if (e == cudaSuccess && splits > 1) {
+        e = cudaMallocAsync((void **)&part, sizeof(double) * (size_t)splits * M * N, s);
+        p.C = part;
+        p.ldc = M;
+        p.split_stride = M * N;
+    } else {
+        p.C = C;
+        p.ldc = ldc;
+        p.split_stride = 0;
+    }
+    ProfScope prof(PROF_OZ_GEMM, 2.0 * M * N * K, 2.0 * NS * ((double)M * K + (double)K * N) + 8.0 * 2 * M * N, s);
+    if (e == cudaSuccess) {
+        dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
+        count_launch();
+        if (x.epilogue == EPI_ERR) oz_gemm_kernel<EPI_ERR><<<grid, NTHREADS, SMEM, s>>>(maps, p);
+        else oz_gemm_kernel<EPI_STORE><<<grid, NTHREADS, SMEM, s>>>(maps, p);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && splits > 1) {
+        count_launch();
+        const int blocks = (int)std::min<int64_t>((M * N + 255) / 256, 4LL * kNumSMs * 8);
+        split_sum_kernel<<<blocks, 256, 0, s>>>(part, (int)splits, M, N, alpha, beta, C, ldc);
+        e = cudaGetLastError();
+    }
+    if (part) cudaFreeAsync(part, s);
+    return e;
+}
+
+// C = alpha op(A) op(B) + beta C (EPI_STORE) or the squared error against
+// x.ref (EPI_ERR), FP64, through the sliced tensor-core product.
+cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                    const double *B, int64_t ldb, double beta, double *C, int64_t ldc, const GemmExtra &x,
+                    int *err_flag, cudaStream_t s) {
+    using namespace oz;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    Slices sa, sb;
+    // op(A)(i, k): rows i, reduction k; op(B)(k, j) seen as rows j
+    cudaError_t e = make_slices(A, M, K, ta ? lda : 1, ta ? 1 : lda, sa, s);
+    const bool same = (A == B) && (ta != tb) && (lda == ldb) && (M == N);
+    if (e == cudaSuccess && !same) e = make_slices(B, N, K, tb ? 1 : ldb, tb ? ldb : 1, sb, s);
+    const Slices &SB = same ? sa : sb;
+    if (e == cudaSuccess) {
+        OzOperand oa{sa.q, sa.e, 0, sa.ldk, (int64_t)M * sa.ldk};
+        OzOperand ob{SB.q, SB.e, 0, SB.ldk, (int64_t)N * SB.ldk};
+        e = oz_gemm_ops(oa, ob, M, N, K, alpha, beta, C, ldc, x, err_flag, s);
+    }
+    free_slices(sa, s);
+    if (!same) free_slices(sb, s);
+    return e;
+}
+
+int64_t oz_gemm_err_ctas(int64_t M, int64_t N) { return ((M + oz::BM - 1) / oz::BM) * ((N + oz::BN - 1) / oz::BN); }
+
+}  // namespace eod

@@ -1,0 +1,136 @@
+"""The FP64 GEMM emulated on tcgen05 (exact BF16 slices, FP64 accumulation)
+against cuBLAS FP64 (torch) on the same inputs: ragged shapes, every
+transpose combination, split-K, alpha/beta, wide dynamic range, zero rows."""
+import ctypes
+
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eod():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2506_22713_gb300 as eod
+    return eod
+
+
+def _cm(x):
+    return x.t().contiguous().t()
+
+
+def _run(eod, mode, ta, tb, A, B, C, alpha, beta, M, N, K):
+    s = torch.cuda.current_stream()
+    st = eod.eod_abe_debug_f64_gemm(mode, int(ta), int(tb), M, N, K, alpha, ctypes.c_void_p(A.data_ptr()),
+                                    A.stride(1), ctypes.c_void_p(B.data_ptr()), B.stride(1), beta,
+                                    ctypes.c_void_p(C.data_ptr()), C.stride(1), ctypes.c_void_p(s.cuda_stream))
+    assert st == eod.EOD_OK, eod.status_string(st)
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("M,N,K", [(128, 64, 128), (300, 70, 200), (1000, 513, 777), (64, 16, 4000),
+                                   (2048, 2037, 2048)])
+def test_emulated_matches_fp64(eod, ta, tb, M, N, K):
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K + 11 * ta + 5 * tb)
+    A = _cm(torch.randn((K, M) if ta else (M, K), generator=g, device="cuda", dtype=torch.float64))
+    B = _cm(torch.randn((N, K) if tb else (K, N), generator=g, device="cuda", dtype=torch.float64))
+    C0 = _cm(torch.randn((M, N), generator=g, device="cuda", dtype=torch.float64))
+    opA = A.t() if ta else A
+    opB = B.t() if tb else B
+    ref = 0.75 * (opA @ opB) - 0.5 * C0
+    C = C0.clone()
+    _run(eod, 1, ta, tb, A, B, C, 0.75, -0.5, M, N, K)
+    scale = 0.75 * (opA.abs() @ opB.abs()) + 0.5 * C0.abs()
+    err = ((C - ref).abs() / scale).max().item()
+    assert err <= 1e-13, err   # FP64-class: BF16 alone would give ~1e-3, FP32 ~1e-7
+
+
+def test_emulated_dynamic_range_and_zero_rows(eod):
+    M, N, K = 257, 190, 1030
+    g = torch.Generator(device="cuda").manual_seed(3)
+    rs = torch.logspace(-8, 8, M, device="cuda", dtype=torch.float64)
+    cs = torch.logspace(6, -6, N, device="cuda", dtype=torch.float64)
+    A = _cm(torch.randn((M, K), generator=g, device="cuda", dtype=torch.float64) * rs[:, None])
+    B = _cm(torch.randn((K, N), generator=g, device="cuda", dtype=torch.float64) * cs[None, :])
+    A[17] = 0.0
+    B[:, 5] = 0.0
+    C = _cm(torch.zeros((M, N), device="cuda", dtype=torch.float64))
+    _run(eod, 1, False, False, A, B, C, 1.0, 0.0, M, N, K)
+    ref = A @ B
+    scale = A.abs() @ B.abs()
+    assert (C[17] == 0).all() and (C[:, 5] == 0).all()
+    mask = scale > 0
+    assert ((C - ref).abs()[mask] / scale[mask]).max().item() <= 1e-13
+
+
+def test_simt_and_emulated_agree_on_gram(eod):
+    M, K = 700, 3000
+    g = torch.Generator(device="cuda").manual_seed(9)
+    W = _cm(torch.randn((K, M), generator=g, device="cuda", dtype=torch.float64))
+    C1 = _cm(torch.zeros((M, M), device="cuda", dtype=torch.float64))
+    C2 = C1.clone()
+    _run(eod, 0, True, False, W, W, C1, 1.0, 0.0, M, M, K)
+    _run(eod, 1, True, False, W, W, C2, 1.0, 0.0, M, M, K)
+    ref = W.t() @ W
+    assert ((C2 - ref).abs() / (W.abs().t() @ W.abs())).max().item() <= 1e-13
+    assert ((C1 - ref).abs() / (W.abs().t() @ W.abs())).max().item() <= 1e-13
+
+
+# --------------------------------------------------------------------------
+# whole factorisation: every FP64 product emulated vs every product on SIMT
+# --------------------------------------------------------------------------
+
+_CHILD = r"""
+import sys, numpy as np, torch
+import paper_2506_22713_gb300 as eod
+import workloads as W
+which, out = sys.argv[1], sys.argv[2]
+if which == "exact":
+    w = W.exact_rank(m=900, n=700, r=60, seed=8)
+    A, tol, k, seed = w.A, 1e-8, 32, 5
+else:
+    w = W.image_like(m=640, n=520, r=90, seed=13, tol=0.01)
+    A, tol, k, seed = w.A, w.tol, 64, w.seed
+f = eod.factor(torch.from_numpy(np.asfortranarray(A)).cuda(), tol, seed, block_k=k, tol_mode="rel")
+np.savez(out, rank=f.rank, rel_err=f.rel_err, tdiag=np.array(f.tdiag), U=f.U.cpu().numpy(),
+         V=f.V.cpu().numpy(), D=f.D.cpu().numpy(), tol=tol, k=k, seed=seed)
+"""
+
+
+def _child(which, mode, tmp_path):
+    import os
+    import subprocess
+    import sys
+    import numpy as np
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / f"{which}_{mode}.npz")
+    env = dict(os.environ, EOD_FP64_GEMM=mode, PYTHONPATH=root)
+    subprocess.run([sys.executable, "-c", _CHILD, which, out], check=True, cwd=root, env=env, timeout=600)
+    return np.load(out)
+
+
+@pytest.mark.parametrize("which", ["exact", "image"])
+def test_factorisation_emulated_matches_simt_and_oracle(eod, which, tmp_path):
+    import numpy as np
+    import oracle
+    import workloads as W
+    em = _child(which, "emulated", tmp_path)
+    si = _child(which, "simt", tmp_path)
+    assert int(em["rank"]) == int(si["rank"])
+    # the diagonal of T decides the rank: the two product paths agree to FP64 rounding
+    te, ts = np.abs(em["tdiag"]), np.abs(si["tdiag"])
+    assert te.shape == ts.shape
+    assert np.all(np.abs(te - ts) <= 1e-9 * ts.max())
+    assert abs(float(em["rel_err"]) - float(si["rel_err"])) <= 1e-12
+    Ue, Us = em["U"], si["U"]
+    assert np.linalg.norm(Ue.T @ Ue - np.eye(Ue.shape[1])) <= 1e-12
+    Ae = Ue @ em["D"] @ em["V"].T      # A ~ U D V^T with D upper triangular
+    As = Us @ si["D"] @ si["V"].T
+    assert np.linalg.norm(Ae - As) <= 1e-10 * np.linalg.norm(As)
+    w = W.exact_rank(m=900, n=700, r=60, seed=8) if which == "exact" else W.image_like(m=640, n=520, r=90,
+                                                                                     seed=13, tol=0.01)
+    ref = oracle.eod_abe(w.A, float(em["tol"]), 1, k=int(em["k"]), seed=int(em["seed"]))
+    assert int(em["rank"]) == ref["r"]
+    assert abs(float(em["rel_err"]) - ref["rel_err"]) <= 1e-10
