@@ -265,9 +265,14 @@ EOD_API eod_status eod_abe_fro_norm_noalloc(const void *A, int64_t m, int64_t n,
 
 /* Test hook (no counterpart in the paper): one FP64 GEMM C = alpha op(A)
  * op(B) + beta C on device matrices, column-major, op(X) = X^T when the
- * matching flag is nonzero; mode 0 runs the SIMT DFMA kernel, mode 1 the FP64
- * emulation on tcgen05 tensor cores that the plain FP64 path uses for large
- * products (exact BF16 slices, FP64 accumulation).  Returns after
+ * matching flag is nonzero; mode & 3 == 0 runs the SIMT DFMA kernel, 1 the
+ * FP64 emulation on tcgen05 tensor cores that the plain FP64 path uses for
+ * large products (exact BF16 slices, FP64 accumulation).  Bits of mode above
+ * those select the structured forms the factorisation uses: 16 = only the
+ * upper triangle of C is wanted (the emulation stores row <= col only, the
+ * SIMT kernel whole tiles that touch it), 32 = op(A) upper triangular,
+ * 64 = op(B) upper triangular (the zero part is then not read by the
+ * emulation; the SIMT kernel expects it to hold zeros).  Returns after
  * synchronising `stream`; EOD_EINVAL for bad sizes or leading dimensions,
  * EOD_ETIMEOUT if a bounded device wait ran out. */
 EOD_API eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,

@@ -236,6 +236,9 @@ enum CholCode { CHOL_ALL = 0, CHOL_BELOW = 1, CHOL_UNCERTAIN = 2, CHOL_FAIL = 3 
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2,
                        double delta_coef, double rho, double shift, double *R,
                        double *Rinv, int64_t ldr, int *info, cudaStream_t s);
+// X (p x p, ld ldx) = R^{-1} for upper-triangular R (p <= 256), zeros below
+// the diagonal
+cudaError_t tri_inverse(const double *R, int64_t ldr, int p, double *X, int64_t ldx, cudaStream_t s);
 // tdiag[j] = |R1(j,j) * R2(j,j)|, j < p
 cudaError_t tdiag_product(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
                           double *tdiag, cudaStream_t s);

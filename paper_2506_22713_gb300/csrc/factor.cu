@@ -77,39 +77,69 @@ template <> struct Traits<float> { static constexpr int dtype = EOD_F32; static 
 
 // ---------------------------------------------------------------------------
 // Blocked CholQR pass on W (rows x p, FP64 Gram, FP64 R):  G = W^T W,
-// R = chol(G + shift I) by 64-column blocks (left-looking), W <- W R^{-1}.
-// Each diagonal block's inverse is kept for the triangular solve.
+// R = chol(G + shift I), W <- W R^{-1}.
+// The Cholesky runs right-looking over panels of kPB columns: each diagonal
+// panel is factored left-looking over 64-column leaves (one CTA each, the
+// leaf inverses kept), its triangular inverse formed, then the panel row of R
+// and the trailing Gram update are two large products.  The solve
+// W <- W R^{-1} runs over the same panels (diagonal inverse, then the
+// trailing columns of W), so every large product is a plain GEMM.
 // Returns EOD_EPRECISION (without touching W) if a pivot is not positive.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct CoreWork {
-    double *G = nullptr, *R = nullptr, *Rp = nullptr, *Inv = nullptr, *trace = nullptr;
+    double *G = nullptr, *R = nullptr, *Rp = nullptr, *Inv = nullptr, *RiD = nullptr, *trace = nullptr;
     T *InvT = nullptr, *Tmp = nullptr;
     int *info = nullptr;
     int64_t pcap = 0, rows_cap = 0;
 };
 
-static constexpr int kNB = 64;
+static constexpr int kNB = 64;    // leaf width (one-CTA Cholesky)
+static constexpr int kPB = 256;   // panel width of the core Cholesky and triangular solve
 
 template <typename T>
-static eod_status chol_blocked(CoreWork<T> &w, int64_t p, double shift, HostMirror &hm, Scratch *ws,
-                               cudaStream_t s, double *Rout) {
-    const int64_t nblk = (p + kNB - 1) / kNB;
+static eod_status chol_panel_leaves(CoreWork<T> &w, int64_t p, int64_t j0, int64_t pe, double shift, Scratch *ws,
+                                    cudaStream_t s, double *Rout) {
     GemmExtra ex;
-    EOD_CU(fill_zero<double>(Rout, p, p, p, s));
-    for (int64_t J = 0; J < nblk; ++J) {
-        const int64_t j0 = J * kNB, jb = std::min<int64_t>(kNB, p - j0);
-        if (j0 > 0)
-            EOD_CU((gemm<double, double, double, double>(true, false, jb, p - j0, j0, -1.0, Rout + j0 * p, p,
-                                                          Rout + j0 * p, p, 1.0, w.G + j0 + j0 * p, p, ex, ws, s)));
-        EOD_CU(chol_small(w.G + j0 + j0 * p, p, (int)jb, 0, 0.0, 0.0, 0.0, shift, w.Rp, w.Inv + J * kNB * kNB,
-                          kNB, w.info + 2 * J, s));
-        EOD_CU(copy_matrix<double, double>(w.Rp, kNB, Rout + j0 + j0 * p, p, jb, jb, false, s));
-        if (j0 + jb < p)
-            EOD_CU((gemm<double, double, double, double>(true, false, jb, p - j0 - jb, jb, 1.0,
-                                                          w.Inv + J * kNB * kNB, kNB, w.G + j0 + (j0 + jb) * p, p,
-                                                          0.0, Rout + j0 + (j0 + jb) * p, p, ex, ws, s)));
+    for (int64_t l0 = j0; l0 < pe; l0 += kNB) {
+        const int64_t lb = std::min<int64_t>(kNB, pe - l0), L = l0 / kNB;
+        if (l0 > j0)   // G(l, l:pe) -= R(j0:l0, l)^T R(j0:l0, l:pe)
+            EOD_CU((gemm<double, double, double, double>(true, false, lb, pe - l0, l0 - j0, -1.0, Rout + j0 + l0 * p,
+                                                          p, Rout + j0 + l0 * p, p, 1.0, w.G + l0 + l0 * p, p, ex,
+                                                          ws, s)));
+        EOD_CU(chol_small(w.G + l0 + l0 * p, p, (int)lb, 0, 0.0, 0.0, 0.0, shift, w.Rp, w.Inv + L * kNB * kNB, kNB,
+                          w.info + 2 * L, s));
+        EOD_CU(copy_matrix<double, double>(w.Rp, kNB, Rout + l0 + l0 * p, p, lb, lb, false, s));
+        if (l0 + lb < pe)   // R(l, l+1:pe) = R_ll^{-T} G(l, l+1:pe)
+            EOD_CU((gemm<double, double, double, double>(true, false, lb, pe - l0 - lb, lb, 1.0,
+                                                          w.Inv + L * kNB * kNB, kNB, w.G + l0 + (l0 + lb) * p, p,
+                                                          0.0, Rout + l0 + (l0 + lb) * p, p, ex, ws, s)));
     }
+    return EOD_OK;
+}
+
+template <typename T>
+static eod_status chol_panels(CoreWork<T> &w, int64_t p, double shift, HostMirror &hm, Scratch *ws,
+                              cudaStream_t s, double *Rout) {
+    GemmExtra ex, sym;
+    sym.upper_only = true;
+    EOD_CU(fill_zero<double>(Rout, p, p, p, s));
+    for (int64_t j0 = 0; j0 < p; j0 += kPB) {
+        const int64_t pe = std::min<int64_t>(p, j0 + kPB), jb = pe - j0;
+        double *RiJ = w.RiD + (j0 / kPB) * kPB * kPB;   // ld kPB
+        EOD_TRY(chol_panel_leaves(w, p, j0, pe, shift, ws, s, Rout));
+        EOD_CU(tri_inverse(Rout + j0 + j0 * p, p, (int)jb, RiJ, kPB, s));
+        if (pe < p) {
+            // R(J, pe:p) = R_JJ^{-T} G(J, pe:p);  G(pe:p, pe:p) -= R(J, pe:p)^T R(J, pe:p)
+            EOD_CU((gemm<double, double, double, double>(true, false, jb, p - pe, jb, 1.0, RiJ, kPB,
+                                                          w.G + j0 + pe * p, p, 0.0, Rout + j0 + pe * p, p, ex, ws,
+                                                          s)));
+            EOD_CU((gemm<double, double, double, double>(true, false, p - pe, p - pe, jb, -1.0, Rout + j0 + pe * p,
+                                                          p, Rout + j0 + pe * p, p, 1.0, w.G + pe + pe * p, p, sym,
+                                                          ws, s)));
+        }
+    }
+    const int64_t nblk = (p + kNB - 1) / kNB;
     std::vector<int> infos(2 * nblk);
     EOD_CU(cudaMemcpyAsync(infos.data(), w.info, sizeof(int) * 2 * nblk, cudaMemcpyDeviceToHost, s));
     EOD_CU(cudaStreamSynchronize(s));
@@ -120,38 +150,36 @@ static eod_status chol_blocked(CoreWork<T> &w, int64_t p, double shift, HostMirr
     return EOD_OK;
 }
 
-// W <- W R^{-1}, R upper p x p (ld p) with diagonal-block inverses in w.Inv.
+// W <- W R^{-1}, R upper p x p (ld p) with the diagonal panels' inverses in w.RiD.
 template <typename T>
-static eod_status trsm_right(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64_t p, const double *R,
-                             Scratch *ws, cudaStream_t s) {
-    const int64_t nblk = (p + kNB - 1) / kNB;
-    GemmExtra ex;
-    GemmExtra exb;
+static eod_status trsm_panels(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64_t p, const double *R,
+                              Scratch *ws, cudaStream_t s) {
+    GemmExtra ex, exb;
     exb.b_upper = true;
-    for (int64_t J = 0; J < nblk; ++J) {
-        const int64_t j0 = J * kNB, jb = std::min<int64_t>(kNB, p - j0);
-        if (j0 > 0) {
-            const T *Rb = nullptr;
-            if (std::is_same<T, double>::value) {
-                Rb = (const T *)(R + j0 * p);
-                EOD_CU((gemm<T, T, T, T>(false, false, rows, jb, j0, -1.0, W, ldw, Rb, p, 1.0, W + j0 * ldw, ldw,
-                                         ex, ws, s)));
-            } else {
-                EOD_CU((copy_matrix<double, T>(R + j0 * p, p, w.InvT, j0, j0, jb, false, s)));
-                EOD_CU((gemm<T, T, T, T>(false, false, rows, jb, j0, -1.0, W, ldw, w.InvT, j0, 1.0, W + j0 * ldw,
-                                         ldw, ex, ws, s)));
-            }
+    for (int64_t j0 = 0; j0 < p; j0 += kPB) {
+        const int64_t pe = std::min<int64_t>(p, j0 + kPB), jb = pe - j0;
+        const double *RiJ = w.RiD + (j0 / kPB) * kPB * kPB;
+        const T *Ri = (const T *)RiJ;
+        if (!std::is_same<T, double>::value) {
+            EOD_CU((copy_matrix<double, T>(RiJ, kPB, w.InvT, kPB, jb, jb, false, s)));
+            Ri = w.InvT;
         }
-        const T *Inv;
-        if (std::is_same<T, double>::value) {
-            Inv = (const T *)(w.Inv + J * kNB * kNB);
-        } else {
-            EOD_CU((copy_matrix<double, T>(w.Inv + J * kNB * kNB, kNB, w.InvT, kNB, jb, jb, false, s)));
-            Inv = w.InvT;
-        }
-        EOD_CU((gemm<T, T, T, T>(false, false, rows, jb, jb, 1.0, W + j0 * ldw, ldw, Inv, kNB, 0.0, w.Tmp, rows,
-                                 exb, ws, s)));
+        // X_J = W_J R_JJ^{-1}
+        EOD_CU((gemm<T, T, T, T>(false, false, rows, jb, jb, 1.0, W + j0 * ldw, ldw, Ri, kPB, 0.0, w.Tmp, rows, exb,
+                                 ws, s)));
         EOD_CU((copy_matrix<T, T>(w.Tmp, rows, W + j0 * ldw, ldw, rows, jb, false, s)));
+        if (pe < p) {
+            // W(:, pe:p) -= X_J R(J, pe:p)
+            const T *Rb = (const T *)(R + j0 + pe * p);
+            int64_t ldb = p;
+            if (!std::is_same<T, double>::value) {
+                EOD_CU((copy_matrix<double, T>(R + j0 + pe * p, p, w.InvT, jb, jb, p - pe, false, s)));
+                Rb = w.InvT;
+                ldb = jb;
+            }
+            EOD_CU((gemm<T, T, T, T>(false, false, rows, p - pe, jb, -1.0, W + j0 * ldw, ldw, Rb, ldb, 1.0,
+                                     W + pe * ldw, ldw, ex, ws, s)));
+        }
     }
     return EOD_OK;
 }
@@ -182,7 +210,7 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
     for (int pass = 0; pass < passes; ++pass) {
         EOD_TRY(gram_full(W, rows, p, ldw, w.G, sym, ws, s));
         double *Rpass = (pass == 0) ? Rout : w.Rp + kNB * kNB;  // pass factor storage
-        eod_status st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
+        eod_status st = chol_panels(w, p, shift, hm, ws, s, Rpass);
         if (st == EOD_EPRECISION && pass == 0 && shift == 0.0) {
             // shifted CholQR: shift = 11 (rows p + p (p+1)) u ||W||_2^2, ||W||_2^2 <= trace(G)
             EOD_CU(trace_sum(w.G, p, p, w.trace, s));
@@ -192,11 +220,11 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
             shift = 11.0 * ((double)rows * p + (double)p * (p + 1)) * u * hm.val[0];
             passes = 3;
             EOD_TRY(gram_full(W, rows, p, ldw, w.G, sym, ws, s));
-            st = chol_blocked(w, p, shift, hm, ws, s, Rpass);
+            st = chol_panels(w, p, shift, hm, ws, s, Rpass);
         }
         if (st != EOD_OK) return st;
         shift = 0.0;
-        EOD_TRY(trsm_right(w, W, rows, ldw, p, Rpass, ws, s));
+        EOD_TRY(trsm_panels(w, W, rows, ldw, p, Rpass, ws, s));
         if (pass > 0) {
             // Racc = Rpass * Rout (both upper), then Rout = Racc
             GemmExtra tri;
@@ -547,9 +575,10 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(ar.get(&cw.R, (size_t)r * r));
     EOD_TRY(ar.get(&cw.Rp, (size_t)kNB * kNB + (size_t)r * r));
     EOD_TRY(ar.get(&cw.Inv, (size_t)nblk * kNB * kNB));
+    EOD_TRY(ar.get(&cw.RiD, (size_t)((r + kPB - 1) / kPB) * kPB * kPB));
     EOD_TRY(ar.get(&cw.trace, 1));
-    EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kNB) * kNB));
-    EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kNB));
+    EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kPB) * kPB));
+    EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kPB));
     EOD_TRY(ar.get(&cw.info, (size_t)2 * nblk));
     Phase ph_core("eod.core");
     EOD_CU((copy_matrix<T, T>(Ct, n, V, n, n, r, false, s)));

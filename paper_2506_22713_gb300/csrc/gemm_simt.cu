@@ -6,10 +6,13 @@
 // of the core (steps 9-11) and the reconstruction Q C with its fused
 // Frobenius error (Sec. 4.1).
 //
-// Tile 64 x 64 x 16, 256 threads, 4 x 4 outputs per thread with the row
+// Tile TS x TS x 16 (TS = 64, or 32 for products too small to fill the 152
+// SMs with 64-tiles), 256 threads, (TS/16)^2 outputs per thread with the row
 // index fastest across lanes so that column-major stores coalesce.  When the
-// tile grid is smaller than two waves of the 152 SMs the K range is split and
-// the partial tiles are summed by a second kernel in a fixed order.
+// tile grid is smaller than two waves of the SMs the K range is split and the
+// partial tiles are summed by a second kernel in a fixed order.  FP64 runs at
+// a few DFMA per clock per SM here, so small FP64 products are only fast when
+// they are spread over every SM.
 #include "common.cuh"
 #include "instrument.cuh"
 
@@ -21,16 +24,18 @@
 namespace eod {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
+constexpr int BM = 64, BN = 64;   // the large tile (gemm_err_ctas)
 constexpr int F_UPPER_ONLY = 1, F_A_UPPER = 2, F_B_UPPER = 4;
 
-template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB, int EPI, bool SPLIT>
+template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB, int EPI, bool SPLIT, int TS>
 __global__ void __launch_bounds__(NT)
 gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restrict__ A, int64_t lda,
                  const TB *__restrict__ B, int64_t ldb, Acc beta, TC *C, int64_t ldc, int64_t kchunk,
                  Acc *__restrict__ part, int flags, const TC *__restrict__ ref, int64_t ldref,
                  double *__restrict__ errp)
 {
+    constexpr int BM = TS, BN = TS, TPT = TS / 16;   // outputs per thread along each axis
     __shared__ Acc As[BK][BM + 1];
     __shared__ Acc Bs[BK][BN + 1];
     __shared__ double red[32];
@@ -47,11 +52,11 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
     if (flags & F_A_UPPER) kb = kb > m0 ? kb : m0;                // op(A)(i,l) = 0 for l < i
     if (flags & F_B_UPPER) ke = ke < n0 + BN ? ke : n0 + BN;      // op(B)(l,j) = 0 for l > j
 
-    Acc acc[4][4];
+    Acc acc[TPT][TPT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TPT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = Acc(0);
+        for (int j = 0; j < TPT; ++j) acc[i][j] = Acc(0);
 
     for (int64_t k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
@@ -77,15 +82,15 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            Acc a[4], b[4];
+            Acc a[TPT], b[TPT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tx + 16 * i];
+            for (int i = 0; i < TPT; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][ty + 16 * j];
+            for (int j = 0; j < TPT; ++j) b[j] = Bs[kk][ty + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TPT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < TPT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
@@ -93,11 +98,11 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
     if (SPLIT) {
         Acc *dst = part + (int64_t)blockIdx.z * M * N;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TPT; ++j) {
             const int64_t col = n0 + ty + 16 * j;
             if (col >= N) continue;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < TPT; ++i) {
                 const int64_t row = m0 + tx + 16 * i;
                 if (row < M) dst[row + col * M] = acc[i][j];
             }
@@ -106,11 +111,11 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
     }
     double local = 0.0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TPT; ++j) {
         const int64_t col = n0 + ty + 16 * j;
         if (col >= N) continue;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < TPT; ++i) {
             const int64_t row = m0 + tx + 16 * i;
             if (row >= M) continue;
             Acc v = alpha * acc[i][j];
@@ -133,13 +138,13 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
 
 template <typename TC, typename Acc>
 __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int S, const Acc *__restrict__ part,
-                                     Acc alpha, Acc beta, TC *C, int64_t ldc, int upper_only)
+                                     Acc alpha, Acc beta, TC *C, int64_t ldc, int upper_only, int ts)
 {
     const int64_t total = M * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = e % M, col = e / M;
-        if (upper_only && (row / BM) * BM > (col / BN) * BN + BN - 1) continue;
+        if (upper_only && (row / ts) * ts > (col / ts) * ts + ts - 1) continue;
         Acc s = Acc(0);
         for (int z = 0; z < S; ++z) s += part[(int64_t)z * total + e];
         Acc v = alpha * s;
@@ -148,41 +153,34 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int S, const Acc *__r
     }
 }
 
-template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB>
-cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, int64_t lda,
-                   const TB *B, int64_t ldb, double beta, TC *C, int64_t ldc, const GemmExtra &x,
-                   Scratch *ws, cudaStream_t s)
-{
-    const int64_t gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
-    const int flags = (x.upper_only ? F_UPPER_ONLY : 0) | (x.a_upper ? F_A_UPPER : 0) |
-                      (x.b_upper ? F_B_UPPER : 0);
-    if (gn > 65535) return cudaErrorInvalidValue;
-    double frac = 1.0;
-    if (x.upper_only) frac *= 0.5;
-    if (x.a_upper && x.b_upper) frac /= 6.0;
-    else if (x.a_upper || x.b_upper) frac *= 0.5;
-    const double flops = 2.0 * (double)M * (double)N * (double)K * frac;
-    double bytes = (double)sizeof(TA) * M * K + (double)sizeof(TB) * K * N + (double)sizeof(TC) * M * N;
-    if (beta != 0.0 || x.epilogue == EPI_ERR) bytes += (double)sizeof(TC) * M * N;
-    ProfScope prof(PROF_GEMM_SIMT, flops, bytes, s);
-    if (x.epilogue == EPI_ERR) {
-        count_launch();
-        dim3 grid((unsigned)gm, (unsigned)gn, 1);
-        gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_ERR, false><<<grid, NT, 0, s>>>(
-            M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, K > 0 ? K : 1, nullptr, flags,
-            (const TC *)x.ref, x.ldref, x.err_partials);
-        return cudaGetLastError();
-    }
-    int64_t tiles = gm * gn;
-    if (x.upper_only) tiles = (tiles + gm) / 2 + 1;
+// tile grid and K split for tile size ts
+struct SimtPlan {
+    int64_t gm, gn, S;
+};
+
+inline SimtPlan simt_plan(int ts, int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
+    SimtPlan p;
+    p.gm = (M + ts - 1) / ts;
+    p.gn = (N + ts - 1) / ts;
+    int64_t tiles = p.gm * p.gn;
+    if (x.upper_only) tiles = (tiles + p.gm) / 2 + 1;
     const int64_t target = 2 * kNumSMs;
-    int64_t S = 1;
-    if (tiles < target && K > 4 * BK) {
-        S = (target + tiles - 1) / tiles;
-        int64_t kmax = (K + 4 * BK - 1) / (4 * BK);
-        if (S > kmax) S = kmax;
-        if (S > x.max_split) S = x.max_split;
+    p.S = 1;
+    if (tiles < target && K > 2 * BK) {
+        p.S = (target + tiles - 1) / tiles;
+        const int64_t kmax = (K + 2 * BK - 1) / (2 * BK);
+        if (p.S > kmax) p.S = kmax;
+        if (p.S > x.max_split) p.S = x.max_split;
     }
+    return p;
+}
+
+template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB, int TS>
+cudaError_t launch_store(const SimtPlan &pl, int64_t M, int64_t N, int64_t K, double alpha, const TA *A,
+                         int64_t lda, const TB *B, int64_t ldb, double beta, TC *C, int64_t ldc, int flags,
+                         const GemmExtra &x, Scratch *ws, cudaStream_t s)
+{
+    int64_t S = pl.S;
     Acc *part = nullptr;
     size_t mark = ws ? ws->mark() : 0;
     while (S > 1) {
@@ -195,10 +193,10 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
         kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
         S = (K + kchunk - 1) / kchunk;
     }
-    dim3 grid((unsigned)gm, (unsigned)gn, (unsigned)S);
+    dim3 grid((unsigned)pl.gm, (unsigned)pl.gn, (unsigned)S);
     if (S > 1) {
         count_launch(2);
-        gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, true><<<grid, NT, 0, s>>>(
+        gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, true, TS><<<grid, NT, 0, s>>>(
             M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, part, flags, nullptr, 0,
             nullptr);
         EOD_CUDA_TRY(cudaGetLastError());
@@ -206,16 +204,50 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4 * kNumSMs * 8) blocks = 4 * kNumSMs * 8;
         splitk_reduce_kernel<TC, Acc><<<blocks, 256, 0, s>>>(M, N, (int)S, part, (Acc)alpha, (Acc)beta,
-                                                             C, ldc, x.upper_only ? 1 : 0);
+                                                             C, ldc, x.upper_only ? 1 : 0, TS);
         EOD_CUDA_TRY(cudaGetLastError());
         ws->release(mark);
         return cudaSuccess;
     }
     count_launch();
-    gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, false><<<grid, NT, 0, s>>>(
+    gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, false, TS><<<grid, NT, 0, s>>>(
         M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, nullptr, flags, nullptr, 0,
         nullptr);
     return cudaGetLastError();
+}
+
+template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB>
+cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, int64_t lda,
+                   const TB *B, int64_t ldb, double beta, TC *C, int64_t ldc, const GemmExtra &x,
+                   Scratch *ws, cudaStream_t s)
+{
+    const int flags = (x.upper_only ? F_UPPER_ONLY : 0) | (x.a_upper ? F_A_UPPER : 0) |
+                      (x.b_upper ? F_B_UPPER : 0);
+    if ((N + 31) / 32 > 65535) return cudaErrorInvalidValue;
+    double frac = 1.0;
+    if (x.upper_only) frac *= 0.5;
+    if (x.a_upper && x.b_upper) frac /= 6.0;
+    else if (x.a_upper || x.b_upper) frac *= 0.5;
+    const double flops = 2.0 * (double)M * (double)N * (double)K * frac;
+    double bytes = (double)sizeof(TA) * M * K + (double)sizeof(TB) * K * N + (double)sizeof(TC) * M * N;
+    if (beta != 0.0 || x.epilogue == EPI_ERR) bytes += (double)sizeof(TC) * M * N;
+    ProfScope prof(PROF_GEMM_SIMT, flops, bytes, s);
+    if (x.epilogue == EPI_ERR) {
+        count_launch();
+        dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), 1);
+        gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_ERR, false, 64><<<grid, NT, 0, s>>>(
+            M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, K > 0 ? K : 1, nullptr, flags,
+            (const TC *)x.ref, x.ldref, x.err_partials);
+        return cudaGetLastError();
+    }
+    // 64-tiles unless they leave most SMs idle
+    const SimtPlan p64 = simt_plan(64, M, N, K, x);
+    if (p64.gm * p64.gn * p64.S >= kNumSMs)
+        return launch_store<TA, TB, TC, Acc, TRA, TRB, 64>(p64, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                            flags, x, ws, s);
+    const SimtPlan p32 = simt_plan(32, M, N, K, x);
+    return launch_store<TA, TB, TC, Acc, TRA, TRB, 32>(p32, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags,
+                                                        x, ws, s);
 }
 
 }  // namespace
@@ -277,8 +309,12 @@ extern "C" eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t t
     if (lda < (ta ? K : M) || ldb < (tb ? N : K)) return EOD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     GemmExtra x;
+    x.upper_only = (mode & 16) != 0;
+    x.a_upper = (mode & 32) != 0;
+    x.b_upper = (mode & 64) != 0;
+    if ((mode & 3) > 1 || (mode & ~(3 | 16 | 32 | 64)) != 0) return EOD_EINVAL;
     cudaError_t e;
-    if (mode == 1) {
+    if ((mode & 3) == 1) {
         int *flag = nullptr;
         if (cudaMallocAsync((void **)&flag, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
         cudaMemsetAsync(flag, 0, sizeof(int), s);

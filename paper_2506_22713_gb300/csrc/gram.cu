@@ -270,7 +270,9 @@ template <typename T>
 cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, int64_t ldg, Scratch *ws,
                         cudaStream_t s) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
-    int64_t ctas = (m + GR - 1) / GR;
+    // at least 16 rows per CTA, up to two CTAs per SM: a short panel still
+    // spreads its FP64 work over most SMs
+    int64_t ctas = (m + 15) / 16;
     if (ctas > 2 * kNumSMs) ctas = 2 * kNumSMs;
     if (ctas < 1) ctas = 1;
     int64_t rows_per = (m + ctas - 1) / ctas;

@@ -68,6 +68,8 @@ struct Params {
     int64_t ldr;
     double *errp;
     int *err_flag;
+    int upper_only;           // store only entries with row <= col
+    int a_tri, b_tri;         // op(A) / op(B) upper triangular: skip their zero K blocks
 };
 
 template <int EPI>
@@ -87,9 +89,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
-    const int64_t kb0 = (int64_t)blockIdx.z * p.kb_per_split;
+    if (p.upper_only && m0 >= n0 + BN) return;   // every entry of the tile is below the diagonal
+    int64_t kb0 = (int64_t)blockIdx.z * p.kb_per_split;
     int64_t kb1 = kb0 + p.kb_per_split;
     if (kb1 > p.kblocks) kb1 = p.kblocks;
+    if (p.a_tri && kb0 < m0 / BK) kb0 = m0 / BK;              // op(A)(i, k) = 0 for k < i
+    if (p.b_tri && kb1 > (n0 + BN + BK - 1) / BK) kb1 = (n0 + BN + BK - 1) / BK;   // op(B)(k, j) = 0 for k > j
     const int64_t nkb = kb1 > kb0 ? kb1 - kb0 : 0;
     const int64_t nchunks = (nkb + KCH - 1) / KCH;
 
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
 #pragma unroll
             for (int j = 0; j < ECOLS; ++j) {
                 const int64_t col = n0 + c0 + j;
-                if (col < p.N) {
+                if (col < p.N && !(p.upper_only && row > col)) {
                     const double val = ldexp(acc[j], ei + (p.eb ? max(p.eb[col], -1100) : p.eb_fixed));
                     if (EPI == EPI_STORE) {
                         if (p.split_stride > 0) {
@@ -263,65 +268,88 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
     }
 }
 
+// Triangular operands (the SIMT kernel's a_upper / b_upper): with tri == 1
+// op(A) is upper triangular, X(r, k) = op(A)(r, k) is zero for r > k; with
+// tri == 2 op(B) is, and X(r, k) = op(B)(k, r) is zero for k > r.  Those
+// entries are never read.
+__device__ __forceinline__ bool tri_zero(int tri, int64_t r, int64_t k) {
+    return (tri == 1 && r > k) || (tri == 2 && k > r);
+}
+
+// |x| as its bit pattern (orders like the value for non-negative doubles);
+// non-finite entries count as zero (the contraction expects finite data).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return (a >> 52) == 0x7ff ? 0ull : a;
+}
+
+// frexp exponent of the double with bit pattern a > 0 (a < 2^e)
+__device__ __forceinline__ int exp_of_bits(unsigned long long a) {
+    const int E = (int)(a >> 52);
+    if (E > 0) return E - 1022;
+    int ex;
+    frexp(__longlong_as_double((long long)a), &ex);   // subnormal
+    return ex;
+}
+
 // e[r] = exponent of max_k |X(r, k)| (frexp convention: max < 2^e), by
 // atomicMax over blocks that each cover 32 rows x a K range; rows that stay
-// all zero keep the sentinel value (< -1100) the caller stored.
+// all zero keep the sentinel value (< -1100) the caller stored.  Integer
+// compares of the bit patterns: no FP64 arithmetic.
 __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
-                              int64_t kper, int *e) {
-    __shared__ double red[8][33];
+                              int64_t kper, int tri, int *e) {
+    __shared__ unsigned long long red[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int64_t kb = (int64_t)blockIdx.y * kper;
     int64_t ke = kb + kper;
     if (ke > K) ke = K;
-    double mx = 0.0;
     if (sk == 1) {
         // K contiguous: lanes along k, warps over rows
         for (int rr = ty; rr < 32; rr += 8) {
             const int64_t r = r0 + rr;
-            double m = 0.0;
+            unsigned long long m = 0ull;
             if (r < R)
-                for (int64_t k = kb + tx; k < ke; k += 32) m = fmax(m, fabs(X[r * sr + k]));
+                for (int64_t k = kb + tx; k < ke; k += 32)
+                    if (!tri_zero(tri, r, k)) m = max(m, abs_bits(X[r * sr + k]));
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (tx == 0 && r < R && m > 0.0) {
-                int ex;
-                frexp(m, &ex);
-                atomicMax(&e[r], ex);
-            }
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (tx == 0 && r < R && m > 0ull) atomicMax(&e[r], exp_of_bits(m));
         }
         return;
     }
     // rows contiguous: lanes along rows, warps split the K range
     const int64_t r = r0 + tx;
+    unsigned long long mx = 0ull;
     if (r < R)
-        for (int64_t k = kb + ty; k < ke; k += 8) mx = fmax(mx, fabs(X[r + k * sk]));
+        for (int64_t k = kb + ty; k < ke; k += 8)
+            if (!tri_zero(tri, r, k)) mx = max(mx, abs_bits(X[r + k * sk]));
     red[ty][tx] = mx;
     __syncthreads();
     if (ty == 0 && r < R) {
-        double m = red[0][tx];
+        unsigned long long m = red[0][tx];
 #pragma unroll
-        for (int i = 1; i < 8; ++i) m = fmax(m, red[i][tx]);
-        if (m > 0.0) {
-            int ex;
-            frexp(m, &ex);
-            atomicMax(&e[r], ex);
-        }
+        for (int i = 1; i < 8; ++i) m = max(m, red[i][tx]);
+        if (m > 0ull) atomicMax(&e[r], exp_of_bits(m));
     }
 }
 
 // out[s][r * ldk + k] = slice s of X(r, k) 2^-e[r]; 32 x 32 tiles through
 // shared memory so reads follow X's contiguous axis and writes follow k.
+// Integer arithmetic on the bit pattern: v = round(|x| 2^(55 - e)) < 2^55 + 1
+// is split into 8 balanced base-128 digits q_s in [-64, 64] (digit s has
+// weight 2^(49 - 7 s)), so x = sign 2^(e - 55) sum_s q_s 2^(49 - 7 s) up to
+// 2^(e - 56); every q_s is exact in BF16.
 __global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
-                             const int *__restrict__ e, int fixed_e, __nv_bfloat16 *__restrict__ out, int64_t ldk,
-                             int64_t slice_stride) {
+                             int tri, const int *__restrict__ e, int fixed_e, __nv_bfloat16 *__restrict__ out,
+                             int64_t ldk, int64_t slice_stride) {
     __shared__ double tile[32][33];
     const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     for (int i = ty; i < 32; i += 8) {
         int64_t r, k;
         if (sk == 1) { r = r0 + i; k = k0 + tx; } else { r = r0 + tx; k = k0 + i; }
-        const double v = (r < R && k < K) ? X[r * sr + k * sk] : 0.0;
+        const double v = (r < R && k < K && !tri_zero(tri, r, k)) ? X[r * sr + k * sk] : 0.0;
         if (sk == 1) tile[i][tx] = v; else tile[tx][i] = v;   // tile[r - r0][k - k0]
     }
     __syncthreads();
@@ -329,23 +357,40 @@ __global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K,
         const int64_t r = r0 + i, k = k0 + tx;
         if (r >= R || k >= K) continue;
         const int er = e ? e[r] : fixed_e;
-        double t = er < -1100 ? 0.0 : ldexp(tile[i][tx], -er) * 64.0;   // exact: |t| < 64
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(tile[i][tx]);
+        const bool neg = (bits >> 63) != 0;
+        int E = (int)((bits >> 52) & 0x7ff);
+        unsigned long long M = bits & 0xfffffffffffffull;
+        if (E == 0x7ff) M = 0;               // non-finite: not representable, taken as zero
+        else if (E == 0) E = 1;              // subnormal: M 2^(1 - 1075)
+        else M |= 1ull << 52;                // |x| = M 2^(E - 1075)
+        long long v = 0;
+        const int sh = E - 1020 - er;        // v = M 2^sh; sh <= 2 since |x| < 2^er
+        if (er >= -1100 && M != 0) {
+            if (sh >= 0) v = (long long)(M << sh);
+            else if (sh > -63) v = (long long)((M >> (-sh)) + ((M >> (-sh - 1)) & 1ull));
+        }
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const double q = rint(t);                   // integer in [-64, 64]
-            out[s * slice_stride + r * ldk + k] = __double2bfloat16(q);
-            t = (t - q) * 128.0;                        // exact, |t| <= 64
+            const int w = 49 - 7 * s;
+            long long q;
+            if (w > 0) q = (v + (1ll << (w - 1))) >> w;   // balanced digit: |q| <= 64
+            else q = v;
+            v -= q << w;
+            const float qf = (float)(neg ? -q : q);
+            out[s * slice_stride + r * ldk + k] = __float2bfloat16_rn(qf);
         }
     }
 }
 
 __global__ void split_sum_kernel(const double *__restrict__ part, int S, int64_t M, int64_t N, double alpha,
-                                 double beta, double *C, int64_t ldc) {
+                                 double beta, double *C, int64_t ldc, int upper_only) {
     const int64_t total = M * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % M, j = e / M;
+        if (upper_only && i > j) continue;
         double sum = 0.0;
         for (int z = 0; z < S; ++z) sum += part[(int64_t)z * total + e];
-        const int64_t i = e % M, j = e / M;
         double out = alpha * sum;
         if (beta != 0.0) out = fma(beta, C[i + j * ldc], out);
         C[i + j * ldc] = out;
@@ -359,7 +404,7 @@ struct Slices {
 };
 
 cudaError_t slice_into(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, __nv_bfloat16 *q, int *e,
-                       int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s) {
+                       int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s, int tri = 0) {
     if (R <= 0 || K <= 0) return cudaSuccess;
     if (e) {
         count_launch();
@@ -371,21 +416,22 @@ cudaError_t slice_into(const double *X, int64_t R, int64_t K, int64_t sr, int64_
         if (ksplit > kmax) ksplit = kmax;
         if (ksplit < 1) ksplit = 1;
         const int64_t kper = (K + ksplit - 1) / ksplit;
-        rowexp_kernel<<<dim3((unsigned)rblocks, (unsigned)ksplit), 256, 0, s>>>(X, R, K, sr, sk, kper, e);
+        rowexp_kernel<<<dim3((unsigned)rblocks, (unsigned)ksplit), 256, 0, s>>>(X, R, K, sr, sk, kper, tri, e);
         EOD_CUDA_TRY(cudaGetLastError());
     }
     count_launch();
     dim3 grid((unsigned)((K + 31) / 32), (unsigned)((R + 31) / 32));
-    slice_kernel<<<grid, dim3(32, 8), 0, s>>>(X, R, K, sr, sk, e, fixed_e, q, ldk, slice_stride);
+    slice_kernel<<<grid, dim3(32, 8), 0, s>>>(X, R, K, sr, sk, tri, e, fixed_e, q, ldk, slice_stride);
     return cudaGetLastError();
 }
 
-cudaError_t make_slices(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, Slices &sl, cudaStream_t s) {
+cudaError_t make_slices(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, Slices &sl, cudaStream_t s,
+                        int tri = 0) {
     sl.R = R;
     sl.ldk = round_up(K, 8);
     EOD_CUDA_TRY(cudaMallocAsync((void **)&sl.q, sizeof(__nv_bfloat16) * (size_t)NS * R * sl.ldk, s));
     EOD_CUDA_TRY(cudaMallocAsync((void **)&sl.e, sizeof(int) * (size_t)R, s));
-    return slice_into(X, R, K, sr, sk, sl.q, sl.e, 0, sl.ldk, R * sl.ldk, s);
+    return slice_into(X, R, K, sr, sk, sl.q, sl.e, 0, sl.ldk, R * sl.ldk, s, tri);
 }
 
 void free_slices(Slices &sl, cudaStream_t s) {
@@ -432,6 +478,9 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
     p.errp = x.err_partials;
     p.ea_fixed = A.e_fixed;
     p.eb_fixed = B.e_fixed;
+    p.upper_only = x.upper_only ? 1 : 0;
+    p.a_tri = x.a_upper ? 1 : 0;
+    p.b_tri = x.b_upper ? 1 : 0;
     const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
     int64_t splits = 1;
     if (x.epilogue == EPI_STORE && tiles < kNumSMs) {
@@ -468,7 +517,7 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
     if (e == cudaSuccess && splits > 1) {
         count_launch();
         const int blocks = (int)std::min<int64_t>((M * N + 255) / 256, 4LL * kNumSMs * 8);
-        split_sum_kernel<<<blocks, 256, 0, s>>>(part, (int)splits, M, N, alpha, beta, C, ldc);
+        split_sum_kernel<<<blocks, 256, 0, s>>>(part, (int)splits, M, N, alpha, beta, C, ldc, p.upper_only);
         e = cudaGetLastError();
     }
     if (part) cudaFreeAsync(part, s);
@@ -484,9 +533,11 @@ cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double al
     if (M <= 0 || N <= 0) return cudaSuccess;
     Slices sa, sb;
     // op(A)(i, k): rows i, reduction k; op(B)(k, j) seen as rows j
-    cudaError_t e = make_slices(A, M, K, ta ? lda : 1, ta ? 1 : lda, sa, s);
-    const bool same = (A == B) && (ta != tb) && (lda == ldb) && (M == N);
-    if (e == cudaSuccess && !same) e = make_slices(B, N, K, tb ? 1 : ldb, tb ? ldb : 1, sb, s);
+    // a_upper / b_upper: op(A) / op(B) is upper triangular and its zero part
+    // is not read, as in the SIMT kernel
+    cudaError_t e = make_slices(A, M, K, ta ? lda : 1, ta ? 1 : lda, sa, s, x.a_upper ? 1 : 0);
+    const bool same = (A == B) && (ta != tb) && (lda == ldb) && (M == N) && !x.a_upper && !x.b_upper;
+    if (e == cudaSuccess && !same) e = make_slices(B, N, K, tb ? 1 : ldb, tb ? ldb : 1, sb, s, x.b_upper ? 2 : 0);
     const Slices &SB = same ? sa : sb;
     if (e == cudaSuccess) {
         OzOperand oa{sa.q, sa.e, 0, sa.ldk, (int64_t)M * sa.ldk};

@@ -134,3 +134,68 @@ def test_factorisation_emulated_matches_simt_and_oracle(eod, which, tmp_path):
     ref = oracle.eod_abe(w.A, float(em["tol"]), 1, k=int(em["k"]), seed=int(em["seed"]))
     assert int(em["rank"]) == ref["r"]
     assert abs(float(em["rel_err"]) - ref["rel_err"]) <= 1e-10
+
+
+def _tol(mode, A, B, K):
+    """Entrywise bound for C = A B.  SIMT DFMA: the usual componentwise FP64
+    bound.  Emulation: each row of A and column of B is sliced against its
+    own largest entry, so an entry's error is bounded by K 2^-48 max|A(i,:)|
+    max|B(:,j)| on top (8 slices of 7 bits, the pairs below 2^-56 dropped):
+    normwise per row and column, not relative to |A||B| where a triangular
+    column has a single term."""
+    t = 1e-13 * (A.abs() @ B.abs()) + 1e-300
+    if mode == 1:
+        t = t + K * 2.0 ** -48 * A.abs().amax(dim=1, keepdim=True) * B.abs().amax(dim=0, keepdim=True)
+    return t
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("M,N,K", [(300, 300, 300), (1000, 700, 700), (64, 2050, 2050)])
+def test_triangular_b_operand(eod, mode, M, N, K):
+    """op(B) upper triangular (the triangular solves of the core QR): the
+    emulation never reads the zero part (NaN there must not leak), the SIMT
+    kernel skips whole zero K ranges of it."""
+    g = torch.Generator(device="cuda").manual_seed(M + N + K + mode)
+    A = _cm(torch.randn((M, K), generator=g, device="cuda", dtype=torch.float64))
+    Bu = torch.triu(torch.randn((K, N), generator=g, device="cuda", dtype=torch.float64))
+    B = _cm(Bu.clone())
+    if mode == 1:
+        B[torch.tril(torch.ones_like(Bu, dtype=torch.bool), -1)] = float("nan")
+    C = _cm(torch.zeros((M, N), device="cuda", dtype=torch.float64))
+    _run(eod, mode | 64, False, False, A, B, C, 1.0, 0.0, M, N, K)
+    ref = A @ Bu
+    assert ((C - ref).abs() <= _tol(mode, A, Bu, K)).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_triangular_both_operands(eod, mode):
+    p = 777
+    g = torch.Generator(device="cuda").manual_seed(9 + mode)
+    Au = torch.triu(torch.randn((p, p), generator=g, device="cuda", dtype=torch.float64))
+    Bu = torch.triu(torch.randn((p, p), generator=g, device="cuda", dtype=torch.float64))
+    A, B = _cm(Au.clone()), _cm(Bu.clone())
+    if mode == 1:
+        low = torch.tril(torch.ones_like(Au, dtype=torch.bool), -1)
+        A[low] = float("nan")
+        B[low] = float("inf")
+    C = _cm(torch.zeros((p, p), device="cuda", dtype=torch.float64))
+    _run(eod, mode | 32 | 64, False, False, A, B, C, 1.0, 0.0, p, p, p)
+    ref = Au @ Bu
+    assert ((C - ref).abs() <= _tol(mode, Au, Bu, p)).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("p,K", [(300, 4000), (1100, 2048)])
+def test_upper_only_gram(eod, mode, p, K):
+    """G = W^T W with only the upper triangle wanted (split-K and single
+    pass); the emulation leaves every entry below the diagonal as it was."""
+    g = torch.Generator(device="cuda").manual_seed(p + K + mode)
+    W = _cm(torch.randn((K, p), generator=g, device="cuda", dtype=torch.float64))
+    C = _cm(torch.full((p, p), -7.0, device="cuda", dtype=torch.float64))
+    _run(eod, mode | 16, True, False, W, W, C, 1.0, 0.0, p, p, K)
+    ref = W.t() @ W
+    scale = W.abs().t() @ W.abs()
+    up = torch.triu(torch.ones((p, p), dtype=torch.bool, device="cuda"))
+    assert ((C - ref).abs()[up] <= 1e-13 * scale[up]).all()
+    if mode == 1:
+        assert (C[~up] == -7.0).all()
