@@ -256,7 +256,9 @@ int64_t gemm_err_ctas(int64_t M, int64_t N) { return ((M + BM - 1) / BM) * ((N +
 
 // Large FP64 products go to the tensor-core emulation (oz_gemm.cu) unless
 // EOD_FP64_GEMM=simt; products below 2^25 multiply-adds stay on the SIMT
-// kernel, whose launch and slicing overheads are smaller there.
+// kernel, whose launch and slicing overheads are smaller there.  A skinny
+// side (a few columns) does not exclude the emulation: the SIMT tiles waste
+// as much, and FP64 issue is what they are short of.
 bool fp64_use_emulated(int64_t M, int64_t N, int64_t K) {
     static const int mode = [] {
         const char *v = std::getenv("EOD_FP64_GEMM");
@@ -266,7 +268,7 @@ bool fp64_use_emulated(int64_t M, int64_t N, int64_t K) {
     }();
     if (mode == 0) return false;
     if (mode == 2) return M >= 1 && N >= 1 && K >= 1;
-    return (double)M * (double)N * (double)K >= 33554432.0 && M >= 128 && N >= 64 && K >= 128;
+    return (double)M * (double)N * (double)K >= 33554432.0 && K >= 8 && (M >= 128 || N >= 128);
 }
 
 template <typename TA, typename TB, typename TC, typename Acc>

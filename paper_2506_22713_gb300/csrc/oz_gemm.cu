@@ -42,7 +42,16 @@ constexpr int NG = 8;                 // weight groups g = s + t, pairs with s +
 constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int KCH = 7;                // K blocks per exact chunk (448)
 constexpr int UMMA_K = 16;            // K per tcgen05.mma kind::f16
-constexpr int ASTAGES = 4, BSTAGES = 2;
+#ifndef OZ_ASTAGES
+#define OZ_ASTAGES 4
+#endif
+#ifndef OZ_BSTAGES
+#define OZ_BSTAGES 2
+#endif
+#ifndef OZ_DRAIN_X4
+#define OZ_DRAIN_X4 1
+#endif
+constexpr int ASTAGES = OZ_ASTAGES, BSTAGES = OZ_BSTAGES;
 constexpr int A_TILE = BM * BK * 2;   // 16 KB
 constexpr int B_TILE = BN * BK * 2;   // 8 KB
 constexpr int B_SET = NS * B_TILE;    // 64 KB
@@ -140,39 +149,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
         if (!ok) { atomicExch(p.err_flag, 1); *abort_sh = 1; }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
+        // Fully unrolled over the 36 slice pairs and the 4 K steps of a
+        // block: descriptors are a base plus constant offsets (the 16-byte
+        // unit field advances by 2 per 32-byte K step and by 512 per 8 KB B
+        // slice), so the single issuing thread spends a few instructions per
+        // MMA.
         constexpr uint32_t idesc = idesc_bf16(BM, BN, false, false);
         int64_t ib = 0, ia = 0;
         bool ok = true;
-        bool init[NG];
         for (int64_t q = 0; q < nkb && ok; ++q) {
-            if (q % KCH == 0) {
+            const bool first = (q % KCH) == 0;
+            if (first) {
                 const int64_t chunk = q / KCH;
                 if (chunk > 0 && !mbar_wait(tmem_empty, (uint32_t)((chunk - 1) & 1))) { ok = false; break; }
                 tc_fence_after();
-#pragma unroll
-                for (int g = 0; g < NG; ++g) init[g] = false;
             }
             const int sb = (int)(ib % BSTAGES);
             if (!mbar_wait(&fullB[sb], (uint32_t)((ib / BSTAGES) & 1))) { ok = false; break; }
             tc_fence_after();
-            const uint32_t bbase = smem_u32(bbuf + sb * B_SET);
+            const uint64_t bd0 = sdesc(smem_u32(bbuf + sb * B_SET), 16, 1024);
+#pragma unroll
             for (int s = 0; s < NS; ++s) {
                 const int sa = (int)(ia % ASTAGES);
-                if (!mbar_wait(&fullA[sa], (uint32_t)((ia / ASTAGES) & 1))) { ok = false; break; }
-                if (*(volatile int *)abort_sh) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t abase = smem_u32(abuf + sa * A_TILE);
-                for (int t = 0; t + s < NG; ++t) {
-                    const int g = s + t;
+                if (ok && !mbar_wait(&fullA[sa], (uint32_t)((ia / ASTAGES) & 1))) ok = false;
+                if (ok && *(volatile int *)abort_sh) ok = false;
+                if (ok) {
+                    tc_fence_after();
+                    const uint64_t ad0 = sdesc(smem_u32(abuf + sa * A_TILE), 16, 1024);
 #pragma unroll
-                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-                        const uint64_t ad = sdesc(abase + kk * (UMMA_K * 2), 16, 1024);
-                        const uint64_t bd = sdesc(bbase + t * B_TILE + kk * (UMMA_K * 2), 16, 1024);
-                        umma_bf16(tmem + (uint32_t)(g * BN), ad, bd, idesc, (init[g] || kk > 0) ? 1u : 0u);
+                    for (int t = 0; t < NG; ++t) {
+                        if (s + t < NG) {
+#pragma unroll
+                            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                                // the first MMA of a group in a chunk overwrites it
+                                const uint32_t accum = (first && s == 0 && kk == 0) ? 0u : 1u;
+                                umma_bf16(tmem + (uint32_t)((s + t) * BN), ad0 + (uint64_t)(2 * kk),
+                                          bd0 + (uint64_t)(512 * t + 2 * kk), idesc, accum);
+                            }
+                        }
                     }
-                    init[g] = true;
+                    umma_commit(&emptyA[sa]);
                 }
-                umma_commit(&emptyA[sa]);
                 ++ia;
             }
             if (!ok) break;
@@ -201,6 +218,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
             ok = __all_sync(0xffffffffu, mbar_wait(tmem_full, (uint32_t)(c & 1)) ? 1 : 0) != 0;
             if (!ok || *(volatile int *)abort_sh) { ok = false; break; }
             tc_fence_after();
+#if OZ_DRAIN_X4
+            // 4 columns at a time: the 8 groups' loads are in flight together
+#pragma unroll
+            for (int cc = 0; cc < ECOLS; cc += 4) {
+                uint32_t r[NG][4];
+#pragma unroll
+                for (int g = 0; g < NG; ++g)
+                    tmem_ld4_nowait(tmem + ((uint32_t)(32 * qtr) << 16) + (uint32_t)(g * BN + c0 + cc), r[g]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    long long hi = 0, lo = 0;
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) {
+                        const long long iv = (long long)__float2int_rn(__uint_as_float(r[g][j]));   // exact: |v| <= 2^24
+                        if (g < 4) hi = hi * 128 + iv;
+                        else lo = lo * 128 + iv;
+                    }
+                    acc[cc + j] = fma((double)lo, w_lo, fma((double)hi, w_hi, acc[cc + j]));
+                }
+            }
+#else
 #pragma unroll
             for (int cc = 0; cc < ECOLS; cc += 8) {
                 long long hi[8], lo[8];
@@ -221,6 +260,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
                 for (int j = 0; j < 8; ++j)
                     acc[cc + j] = fma((double)lo[j], w_lo, fma((double)hi[j], w_hi, acc[cc + j]));
             }
+#endif
             tc_fence_before();
             mbar_arrive(tmem_empty);
         }
@@ -482,15 +522,17 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
     p.a_tri = x.a_upper ? 1 : 0;
     p.b_tri = x.b_upper ? 1 : 0;
     const int64_t tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    // K split until the grid covers the SMs, at least two K blocks per split
+    // (a split's exact chunks start at its own first block)
     int64_t splits = 1;
     if (x.epilogue == EPI_STORE && tiles < kNumSMs) {
         splits = (kNumSMs + tiles - 1) / tiles;
-        const int64_t chunks = (p.kblocks + KCH - 1) / KCH;
-        if (splits > chunks) splits = chunks;
+        const int64_t smax = p.kblocks / 2;
+        if (splits > smax) splits = smax;
         if (splits < 1) splits = 1;
     }
-    const int64_t chunks_per = ((p.kblocks + KCH - 1) / KCH + splits - 1) / splits;
-    p.kb_per_split = chunks_per * KCH;
+    p.kb_per_split = (p.kblocks + splits - 1) / splits;
+    if (p.kb_per_split < 1) p.kb_per_split = 1;
     splits = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;
     if (splits < 1) splits = 1;
     double *part = nullptr;
