@@ -263,6 +263,21 @@ EOD_API eod_status eod_abe_debug_tc_gemm(int32_t form, int64_t M, int64_t N, int
 EOD_API eod_status eod_abe_fro_norm_noalloc(const void *A, int64_t m, int64_t n, int64_t lda, int32_t dtype,
                                             double *norm_out, int32_t *nonfinite_out, void *stream);
 
+/* Test hook (no counterpart in the paper as an entry point; it is the
+ * factorisation behind Alg. 1 steps 5-11 and the CholQR of Alg. 2 steps 9-10):
+ * one leaf factorisation G + shift I = R^T R of a w x w SPD block (w <= 128,
+ * only G's upper triangle is read, column-major, device memory), computed as
+ * L D L^T.  With decide != 0 each pivot d_j = T(j,j)^2 is tested against eps2
+ * with the rounding bound delta_coef G(j,j) and the guard rho G(j,j), and the
+ * factorisation stops at the first pivot that is not kept.  Writes R (upper,
+ * zeros below, leading p x p) and, when Rinv is not null, R^{-1} (same ld);
+ * info[0] = p (columns factored), info[1] = 0 all kept / 1 below eps /
+ * 2 undecided / 3 not positive.  Returns after synchronising `stream`;
+ * EOD_EINVAL for w outside [1, 128] or short leading dimensions. */
+EOD_API eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w, int32_t decide, double eps2,
+                                      double delta_coef, double rho, double shift, double *R, double *Rinv,
+                                      int64_t ldr, int32_t *info, void *stream);
+
 /* Test hook (no counterpart in the paper): one FP64 GEMM C = alpha op(A)
  * op(B) + beta C on device matrices, column-major, op(X) = X^T when the
  * matching flag is nonzero; mode & 3 == 0 runs the SIMT DFMA kernel, 1 the

@@ -23,55 +23,90 @@
 namespace eod {
 namespace {
 
-// Pivot decision for column j (one thread): the rank test when `decide`,
-// else plain positivity.  Sets *go, and on acceptance S(j,j) = sqrt(d) and
-// *rinv = 1/sqrt(d); on rejection *p_out = j and *code.
-__device__ __forceinline__ void chol_pivot(double *S, int w, int j, const double *g0, int decide, double eps2,
-                                           double delta_coef, double rho, int *go, double *rinv, int *p_out,
-                                           int *code) {
+// Monotone integer key of a finite double (x < y  <=>  key(x) < key(y)):
+// the pivot decisions compare through these, on the integer units.
+__device__ __forceinline__ long long dkey(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : -(b & 0x7fffffffffffffffll);
+}
+
+// 1/d for finite d > 0 (normal): FP32 reciprocal of the mantissa as the
+// seed (exponent handled on the integer bits), then two Newton steps
+// r <- r + r (1 - d r) in FP64, each doubling the 23 correct bits.
+__device__ __forceinline__ double recip_pos(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int E = (int)(b >> 52);                                  // biased exponent, 1..2046
+    const unsigned int mf = 0x3f800000u | (unsigned int)((b >> 29) & 0x7fffffu);   // mantissa in [1, 2)
+    const float rf = __frcp_rn(__uint_as_float(mf));               // (0.5, 1]
+    const unsigned int rb = __float_as_uint(rf);
+    const long long re = (long long)((rb >> 23) & 0xff) - 127 + 1023 - (E - 1023);
+    if (re <= 0 || re >= 2047) return 1.0 / d;                     // 1/d subnormal or huge
+    double r = __longlong_as_double((re << 52) | ((long long)(rb & 0x7fffffu) << 29));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
+// Pivot decision for column j (one thread) on the integer keys: the rank test
+// when `decide` (thresholds precomputed per column), else positivity.  A
+// non-finite pivot is undecided (rank test) or a failure.  On acceptance
+// *rd = 1/d.
+__device__ __forceinline__ void ldl_pivot(const double *S, int w, int j, const long long *klo, const long long *khi,
+                                          const long long *krg, int decide, double *dv, int *go, double *rd,
+                                          int *p_out, int *code) {
     const double d = S[j + j * w];
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+    const bool finite = ((bits >> 52) & 0x7ff) != 0x7ff;
+    const long long kd = dkey(d);
     int keep;
-    if (decide) {
-        const double delta = delta_coef * g0[j];
-        if (d < eps2 - delta) { keep = 0; *code = CHOL_BELOW; }
-        else if (d > eps2 + delta && d > rho * g0[j] && isfinite(d)) keep = 1;
+    if (!finite) {
+        keep = 0;
+        *code = decide ? CHOL_UNCERTAIN : CHOL_FAIL;
+    } else if (decide) {
+        if (kd < klo[j]) { keep = 0; *code = CHOL_BELOW; }
+        else if (kd > khi[j] && kd > krg[j]) keep = 1;
         else { keep = 0; *code = CHOL_UNCERTAIN; }
     } else {
-        keep = (d > 0.0 && isfinite(d)) ? 1 : 0;
+        keep = kd > 0 ? 1 : 0;
         if (!keep) *code = CHOL_FAIL;
     }
     if (keep) {
-        const double ri = rsqrt(d);
-        S[j + j * w] = d * ri;
-        *rinv = ri;
+        dv[j] = d;
+        *rd = ((bits >> 52) & 0x7ff) != 0 ? recip_pos(d) : 1.0 / d;   // subnormal: plain division
     } else {
         *p_out = j;
     }
     *go = keep;
 }
 
-// One CTA of 256 threads.  L = R^T is built in shared memory (lower
-// triangle, column-major: column j of L is row j of R).  Step j, after pivot
-// j is accepted:
-//   (A) every thread takes rows i > j: L(i,j) = S(i,j)/L(j,j) and the
-//       update of column j+1, S(i,j+1) -= L(i,j) L(j+1,j);
-//   (B) warp 0 decides pivot j+1 while warps 1-7 apply L(:,j) to the rest
-//       of the trailing triangle (columns > j+1), whose entries are spread
-//       evenly over the threads through a table of (row, column) pairs
-//       ordered by column from the right, so the entries of columns > c form
-//       a prefix of it.
-// Every entry sees the same operations in the same order as the textbook
-// right-looking loop, so the factor is identical to it.
+// One CTA of 256 threads: G + shift I = L D L^T (unit lower L, no square
+// roots on the critical path), R = D^{1/2} L^T, and optionally
+// R^{-1} = L^{-T} D^{-1/2}.  Step j, once pivot j is accepted:
+//   (A) every thread takes rows i > j: keeps u_i = S(i,j), stores
+//       L(i,j) = u_i / d_j, and updates column j+1: S(i,j+1) -= L(i,j) u_{j+1};
+//   (B) warp 0 decides pivot j+1 (integer compares, reciprocal by Newton)
+//       while warps 1-7 apply S(ii,ll) -= L(ii,j) u_ll to the rest of the
+//       trailing triangle, spread evenly over the threads through a table of
+//       (row, column) pairs ordered by column from the right (the entries of
+//       columns > c form a prefix of it).
+// The rank test reads the pivots d_j = T(j,j)^2 exactly as the Cholesky form
+// would; R differs from a square-root Cholesky only by rounding.
 __global__ void __launch_bounds__(256) chol_small_kernel(const double *__restrict__ G, int64_t ldg, int w,
                                                          int decide, double eps2, double delta_coef, double rho,
-                                                         double shift, double *__restrict__ R, int64_t ldr,
-                                                         int *info) {
+                                                         double shift, double *__restrict__ R,
+                                                         double *__restrict__ Rinv, int64_t ldr, int *info) {
     extern __shared__ double sh[];
     double *S = sh;                                    // w x w, lower triangle
-    double *g0 = sh + w * w;                           // original diagonal
-    uint16_t *pairs = (uint16_t *)(g0 + w);            // w (w - 1) / 2 entries: row | column << 8
+    double *u = S + w * w;                             // unscaled column of the step
+    double *dv = u + w;                                // pivots d_j
+    double *sq = dv + w;                               // sqrt(d_j), then 1/sqrt(d_j)
+    long long *klo = (long long *)(sq + w);            // keys of eps^2 - delta_j, eps^2 + delta_j, rho G(j,j)
+    long long *khi = klo + w;
+    long long *krg = khi + w;
+    uint16_t *pairs = (uint16_t *)(krg + w);           // w (w - 1) / 2 entries: row | column << 8
     __shared__ int p_sh, code_sh, go_sh;
-    __shared__ double rinv_sh;
+    __shared__ double rd_sh;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
 
@@ -79,7 +114,15 @@ __global__ void __launch_bounds__(256) chol_small_kernel(const double *__restric
     for (int c = ty; c < w; c += 16)
         for (int i = tx; i < w; i += 16)
             S[i + c * w] = (i >= c) ? G[c + (int64_t)i * ldg] + (i == c ? shift : 0.0) : 0.0;
-    for (int j = tid; j < w; j += blockDim.x) g0[j] = G[j + (int64_t)j * ldg] + shift;
+    if (decide) {
+        for (int j = tid; j < w; j += blockDim.x) {
+            const double g0 = G[j + (int64_t)j * ldg];
+            const double delta = delta_coef * g0;
+            klo[j] = dkey(eps2 - delta);
+            khi[j] = dkey(eps2 + delta);
+            krg[j] = dkey(rho * g0);
+        }
+    }
     const int npairs = w * (w - 1) / 2;
     for (int e = tid; e < npairs; e += blockDim.x) {
         // column ll = w - 1 - c holds c + 1 entries; columns w-1 .. ll hold (c+1)(c+2)/2
@@ -94,86 +137,64 @@ __global__ void __launch_bounds__(256) chol_small_kernel(const double *__restric
         code_sh = CHOL_ALL;
     }
     __syncthreads();
-    if (tid == 0) chol_pivot(S, w, 0, g0, decide, eps2, delta_coef, rho, &go_sh, &rinv_sh, &p_sh, &code_sh);
+    if (tid == 0) ldl_pivot(S, w, 0, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh);
     __syncthreads();
 
     for (int j = 0; j < w; ++j) {
         if (!go_sh) break;
-        const double rinv = rinv_sh;
+        const double rd = rd_sh;
         const bool next = j + 1 < w;
-        // (A) scale column j (rows > j; row j+1 is stored in (B), after every
-        // thread has read it) and update column j+1
-        const double lj1 = next ? S[(j + 1) + j * w] * rinv : 0.0;
+        const double u1 = next ? S[(j + 1) + j * w] : 0.0;   // row j+1 is scaled in (B)
         for (int i = j + 1 + tid; i < w; i += blockDim.x) {
-            const double lij = S[i + j * w] * rinv;
+            const double ui = S[i + j * w];
+            const double lij = ui * rd;
+            u[i] = ui;
             if (i > j + 1) S[i + j * w] = lij;
-            S[i + (j + 1) * w] = fma(-lij, lj1, S[i + (j + 1) * w]);
+            S[i + (j + 1) * w] = fma(-lij, u1, S[i + (j + 1) * w]);
         }
         __syncthreads();
         if (!next) break;
-        // (B) pivot j+1 on warp 0; columns > j+1 on warps 1-7
         if (tid == 0) {
-            chol_pivot(S, w, j + 1, g0, decide, eps2, delta_coef, rho, &go_sh, &rinv_sh, &p_sh, &code_sh);
+            ldl_pivot(S, w, j + 1, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh);
         } else if (tid >= 32) {
-            if (tid == 32) S[(j + 1) + j * w] = lj1;
+            if (tid == 32) S[(j + 1) + j * w] = u1 * rd;
             const int cnt = (w - 2 - j) * (w - 1 - j) / 2;
             for (int e = tid - 32; e < cnt; e += blockDim.x - 32) {
                 const int pr = pairs[e];
                 const int ii = pr & 0xff, ll = pr >> 8;
-                S[ii + ll * w] = fma(-S[ii + j * w], S[ll + j * w], S[ii + ll * w]);
+                S[ii + ll * w] = fma(-S[ii + j * w], u[ll], S[ii + ll * w]);
             }
         }
         __syncthreads();
     }
     const int p = p_sh;
-    for (int c = ty; c < p; c += 16)
-        for (int i = tx; i < p; i += 16) R[i + (int64_t)c * ldr] = (i <= c) ? S[c + i * w] : 0.0;
-    if (tid == 0) { info[0] = p; info[1] = code_sh; }
-}
-
-// X = R^{-1} for upper-triangular R (p x p, ld ldr, p <= 32 PER), one warp
-// per column: column c solves R x = e_c from the bottom, x_j = b_j / R(j,j),
-// then b_i -= x_j R(i,j) for i < j, with b spread over the lanes.
-template <int PER>
-__global__ void __launch_bounds__(128) tri_inverse_kernel(const double *__restrict__ R, int64_t ldr, int p,
-                                                          const int *p_dev, double *__restrict__ X,
-                                                          int64_t ldx) {
-    __shared__ double rd[32 * PER];
-    if (p_dev) p = *p_dev;
-    for (int j = threadIdx.x; j < p; j += blockDim.x) rd[j] = 1.0 / R[j + (int64_t)j * ldr];
+    for (int j = tid; j < p; j += blockDim.x) sq[j] = sqrt(dv[j]);
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (c >= p) return;
-    // lane holds b_i for i = lane + 32 t
-    const int tmax = c >> 5;
-    double b[PER];
-#pragma unroll
-    for (int t = 0; t < PER; ++t) b[t] = (lane + 32 * t == c) ? 1.0 : 0.0;
-    for (int j = c; j >= 0; --j) {
-        const int owner = j & 31, slot = j >> 5;
-        double bj = 0.0;
-#pragma unroll
-        for (int t = 0; t < PER; ++t)
-            if (t == slot) bj = b[t];
-        bj = __shfl_sync(0xffffffffu, bj, owner);
-        const double xj = bj * rd[j];
-        if (lane == owner) {
-#pragma unroll
-            for (int t = 0; t < PER; ++t)
-                if (t == slot) b[t] = xj;
+    // R(i, c) = sqrt(d_i) L(c, i) for i < c, sqrt(d_i) on the diagonal
+    for (int c = ty; c < p; c += 16)
+        for (int i = tx; i < p; i += 16)
+            R[i + (int64_t)c * ldr] = (i < c) ? sq[i] * S[c + i * w] : (i == c ? sq[i] : 0.0);
+    if (tid == 0) { info[0] = p; info[1] = code_sh; }
+    if (!Rinv) return;
+    __syncthreads();
+    for (int j = tid; j < p; j += blockDim.x) sq[j] = 1.0 / sq[j];
+    // Z = L^{-1} in place of L (strictly lower part): at step k the entries
+    // (i > k, c < k) take Z(i,c) -= L(i,k) Z(k,c), then column k becomes
+    // Z(i,k) = -L(i,k) (its first term; later steps add the rest)
+    for (int k = 0; k < p; ++k) {
+        const int rows = p - 1 - k, cnt = rows * k;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const int i = k + 1 + e % rows, c = e / rows;   // i fastest: conflict-free column accesses
+            S[i + c * w] = fma(-S[i + k * w], S[k + c * w], S[i + c * w]);
         }
-#pragma unroll
-        for (int t = 0; t < PER; ++t) {
-            const int i = lane + 32 * t;
-            if (t <= tmax && i < j) b[t] = fma(-xj, R[i + (int64_t)j * ldr], b[t]);
-        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < p; i += blockDim.x) S[i + k * w] = -S[i + k * w];
+        __syncthreads();
     }
-#pragma unroll
-    for (int t = 0; t < PER; ++t) {
-        const int i = lane + 32 * t;
-        if (i < p) X[i + (int64_t)c * ldx] = (i <= c) ? b[t] : 0.0;
-    }
+    // R^{-1}(i, c) = Z(c, i) / sqrt(d_c) for i < c, 1/sqrt(d_c) on the diagonal
+    for (int c = ty; c < p; c += 16)
+        for (int i = tx; i < p; i += 16)
+            Rinv[i + (int64_t)c * ldr] = (i < c) ? S[c + i * w] * sq[c] : (i == c ? sq[c] : 0.0);
 }
 
 __global__ void tdiag_kernel(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
@@ -197,30 +218,14 @@ cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double e
                        double rho, double shift, double *R, double *Rinv, int64_t ldr, int *info,
                        cudaStream_t s) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * ((size_t)w * w + (size_t)w) + sizeof(uint16_t) * (size_t)(w * (w - 1) / 2);
-    EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)(sizeof(double) * (128 * 128 + 128) + sizeof(uint16_t) * 8128)));
-    {
-        ProfScope prof(PROF_CHOL, (double)w * w * w / 3.0, sizeof(double) * 2.0 * w * w, s);
-        count_launch();
-        chol_small_kernel<<<1, 256, smem, s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R, ldr, info);
-        EOD_CUDA_TRY(cudaGetLastError());
-    }
-    if (Rinv) {
-        // the factored order p is read on the device (info[0])
-        ProfScope prof(PROF_CHOL, (double)w * w * w / 3.0, sizeof(double) * 2.0 * w * w, s);
-        count_launch();
-        tri_inverse_kernel<4><<<(w + 3) / 4, 128, 0, s>>>(R, ldr, w, info, Rinv, ldr);
-        EOD_CUDA_TRY(cudaGetLastError());
-    }
-    return cudaSuccess;
-}
-
-cudaError_t tri_inverse(const double *R, int64_t ldr, int p, double *X, int64_t ldx, cudaStream_t s) {
-    if (p < 1 || p > 256) return cudaErrorInvalidValue;
-    ProfScope prof(PROF_CHOL, (double)p * p * p / 3.0, sizeof(double) * 2.0 * p * p, s);
+    auto bytes = [](int n) {
+        return sizeof(double) * ((size_t)n * n + 4 * (size_t)n) + sizeof(long long) * 3 * (size_t)n +
+               sizeof(uint16_t) * (size_t)(n * (n - 1) / 2);
+    };
+    EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)bytes(128)));
+    ProfScope prof(PROF_CHOL, (double)w * w * w * (Rinv ? 2.0 : 1.0) / 3.0, sizeof(double) * 3.0 * w * w, s);
     count_launch();
-    if (p <= 128) tri_inverse_kernel<4><<<(p + 3) / 4, 128, 0, s>>>(R, ldr, p, nullptr, X, ldx);
-    else tri_inverse_kernel<8><<<(p + 3) / 4, 128, 0, s>>>(R, ldr, p, nullptr, X, ldx);
+    chol_small_kernel<<<1, 256, bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R, Rinv, ldr, info);
     return cudaGetLastError();
 }
 
@@ -238,3 +243,21 @@ cudaError_t trace_sum(const double *G, int64_t ldg, int64_t p, double *out, cuda
 }
 
 }  // namespace eod
+
+// ---------------------------------------------------------------------------
+// Test hook: one leaf factorisation (see the header).
+// ---------------------------------------------------------------------------
+extern "C" eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w, int32_t decide, double eps2,
+                                         double delta_coef, double rho, double shift, double *R, double *Rinv,
+                                         int64_t ldr, int32_t *info, void *stream) {
+    using namespace eod;
+    if (!G || !R || !info || w < 1 || w > 128 || ldg < w || ldr < w) return EOD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = chol_small(G, ldg, w, decide ? 1 : 0, eps2, delta_coef, rho, shift, R, Rinv, ldr, info, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return EOD_ECUDA;
+    }
+    return EOD_OK;
+}

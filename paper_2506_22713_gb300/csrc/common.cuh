@@ -228,17 +228,15 @@ cudaError_t gram_tiled_f32(const float *W, int64_t rows, int64_t p, int64_t ldw,
 // --------------------------------------------------------------------------
 enum CholCode { CHOL_ALL = 0, CHOL_BELOW = 1, CHOL_UNCERTAIN = 2, CHOL_FAIL = 3 };
 
-// Cholesky G = R^T R of the w x w matrix G (upper triangle read, FP64) with
-// the rank decision of Alg. 1 steps 6-11 when decide != 0:
+// Cholesky G = R^T R of the w x w matrix G (upper triangle read, FP64; one
+// CTA, computed as L D L^T) with the rank decision of Alg. 1 steps 6-11 when
+// decide != 0:
 //   info[0] = p (leading columns factored), info[1] = CholCode,
 // R (p x p upper, ld ldr) and its inverse Rinv (ld ldr); the original
 // diagonal of G is used for the rounding margin.
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2,
                        double delta_coef, double rho, double shift, double *R,
                        double *Rinv, int64_t ldr, int *info, cudaStream_t s);
-// X (p x p, ld ldx) = R^{-1} for upper-triangular R (p <= 256), zeros below
-// the diagonal
-cudaError_t tri_inverse(const double *R, int64_t ldr, int p, double *X, int64_t ldx, cudaStream_t s);
 // tdiag[j] = |R1(j,j) * R2(j,j)|, j < p
 cudaError_t tdiag_product(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
                           double *tdiag, cudaStream_t s);

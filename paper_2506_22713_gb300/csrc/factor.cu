@@ -88,7 +88,8 @@ template <> struct Traits<float> { static constexpr int dtype = EOD_F32; static 
 // ---------------------------------------------------------------------------
 template <typename T>
 struct CoreWork {
-    double *G = nullptr, *R = nullptr, *Rp = nullptr, *Inv = nullptr, *RiD = nullptr, *trace = nullptr;
+    double *G = nullptr, *R = nullptr, *Rp = nullptr, *Inv = nullptr, *RiD = nullptr, *RiT = nullptr,
+           *trace = nullptr;
     T *InvT = nullptr, *Tmp = nullptr;
     int *info = nullptr;
     int64_t pcap = 0, rows_cap = 0;
@@ -118,6 +119,35 @@ static eod_status chol_panel_leaves(CoreWork<T> &w, int64_t p, int64_t j0, int64
     return EOD_OK;
 }
 
+// RiJ (jb x jb, ld kPB) = R_JJ^{-1} for the diagonal panel at j0, from its
+// leaves' inverses by doubling: inv([A B; 0 C]) = [A^-1, -A^-1 B C^-1; 0, C^-1].
+template <typename T>
+static eod_status panel_inverse(CoreWork<T> &w, int64_t p, int64_t j0, int64_t jb, const double *Rout, double *RiJ,
+                                Scratch *ws, cudaStream_t s) {
+    GemmExtra au, bu;
+    au.a_upper = true;
+    bu.b_upper = true;
+    EOD_CU(fill_zero<double>(RiJ, jb, jb, kPB, s));
+    for (int64_t l0 = 0; l0 < jb; l0 += kNB) {
+        const int64_t lb = std::min<int64_t>(kNB, jb - l0);
+        EOD_CU(copy_matrix<double, double>(w.Inv + ((j0 + l0) / kNB) * kNB * kNB, kNB, RiJ + l0 + l0 * kPB, kPB, lb,
+                                           lb, false, s));
+    }
+    for (int64_t h = kNB; h < jb; h *= 2) {
+        for (int64_t a0 = 0; a0 + h < jb; a0 += 2 * h) {
+            const int64_t b0 = a0 + h, bl = std::min<int64_t>(h, jb - b0);
+            // T = A^-1 B;  RiJ(a, b) = -T C^-1
+            EOD_CU((gemm<double, double, double, double>(false, false, h, bl, h, 1.0, RiJ + a0 + a0 * kPB, kPB,
+                                                          Rout + (j0 + a0) + (j0 + b0) * p, p, 0.0, w.RiT, h, au,
+                                                          ws, s)));
+            EOD_CU((gemm<double, double, double, double>(false, false, h, bl, bl, -1.0, w.RiT, h,
+                                                          RiJ + b0 + b0 * kPB, kPB, 0.0, RiJ + a0 + b0 * kPB, kPB, bu,
+                                                          ws, s)));
+        }
+    }
+    return EOD_OK;
+}
+
 template <typename T>
 static eod_status chol_panels(CoreWork<T> &w, int64_t p, double shift, HostMirror &hm, Scratch *ws,
                               cudaStream_t s, double *Rout) {
@@ -128,7 +158,7 @@ static eod_status chol_panels(CoreWork<T> &w, int64_t p, double shift, HostMirro
         const int64_t pe = std::min<int64_t>(p, j0 + kPB), jb = pe - j0;
         double *RiJ = w.RiD + (j0 / kPB) * kPB * kPB;   // ld kPB
         EOD_TRY(chol_panel_leaves(w, p, j0, pe, shift, ws, s, Rout));
-        EOD_CU(tri_inverse(Rout + j0 + j0 * p, p, (int)jb, RiJ, kPB, s));
+        EOD_TRY(panel_inverse(w, p, j0, jb, Rout, RiJ, ws, s));
         if (pe < p) {
             // R(J, pe:p) = R_JJ^{-T} G(J, pe:p);  G(pe:p, pe:p) -= R(J, pe:p)^T R(J, pe:p)
             EOD_CU((gemm<double, double, double, double>(true, false, jb, p - pe, jb, 1.0, RiJ, kPB,
@@ -576,6 +606,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(ar.get(&cw.Rp, (size_t)kNB * kNB + (size_t)r * r));
     EOD_TRY(ar.get(&cw.Inv, (size_t)nblk * kNB * kNB));
     EOD_TRY(ar.get(&cw.RiD, (size_t)((r + kPB - 1) / kPB) * kPB * kPB));
+    EOD_TRY(ar.get(&cw.RiT, (size_t)kPB * kPB));
     EOD_TRY(ar.get(&cw.trace, 1));
     EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kPB) * kPB));
     EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kPB));

@@ -1,0 +1,96 @@
+"""The one-CTA leaf factorisation behind CholQR (Alg. 1 steps 5-11, Alg. 2
+steps 9-10) against FP64 LAPACK on the host: R^T R = G + shift I, R^{-1} R = I,
+and the three outcomes of the rank test on pivots placed around eps^2."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def eod():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2506_22713_gb300 as eod
+    return eod
+
+
+def _run(eod, G, decide=0, eps2=0.0, coef=0.0, rho=0.0, shift=0.0, inverse=True):
+    w = G.shape[0]
+    Gd = torch.from_numpy(np.asfortranarray(G)).cuda()
+    R = torch.full((w, w), float("nan"), dtype=torch.float64, device="cuda").t()
+    Ri = torch.full((w, w), float("nan"), dtype=torch.float64, device="cuda").t() if inverse else None
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    P = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    st = eod.eod_abe_debug_chol(P(Gd), w, w, decide, eps2, coef, rho, shift, P(R), P(Ri), w, P(info),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == eod.EOD_OK
+    p, code = info.tolist()
+    Rn = R.cpu().numpy()[:p, :p]
+    Rin = Ri.cpu().numpy()[:p, :p] if inverse else None
+    return p, code, Rn, Rin
+
+
+def _spd(w, cond, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((w, w)))
+    s = np.geomspace(1.0, 1.0 / cond, w)
+    return (Q * s) @ Q.T
+
+
+@pytest.mark.parametrize("w", [1, 2, 17, 63, 64, 65, 100, 128])
+@pytest.mark.parametrize("cond", [1e2, 1e8])
+def test_factor_and_inverse(eod, w, cond):
+    G = _spd(w, cond, w)
+    p, code, R, Ri = _run(eod, G)
+    assert (p, code) == (w, 0)
+    assert np.all(np.diag(R) > 0) and np.allclose(np.tril(R, -1), 0.0)
+    # backward error of a Cholesky factorisation: O(w u) ||G||
+    assert np.linalg.norm(R.T @ R - G) <= 20 * w * U64 * np.linalg.norm(G)
+    Rref = np.linalg.cholesky(G).T
+    assert np.linalg.norm(R - Rref) <= 50 * w * U64 * cond * np.linalg.norm(Rref)
+    assert np.allclose(np.tril(Ri, -1), 0.0)
+    assert np.linalg.norm(Ri @ R - np.eye(w)) <= 50 * w * U64 * np.sqrt(cond) * np.sqrt(cond)
+
+
+def test_shift_is_added_to_the_diagonal(eod):
+    G = _spd(40, 1e3, 5)
+    p, code, R, _ = _run(eod, G, shift=0.25, inverse=False)
+    assert (p, code) == (40, 0)
+    assert np.linalg.norm(R.T @ R - (G + 0.25 * np.eye(40))) <= 1e-13 * np.linalg.norm(G)
+
+
+def test_rank_test_outcomes(eod):
+    """Pivots d_j = T(j,j)^2 of a diagonal Gram: kept while above
+    eps^2 + delta, stop below eps^2 - delta (code 1), undecided inside the
+    band (code 2), and the rho guard."""
+    coef = 64.0 * (16 + np.sqrt(1000.0)) * U64
+    eps2 = 1e-6
+    d = np.array([4.0, 1.0, 2e-6, 1e-9, 5.0])
+    p, code, R, _ = _run(eod, np.diag(d), decide=1, eps2=eps2, coef=coef, rho=1e-10, inverse=False)
+    assert (p, code) == (3, 1)
+    assert np.allclose(np.diag(R), np.sqrt(d[:3]), rtol=1e-15)
+    # inside the rounding band around eps^2: undecided
+    d2 = np.array([4.0, eps2 * (1 + 1e-13), 5.0])
+    p, code, _, _ = _run(eod, np.diag(d2), decide=1, eps2=eps2, coef=coef, rho=1e-10, inverse=False)
+    assert (p, code) == (1, 2)
+    # pivot above eps^2 + delta but below rho G(j,j) (nearly dependent
+    # columns): undecided
+    b = np.sqrt(1.0 - 1e-12)
+    G3 = np.array([[1.0, b, 0.0], [b, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    p, code, _, _ = _run(eod, G3, decide=1, eps2=1e-14, coef=coef, rho=1e-10, inverse=False)
+    assert (p, code) == (1, 2)
+    p, code, _, _ = _run(eod, G3, decide=1, eps2=1e-14, coef=coef, rho=1e-13, inverse=False)
+    assert (p, code) == (3, 0)
+
+
+def test_not_positive_definite_stops(eod):
+    G = _spd(30, 10.0, 7)
+    G[12, 12] = -1.0
+    p, code, _, _ = _run(eod, G, inverse=False)
+    assert code == 3 and p <= 12
