@@ -185,6 +185,9 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
 cudaError_t oz_slice(const double *X, int64_t rows, int64_t K, int64_t sr, int64_t sk, void *q, int *e,
                      int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s);
 constexpr int kOzSlices = 8;
+// largest K the emulation takes with the fused squared-error epilogue (which
+// cannot split K)
+constexpr int64_t kOzErrMaxK = 7168;
 
 // whether gemm<double,...> sends an M x N x K product to oz_gemm
 bool fp64_use_emulated(int64_t M, int64_t N, int64_t K);

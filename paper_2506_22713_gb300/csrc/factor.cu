@@ -579,7 +579,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
             ee.ref = A;
             ee.ldref = lda;
             ee.err_partials = part;
-            if (oz.on && fp64_use_emulated(m, n, r)) {
+            if (oz.on && fp64_use_emulated(m, n, r) && r <= kOzErrMaxK) {
                 // B operand (C^T)^T: rows = rows of C^T (n), K = r
                 const int64_t r8 = round_up8(r);
                 uint16_t *cts;

@@ -278,7 +278,7 @@ cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
 {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (std::is_same<TA, double>::value && std::is_same<TB, double>::value && std::is_same<TC, double>::value &&
-        ws && ws->err_flag && K > 0 && fp64_use_emulated(M, N, K))
+        ws && ws->err_flag && K > 0 && fp64_use_emulated(M, N, K) && (x.epilogue != EPI_ERR || K <= kOzErrMaxK))
         return oz_gemm(ta, tb, M, N, K, alpha, (const double *)A, lda, (const double *)B, ldb, beta, (double *)C,
                        ldc, x, ws->err_flag, s);
     if (!ta && !tb) return launch<TA, TB, TC, Acc, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);

@@ -41,15 +41,14 @@ constexpr int NS = kOzSlices;         // slices per operand (8)
 constexpr int NG = 8;                 // weight groups g = s + t, pairs with s + t <= 7
 constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int KCH = 7;                // K blocks per exact chunk (448)
+constexpr int kOzMaxChunks = 16;      // chunks one CTA accumulates in int64
+static_assert(kOzMaxChunks * KCH * BK == kOzErrMaxK, "fused-error K limit");
 constexpr int UMMA_K = 16;            // K per tcgen05.mma kind::f16
 #ifndef OZ_ASTAGES
 #define OZ_ASTAGES 4
 #endif
 #ifndef OZ_BSTAGES
 #define OZ_BSTAGES 2
-#endif
-#ifndef OZ_DRAIN_X4
-#define OZ_DRAIN_X4 1
 #endif
 constexpr int ASTAGES = OZ_ASTAGES, BSTAGES = OZ_BSTAGES;
 constexpr int A_TILE = BM * BK * 2;   // 16 KB
@@ -207,18 +206,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
         const int qtr = warp & 3;                 // TMEM lane quarter this warp may read
         const int c0 = ((warp - 2) >> 2) * ECOLS; // its half of the 64 columns
         const int64_t row = m0 + 32 * qtr + lane;
-        double acc[ECOLS];
+        // Per chunk the eight FP32 group sums (exact integers) merge into one
+        // int64 in units of 2^-50 of the row x column scale:
+        //   hi = groups 0-3 in base 128 (unit 2^-33), lo = groups 4-7 (unit 2^-61),
+        //   c  = hi 2^17 + round(lo 2^-11);
+        // |hi| < 2^41.9 (|v_g| <= (g+1) 2^12 448), so |c| < 2^58.9 and up to
+        // kOzMaxChunks = 16 chunks (the host splits K to respect that)
+        // accumulate without overflow, rounding 2^-51 of the scale per chunk,
+        // with no FP64 instruction in the drain.
+        long long acc[ECOLS];
 #pragma unroll
-        for (int j = 0; j < ECOLS; ++j) acc[j] = 0.0;
+        for (int j = 0; j < ECOLS; ++j) acc[j] = 0;
         bool ok = true;
-        // weights of the merged groups 0-3 and 4-7: 2^(-12 - 7*3), 2^(-12 - 7*7)
-        const double w_hi = __longlong_as_double((long long)(1023 - 33) << 52);
-        const double w_lo = __longlong_as_double((long long)(1023 - 61) << 52);
         for (int64_t c = 0; c < nchunks; ++c) {
             ok = __all_sync(0xffffffffu, mbar_wait(tmem_full, (uint32_t)(c & 1)) ? 1 : 0) != 0;
             if (!ok || *(volatile int *)abort_sh) { ok = false; break; }
             tc_fence_after();
-#if OZ_DRAIN_X4
             // 4 columns at a time: the 8 groups' loads are in flight together
 #pragma unroll
             for (int cc = 0; cc < ECOLS; cc += 4) {
@@ -236,31 +239,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
                         if (g < 4) hi = hi * 128 + iv;
                         else lo = lo * 128 + iv;
                     }
-                    acc[cc + j] = fma((double)lo, w_lo, fma((double)hi, w_hi, acc[cc + j]));
+                    acc[cc + j] += hi * 131072 + ((lo + (1ll << 10)) >> 11);
                 }
             }
-#else
-#pragma unroll
-            for (int cc = 0; cc < ECOLS; cc += 8) {
-                long long hi[8], lo[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) { hi[j] = 0; lo[j] = 0; }
-#pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    float v[8];
-                    tmem_ld8(tmem + ((uint32_t)(32 * qtr) << 16) + (uint32_t)(g * BN + c0 + cc), v);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const long long iv = (long long)__float2int_rn(v[j]);   // exact: |v| <= 2^24
-                        if (g < 4) hi[j] = hi[j] * 128 + iv;
-                        else lo[j] = lo[j] * 128 + iv;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    acc[cc + j] = fma((double)lo[j], w_lo, fma((double)hi[j], w_hi, acc[cc + j]));
-            }
-#endif
             tc_fence_before();
             mbar_arrive(tmem_empty);
         }
@@ -272,7 +253,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
             for (int j = 0; j < ECOLS; ++j) {
                 const int64_t col = n0 + c0 + j;
                 if (col < p.N && !(p.upper_only && row > col)) {
-                    const double val = ldexp(acc[j], ei + (p.eb ? max(p.eb[col], -1100) : p.eb_fixed));
+                    const double val =
+                        ldexp((double)acc[j], ei + (p.eb ? max(p.eb[col], -1100) : p.eb_fixed) - 50);
                     if (EPI == EPI_STORE) {
                         if (p.split_stride > 0) {
                             p.C[(int64_t)blockIdx.z * p.split_stride + row + col * p.M] = val;
@@ -531,6 +513,10 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
         if (splits > smax) splits = smax;
         if (splits < 1) splits = 1;
     }
+    // the drain's int64 accumulators hold at most kOzMaxChunks chunks of KCH blocks
+    const int64_t smin = (p.kblocks + kOzMaxChunks * KCH - 1) / (kOzMaxChunks * KCH);
+    if (smin > 1 && x.epilogue != EPI_STORE) return cudaErrorInvalidValue;   // K > kOzErrMaxK with a fused error
+    if (splits < smin) splits = smin;
     p.kb_per_split = (p.kblocks + splits - 1) / splits;
     if (p.kb_per_split < 1) p.kb_per_split = 1;
     splits = (p.kblocks + p.kb_per_split - 1) / p.kb_per_split;
