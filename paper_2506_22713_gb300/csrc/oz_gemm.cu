@@ -45,16 +45,19 @@ constexpr int kOzMaxChunks = 16;      // chunks one CTA accumulates in int64
 static_assert(kOzMaxChunks * KCH * BK == kOzErrMaxK, "fused-error K limit");
 constexpr int UMMA_K = 16;            // K per tcgen05.mma kind::f16
 #ifndef OZ_ASTAGES
-#define OZ_ASTAGES 4
+#define OZ_ASTAGES 2
 #endif
 #ifndef OZ_BSTAGES
 #define OZ_BSTAGES 2
 #endif
 constexpr int ASTAGES = OZ_ASTAGES, BSTAGES = OZ_BSTAGES;
-constexpr int A_TILE = BM * BK * 2;   // 16 KB
+constexpr int A_TILE = BM * BK * 2;   // 16 KB: one slice
+constexpr int APS = 2;                // A slices per pipeline stage (one wait and one commit each)
+constexpr int A_STAGE = APS * A_TILE;
+static_assert(kOzSlices % APS == 0, "slices per stage");
 constexpr int B_TILE = BN * BK * 2;   // 8 KB
 constexpr int B_SET = NS * B_TILE;    // 64 KB
-constexpr int SMEM = BSTAGES * B_SET + ASTAGES * A_TILE + 1024 + 256;
+constexpr int SMEM = BSTAGES * B_SET + ASTAGES * A_STAGE + 1024 + 256;
 constexpr uint32_t TMEM_COLS = 512;   // 8 x 64 used
 constexpr int NTHREADS = 320;        // producer, MMA issuer, 8 drain warps
 constexpr int ECOLS = BN / 2;         // columns per drain warp
@@ -80,13 +83,20 @@ struct Params {
     int a_tri, b_tri;         // op(A) / op(B) upper triangular: skip their zero K blocks
 };
 
+// v 2^e: one multiply by a power of two built from its bits (exact unless
+// the result leaves the normal range, where ldexp takes over)
+__device__ __forceinline__ double pow2_scale(double v, int e) {
+    if (e >= -1022 && e <= 1023) return v * __longlong_as_double((long long)(e + 1023) << 52);
+    return ldexp(v, e);
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_constant__ Maps maps, Params p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *bbuf = smem;                                 // BSTAGES x 7 B slices
-    uint8_t *abuf = smem + BSTAGES * B_SET;                // ASTAGES A slices
-    uint64_t *fullB = (uint64_t *)(abuf + ASTAGES * A_TILE);
+    uint8_t *abuf = smem + BSTAGES * B_SET;                // ASTAGES stages of APS A slices
+    uint64_t *fullB = (uint64_t *)(abuf + ASTAGES * A_STAGE);
     uint64_t *emptyB = fullB + BSTAGES;
     uint64_t *fullA = emptyB + BSTAGES;
     uint64_t *emptyA = fullA + ASTAGES;
@@ -125,34 +135,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0) {
         // ---------------- TMA producer ----------------
+        // The whole warp runs the loop (waits and control flow stay
+        // warp-uniform); one elected lane issues the copies.
+        const bool leader = elect_one();
         int64_t ib = 0, ia = 0;
         bool ok = true;
         for (int64_t kb = kb0; kb < kb1 && ok; ++kb) {
             const int sb = (int)(ib % BSTAGES);
-            if (ib >= BSTAGES && !mbar_wait(&emptyB[sb], (uint32_t)((ib / BSTAGES - 1) & 1))) { ok = false; break; }
-            if (*(volatile int *)abort_sh) { ok = false; break; }
-            mbar_expect_tx(&fullB[sb], B_SET);
-            for (int t = 0; t < NS; ++t)
-                tma_load_2d(bbuf + sb * B_SET + t * B_TILE, &maps.b[t], &fullB[sb], (int)(kb * BK), (int)n0);
+            if (ib >= BSTAGES) ok = warp_wait(&emptyB[sb], (uint32_t)((ib / BSTAGES - 1) & 1));
+            if (ok && __any_sync(0xffffffffu, *(volatile int *)abort_sh != 0)) ok = false;
+            if (!ok) break;
+            if (leader) {
+                mbar_expect_tx(&fullB[sb], B_SET);
+                for (int t = 0; t < NS; ++t)
+                    tma_load_2d(bbuf + sb * B_SET + t * B_TILE, &maps.b[t], &fullB[sb], (int)(kb * BK), (int)n0);
+            }
             ++ib;
-            for (int s = 0; s < NS; ++s) {
+            for (int s0 = 0; s0 < NS && ok; s0 += APS) {
                 const int sa = (int)(ia % ASTAGES);
-                if (ia >= ASTAGES && !mbar_wait(&emptyA[sa], (uint32_t)((ia / ASTAGES - 1) & 1))) { ok = false; break; }
-                mbar_expect_tx(&fullA[sa], A_TILE);
-                tma_load_2d(abuf + sa * A_TILE, &maps.a[s], &fullA[sa], (int)(kb * BK), (int)m0);
+                if (ia >= ASTAGES) ok = warp_wait(&emptyA[sa], (uint32_t)((ia / ASTAGES - 1) & 1));
+                if (!ok) break;
+                if (leader) {
+                    mbar_expect_tx(&fullA[sa], A_STAGE);
+                    for (int u = 0; u < APS; ++u)
+                        tma_load_2d(abuf + sa * A_STAGE + u * A_TILE, &maps.a[s0 + u], &fullA[sa], (int)(kb * BK),
+                                    (int)m0);
+                }
                 ++ia;
             }
+            __syncwarp();
         }
-        if (!ok) { atomicExch(p.err_flag, 1); *abort_sh = 1; }
-    } else if (warp == 1 && lane == 0) {
+        if (!ok && leader) { atomicExch(p.err_flag, 1); *abort_sh = 1; }
+    } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
+        // Warp-uniform loop, one elected lane issues: single-thread divergent
+        // control flow around tcgen05 instructions slows their issue.
         // Fully unrolled over the 36 slice pairs and the 4 K steps of a
         // block: descriptors are a base plus constant offsets (the 16-byte
         // unit field advances by 2 per 32-byte K step and by 512 per 8 KB B
-        // slice), so the single issuing thread spends a few instructions per
-        // MMA.
+        // slice).
+        const bool leader = elect_one();
         constexpr uint32_t idesc = idesc_bf16(BM, BN, false, false);
         int64_t ib = 0, ia = 0;
         bool ok = true;
@@ -160,43 +184,56 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
             const bool first = (q % KCH) == 0;
             if (first) {
                 const int64_t chunk = q / KCH;
-                if (chunk > 0 && !mbar_wait(tmem_empty, (uint32_t)((chunk - 1) & 1))) { ok = false; break; }
+                if (chunk > 0) ok = warp_wait(tmem_empty, (uint32_t)((chunk - 1) & 1));
+                if (!ok) break;
                 tc_fence_after();
             }
             const int sb = (int)(ib % BSTAGES);
-            if (!mbar_wait(&fullB[sb], (uint32_t)((ib / BSTAGES) & 1))) { ok = false; break; }
+            ok = warp_wait(&fullB[sb], (uint32_t)((ib / BSTAGES) & 1));
+            if (!ok) break;
             tc_fence_after();
             const uint64_t bd0 = sdesc(smem_u32(bbuf + sb * B_SET), 16, 1024);
+            if (__any_sync(0xffffffffu, *(volatile int *)abort_sh != 0)) ok = false;
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
+            for (int s0 = 0; s0 < NS; s0 += APS) {
                 const int sa = (int)(ia % ASTAGES);
-                if (ok && !mbar_wait(&fullA[sa], (uint32_t)((ia / ASTAGES) & 1))) ok = false;
-                if (ok && *(volatile int *)abort_sh) ok = false;
+                if (ok) ok = warp_wait(&fullA[sa], (uint32_t)((ia / ASTAGES) & 1));
                 if (ok) {
                     tc_fence_after();
-                    const uint64_t ad0 = sdesc(smem_u32(abuf + sa * A_TILE), 16, 1024);
+                    if (leader) {
+                        const uint64_t as0 = sdesc(smem_u32(abuf + sa * A_STAGE), 16, 1024);
 #pragma unroll
-                    for (int t = 0; t < NG; ++t) {
-                        if (s + t < NG) {
+                        for (int u = 0; u < APS; ++u) {
+                            const int s = s0 + u;
+                            const uint64_t ad0 = as0 + (uint64_t)(u * (A_TILE >> 4));
 #pragma unroll
-                            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-                                // the first MMA of a group in a chunk overwrites it
-                                const uint32_t accum = (first && s == 0 && kk == 0) ? 0u : 1u;
-                                umma_bf16(tmem + (uint32_t)((s + t) * BN), ad0 + (uint64_t)(2 * kk),
-                                          bd0 + (uint64_t)(512 * t + 2 * kk), idesc, accum);
+                            for (int t = 0; t < NG; ++t) {
+                                if (s + t < NG) {
+#pragma unroll
+                                    for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                                        // the first MMA of a group in a chunk overwrites it
+                                        const uint32_t accum = (first && s == 0 && kk == 0) ? 0u : 1u;
+                                        umma_bf16(tmem + (uint32_t)((s + t) * BN), ad0 + (uint64_t)(2 * kk),
+                                                  bd0 + (uint64_t)(512 * t + 2 * kk), idesc, accum);
+                                    }
+                                }
                             }
                         }
+                        umma_commit(&emptyA[sa]);
                     }
-                    umma_commit(&emptyA[sa]);
+                    __syncwarp();
                 }
                 ++ia;
             }
             if (!ok) break;
-            umma_commit(&emptyB[sb]);
+            if (leader) {
+                umma_commit(&emptyB[sb]);
+                if (q % KCH == KCH - 1 || q == nkb - 1) umma_commit(tmem_full);
+            }
+            __syncwarp();
             ++ib;
-            if (q % KCH == KCH - 1 || q == nkb - 1) umma_commit(tmem_full);
         }
-        if (!ok) {
+        if (!ok && leader) {
             atomicExch(p.err_flag, 1);
             *abort_sh = 1;
             umma_commit(tmem_full);   // release the epilogue once the MMAs already issued finish
@@ -249,22 +286,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
         double local = 0.0;
         if (row < p.M) {
             const int ei = p.ea ? max(p.ea[row], -1100) : p.ea_fixed;
+            const bool unit_alpha = p.alpha == 1.0;
 #pragma unroll
             for (int j = 0; j < ECOLS; ++j) {
                 const int64_t col = n0 + c0 + j;
                 if (col < p.N && !(p.upper_only && row > col)) {
                     const double val =
-                        ldexp((double)acc[j], ei + (p.eb ? max(p.eb[col], -1100) : p.eb_fixed) - 50);
+                        pow2_scale((double)acc[j], ei + (p.eb ? max(p.eb[col], -1100) : p.eb_fixed) - 50);
                     if (EPI == EPI_STORE) {
                         if (p.split_stride > 0) {
                             p.C[(int64_t)blockIdx.z * p.split_stride + row + col * p.M] = val;
                         } else {
-                            double out = p.alpha * val;
+                            double out = unit_alpha ? val : p.alpha * val;
                             if (p.beta != 0.0) out = fma(p.beta, p.C[row + col * p.ldc], out);
                             p.C[row + col * p.ldc] = out;
                         }
                     } else {
-                        const double d = p.R[row + col * p.ldr] - p.alpha * val;
+                        const double d = fma(-p.alpha, val, p.R[row + col * p.ldr]);
                         local = fma(d, d, local);
                     }
                 }
