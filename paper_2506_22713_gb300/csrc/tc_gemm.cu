@@ -109,61 +109,72 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_const
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 0) {
         // ---------------- TMA producer ----------------
+        // Warp-uniform loop, one elected lane issues (single-thread divergent
+        // control flow around the async instructions slows their issue).
+        const bool leader = elect_one();
         for (int64_t it = 0; it < iters; ++it) {
             const int s = (int)(it % C::STAGES);
             const uint32_t round = (uint32_t)(it / C::STAGES);
-            if (it >= C::STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) {
-                atomicExch(p.err_flag, 1);
-                *abort_sh = 1;
+            if (it >= C::STAGES && !warp_wait(&empty[s], (round - 1) & 1)) {
+                if (leader) {
+                    atomicExch(p.err_flag, 1);
+                    *abort_sh = 1;
+                }
                 break;
             }
-            if (*(volatile int *)abort_sh) break;
-            const int pair = (int)(it % p.npairs);
-            const int64_t kb = kb0 + it / p.npairs;
-            uint8_t *sa = smem + s * C::STAGE;
-            uint8_t *sb = sa + C::A_BYTES;
-            mbar_expect_tx(&full[s], C::STAGE);
-            const int k_el = (int)(kb * BK);
-            if (A_MN) {
-                // A stored M-contiguous: two 64 (M) x 64 (K) boxes
-                tma_load_2d(sa, &maps.a[pair], &full[s], (int)m0, k_el);
-                tma_load_2d(sa + BM * BK, &maps.a[pair], &full[s], (int)m0 + 64, k_el);
-            } else {
-                tma_load_2d(sa, &maps.a[pair], &full[s], k_el, (int)m0);
+            if (__any_sync(0xffffffffu, *(volatile int *)abort_sh != 0)) break;
+            if (leader) {
+                const int pair = (int)(it % p.npairs);
+                const int64_t kb = kb0 + it / p.npairs;
+                uint8_t *sa = smem + s * C::STAGE;
+                uint8_t *sb = sa + C::A_BYTES;
+                mbar_expect_tx(&full[s], C::STAGE);
+                const int k_el = (int)(kb * BK);
+                if (A_MN) {
+                    // A stored M-contiguous: two 64 (M) x 64 (K) boxes
+                    tma_load_2d(sa, &maps.a[pair], &full[s], (int)m0, k_el);
+                    tma_load_2d(sa + BM * BK, &maps.a[pair], &full[s], (int)m0 + 64, k_el);
+                } else {
+                    tma_load_2d(sa, &maps.a[pair], &full[s], k_el, (int)m0);
+                }
+                tma_load_2d(sb, &maps.b[pair], &full[s], k_el, (int)n0);
             }
-            tma_load_2d(sb, &maps.b[pair], &full[s], k_el, (int)n0);
+            __syncwarp();
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
+        const bool leader = elect_one();
         constexpr uint32_t idesc = idesc_bf16(BM, BN_, A_MN, false);
-        bool ok = true;
         for (int64_t it = 0; it < iters; ++it) {
             const int s = (int)(it % C::STAGES);
             const uint32_t round = (uint32_t)(it / C::STAGES);
-            if (!mbar_wait(&full[s], round & 1)) {
-                atomicExch(p.err_flag, 1);
-                *abort_sh = 1;
-                ok = false;
+            if (!warp_wait(&full[s], round & 1)) {
+                if (leader) {
+                    atomicExch(p.err_flag, 1);
+                    *abort_sh = 1;
+                }
                 break;
             }
-            if (*(volatile int *)abort_sh) { ok = false; break; }
+            if (__any_sync(0xffffffffu, *(volatile int *)abort_sh != 0)) break;
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * C::STAGE);
-            const uint32_t sb = sa + C::A_BYTES;
+            if (leader) {
+                const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-                uint64_t ad, bd;
-                if (A_MN) ad = sdesc(sa + kk * (UMMA_K * 128), BM * BK, 1024);   // LBO: next 64-row M block
-                else ad = sdesc(sa + kk * (UMMA_K * 2), 16, 1024);
-                bd = sdesc(sb + kk * (UMMA_K * 2), 16, 1024);
-                umma_bf16(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+                    uint64_t ad, bd;
+                    if (A_MN) ad = sdesc(sa + kk * (UMMA_K * 128), BM * BK, 1024);   // LBO: next 64-row M block
+                    else ad = sdesc(sa + kk * (UMMA_K * 2), 16, 1024);
+                    bd = sdesc(sb + kk * (UMMA_K * 2), 16, 1024);
+                    umma_bf16(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&empty[s]);
+            __syncwarp();
         }
-        (void)ok;
-        umma_commit(tmem_full);   // completes once every MMA issued above has finished
+        if (leader) umma_commit(tmem_full);   // completes once every MMA issued above has finished
     } else if (warp >= 2) {
         // ---------------- epilogue ----------------
         const int q = warp & 3;   // TMEM lane quarter this warp may access
