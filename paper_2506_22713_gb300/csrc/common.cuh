@@ -103,6 +103,13 @@ struct Scratch {
 // --------------------------------------------------------------------------
 extern int g_fail_alloc_after;   // test hook: n-th allocation from now fails
 
+// Stream-ordered allocation from the library's own memory pool on the
+// current device.  The pool keeps up to 64 GiB of freed blocks mapped, so the
+// gigabyte-sized per-call buffers (operand slices, the basis) are not mapped
+// and unmapped again on every call, and the caller's default pool is left as
+// it is.
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+
 struct Arena {
     cudaStream_t s;
     std::vector<void *> ptrs;
@@ -115,7 +122,7 @@ struct Arena {
             if (--g_fail_alloc_after == 0) return EOD_ENOMEM;
         }
         void *q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, sizeof(T) * count, s);
+        cudaError_t e = lib_malloc_async(&q, sizeof(T) * count, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return e == cudaErrorMemoryAllocation ? EOD_ENOMEM : EOD_ECUDA;

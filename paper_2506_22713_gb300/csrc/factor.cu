@@ -719,7 +719,7 @@ eod_status factor_any(const void *A, int64_t m, int64_t n, int64_t lda, double t
 eod_status factor_mixed_from_f64(const double *A, int64_t m, int64_t n, int64_t lda, double tol, uint64_t seed,
                                  const eod_opts &o, cudaStream_t s, eod_factors *F) {
     float *A32 = nullptr;
-    cudaError_t e = cudaMallocAsync(&A32, sizeof(float) * (size_t)m * n, s);
+    cudaError_t e = lib_malloc_async((void **)&A32, sizeof(float) * (size_t)m * n, s);
     if (e != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
     eod_status st = EOD_OK;
     if (copy_matrix<double, float>(A, lda, A32, m, m, n, false, s) != cudaSuccess) st = EOD_ECUDA;
@@ -802,7 +802,7 @@ eod_status eod_abe_factor_host(const void *A_host, int64_t m, int64_t n, int64_t
     const size_t es = o.a_dtype == EOD_F64 ? 8 : 4;
     void *Ad = nullptr;
     if (g_fail_alloc_after > 0 && --g_fail_alloc_after == 0) return EOD_ENOMEM;
-    if (cudaMallocAsync(&Ad, es * (size_t)m * n, s) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
+    if (lib_malloc_async(&Ad, es * (size_t)m * n, s) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
     eod_status st = EOD_OK;
     if (cudaMemcpy2DAsync(Ad, es * m, A_host, es * lda, es * m, n, cudaMemcpyHostToDevice, s) != cudaSuccess)
         st = EOD_ECUDA;

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "instrument.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -153,6 +154,85 @@ __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int S, const Acc *__r
     }
 }
 
+// Matrix-vector products (N = 1: the explicit CGS2 residual of an undecided
+// pivot, Alg. 1 steps 6-11): HBM-bound, so one pass over A with full lanes
+// instead of a GEMM tile that is 1/32 used.
+//   y = alpha A x + beta y   (A M x K): a thread per row, K loop, coalesced;
+//   y = alpha A^T x + beta y (A K x M): a CTA per (column, K range), a fixed
+//   order block reduction, partial sums reduced in order by a second kernel.
+template <typename TA, typename TB, typename TC, typename Acc>
+__global__ void gemv_n_kernel(int64_t M, int64_t K, Acc alpha, const TA *__restrict__ A, int64_t lda,
+                              const TB *__restrict__ x, Acc beta, TC *y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        Acc acc = Acc(0);
+        for (int64_t k = 0; k < K; ++k) acc = fma((Acc)A[i + k * lda], (Acc)x[k], acc);
+        Acc v = alpha * acc;
+        if (beta != Acc(0)) v = fma(beta, (Acc)y[i], v);
+        y[i] = (TC)v;
+    }
+}
+
+template <typename TA, typename TB, typename Acc>
+__global__ void __launch_bounds__(256) gemv_t_partial_kernel(int64_t M, int64_t K, int64_t chunk,
+                                                             const TA *__restrict__ A, int64_t lda,
+                                                             const TB *__restrict__ x, Acc *__restrict__ part) {
+    __shared__ Acc red[256];
+    const int64_t i = blockIdx.x, k0 = (int64_t)blockIdx.y * chunk;
+    int64_t k1 = k0 + chunk;
+    if (k1 > K) k1 = K;
+    Acc acc = Acc(0);
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) acc = fma((Acc)A[k + i * lda], (Acc)x[k], acc);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * M + i] = red[0];
+}
+
+template <typename TC, typename Acc>
+__global__ void gemv_t_reduce_kernel(int64_t M, int S, const Acc *__restrict__ part, Acc alpha, Acc beta, TC *y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        Acc s = Acc(0);
+        for (int z = 0; z < S; ++z) s += part[(int64_t)z * M + i];
+        Acc v = alpha * s;
+        if (beta != Acc(0)) v = fma(beta, (Acc)y[i], v);
+        y[i] = (TC)v;
+    }
+}
+
+template <typename TA, typename TB, typename TC, typename Acc>
+cudaError_t launch_gemv(bool ta, int64_t M, int64_t K, double alpha, const TA *A, int64_t lda, const TB *x,
+                        double beta, TC *y, Scratch *ws, cudaStream_t s) {
+    ProfScope prof(PROF_GEMM_SIMT, 2.0 * (double)M * K, (double)sizeof(TA) * M * K, s);
+    if (!ta) {
+        count_launch();
+        const int64_t blocks = std::min<int64_t>((M + 255) / 256, 8LL * kNumSMs);
+        gemv_n_kernel<TA, TB, TC, Acc><<<(unsigned)blocks, 256, 0, s>>>(M, K, (Acc)alpha, A, lda, x, (Acc)beta, y);
+        return cudaGetLastError();
+    }
+    // K split so that about four CTAs per SM work, chunks of at least 2048
+    int64_t S = (4 * kNumSMs + M - 1) / M;
+    const int64_t smax = (K + 2047) / 2048;
+    if (S > smax) S = smax;
+    if (S < 1) S = 1;
+    const int64_t chunk = (K + S - 1) / S;
+    S = (K + chunk - 1) / chunk;
+    if (S < 1) S = 1;
+    size_t mark = ws ? ws->mark() : 0;
+    Acc *part = ws ? (Acc *)ws->take(sizeof(Acc) * (size_t)S * (size_t)M) : nullptr;
+    if (!part) return cudaErrorMemoryAllocation;
+    count_launch(2);
+    gemv_t_partial_kernel<TA, TB, Acc><<<dim3((unsigned)M, (unsigned)S), 256, 0, s>>>(M, K, chunk, A, lda, x, part);
+    EOD_CUDA_TRY(cudaGetLastError());
+    const int64_t blocks = std::min<int64_t>((M + 255) / 256, 8LL * kNumSMs);
+    gemv_t_reduce_kernel<TC, Acc><<<(unsigned)blocks, 256, 0, s>>>(M, (int)S, part, (Acc)alpha, (Acc)beta, y);
+    EOD_CUDA_TRY(cudaGetLastError());
+    ws->release(mark);
+    return cudaSuccess;
+}
+
 // tile grid and K split for tile size ts
 struct SimtPlan {
     int64_t gm, gn, S;
@@ -281,6 +361,9 @@ cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
         ws && ws->err_flag && K > 0 && fp64_use_emulated(M, N, K) && (x.epilogue != EPI_ERR || K <= kOzErrMaxK))
         return oz_gemm(ta, tb, M, N, K, alpha, (const double *)A, lda, (const double *)B, ldb, beta, (double *)C,
                        ldc, x, ws->err_flag, s);
+    // matrix-vector products: op(B) is one column of K contiguous values
+    if (N == 1 && !tb && K > 0 && x.epilogue == EPI_STORE && !x.upper_only && !x.a_upper && !x.b_upper && ws)
+        return launch_gemv<TA, TB, TC, Acc>(ta, M, K, alpha, A, lda, B, beta, C, ws, s);
     if (!ta && !tb) return launch<TA, TB, TC, Acc, false, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
     if (ta && !tb) return launch<TA, TB, TC, Acc, true, false>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);
     if (!ta && tb) return launch<TA, TB, TC, Acc, false, true>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, ws, s);

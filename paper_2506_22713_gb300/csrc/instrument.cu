@@ -43,6 +43,36 @@ cudaEvent_t take_event() {
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    constexpr int kMaxDev = 64;
+    static cudaMemPool_t pools[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np;
+            e = cudaMemPoolCreate(&np, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = 64ull << 30;
+            e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+            pools[dev] = np;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
 ProfScope::ProfScope(int kind, double flops, double bytes, cudaStream_t s) : s_(s), rec_(-1) {
     if (!g_enabled.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_mu);

@@ -489,8 +489,8 @@ cudaError_t make_slices(const double *X, int64_t R, int64_t K, int64_t sr, int64
                         int tri = 0) {
     sl.R = R;
     sl.ldk = round_up(K, 8);
-    EOD_CUDA_TRY(cudaMallocAsync((void **)&sl.q, sizeof(__nv_bfloat16) * (size_t)NS * R * sl.ldk, s));
-    EOD_CUDA_TRY(cudaMallocAsync((void **)&sl.e, sizeof(int) * (size_t)R, s));
+    EOD_CUDA_TRY(lib_malloc_async((void **)&sl.q, sizeof(__nv_bfloat16) * (size_t)NS * R * sl.ldk, s));
+    EOD_CUDA_TRY(lib_malloc_async((void **)&sl.e, sizeof(int) * (size_t)R, s));
     return slice_into(X, R, K, sr, sk, sl.q, sl.e, 0, sl.ldk, R * sl.ldk, s, tri);
 }
 
@@ -563,7 +563,7 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
     e = set_smem_once(oz_gemm_kernel<EPI_STORE>, SMEM);
     if (e == cudaSuccess) e = set_smem_once(oz_gemm_kernel<EPI_ERR>, SMEM);
     if (e == cudaSuccess && splits > 1) {
-        e = cudaMallocAsync((void **)&part, sizeof(double) * (size_t)splits * M * N, s);
+        e = lib_malloc_async((void **)&part, sizeof(double) * (size_t)splits * M * N, s);
         p.C = part;
         p.ldc = M;
         p.split_stride = M * N;

@@ -199,3 +199,26 @@ def test_upper_only_gram(eod, mode, p, K):
     assert ((C - ref).abs()[up] <= 1e-13 * scale[up]).all()
     if mode == 1:
         assert (C[~up] == -7.0).all()
+
+
+@pytest.mark.parametrize("ta", [False, True])
+@pytest.mark.parametrize("M,K", [(9, 262144), (262144, 9), (1, 1), (3000, 2100), (37, 5)])
+def test_matrix_vector_products(eod, ta, M, K):
+    """N = 1 (the explicit residual of an undecided pivot) through the SIMT
+    path's matrix-vector kernels, both orientations, with alpha and beta."""
+    g = torch.Generator(device="cuda").manual_seed(M + K + ta)
+    A = _cm(torch.randn((K, M) if ta else (M, K), generator=g, device="cuda", dtype=torch.float64))
+    x = _cm(torch.randn((K, 1), generator=g, device="cuda", dtype=torch.float64))
+    C0 = _cm(torch.randn((M, 1), generator=g, device="cuda", dtype=torch.float64))
+    opA = A.t() if ta else A
+    ref = -1.0 * (opA @ x) + 0.5 * C0
+    C = C0.clone()
+    s = torch.cuda.current_stream()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    # single columns: their leading dimensions are their lengths (torch may
+    # report a unit stride for a one-column tensor)
+    st = eod.eod_abe_debug_f64_gemm(0, int(ta), 0, M, 1, K, -1.0, P(A), A.stride(1), P(x), K, 0.5, P(C), M,
+                                    ctypes.c_void_p(s.cuda_stream))
+    assert st == eod.EOD_OK, eod.status_string(st)
+    scale = opA.abs() @ x.abs() + 0.5 * C0.abs()
+    assert ((C - ref).abs() <= 1e-13 * scale + 1e-300).all()
