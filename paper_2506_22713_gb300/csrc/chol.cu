@@ -30,22 +30,26 @@ __device__ __forceinline__ long long dkey(double x) {
     return b >= 0 ? b : -(b & 0x7fffffffffffffffll);
 }
 
-// 1/d for finite d > 0 (normal): FP32 reciprocal of the mantissa as the
-// seed (exponent handled on the integer bits), then two Newton steps
-// r <- r + r (1 - d r) in FP64, each doubling the 23 correct bits.
+// 1/d for finite d > 0: FP32 reciprocal of the mantissa as the seed (the
+// exponent handled on the integer bits), then two Newton steps
+// r <- r + r (1 - d r) in FP64, each doubling the 23 correct bits.  No FP64
+// division anywhere (each FP64 instruction costs a warp 64 cycles here):
+// a subnormal d gives +inf, a d near the top of the range 0.
 __device__ __forceinline__ double recip_pos(double d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int E = (int)(b >> 52);                                  // biased exponent, 1..2046
+    const int E = (int)(b >> 52);                                  // biased exponent
     const unsigned int mf = 0x3f800000u | (unsigned int)((b >> 29) & 0x7fffffu);   // mantissa in [1, 2)
     const float rf = __frcp_rn(__uint_as_float(mf));               // (0.5, 1]
     const unsigned int rb = __float_as_uint(rf);
     const long long re = (long long)((rb >> 23) & 0xff) - 127 + 1023 - (E - 1023);
-    if (re <= 0 || re >= 2047) return 1.0 / d;                     // 1/d subnormal or huge
-    double r = __longlong_as_double((re << 52) | ((long long)(rb & 0x7fffffu) << 29));
+    const long long rbits = (re << 52) | ((long long)(rb & 0x7fffffu) << 29);
+    double r = __longlong_as_double(rbits);
     double e = fma(-d, r, 1.0);
     r = fma(r, e, r);
     e = fma(-d, r, 1.0);
-    return fma(r, e, r);
+    r = fma(r, e, r);
+    const double inf = __longlong_as_double(0x7ff0000000000000ll);
+    return (E == 0 || re >= 2047) ? inf : (re <= 0 ? 0.0 : r);
 }
 
 // Pivot decision for column j (one thread) on the integer keys: the rank test
@@ -54,30 +58,34 @@ __device__ __forceinline__ double recip_pos(double d) {
 // *rd = 1/d.
 __device__ __forceinline__ void ldl_pivot(const double *S, int w, int j, const long long *klo, const long long *khi,
                                           const long long *krg, int decide, double *dv, int *go, double *rd,
-                                          int *p_out, int *code) {
+                                          int *p_out, int *code, bool writer) {
     const double d = S[j + j * w];
     const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
     const bool finite = ((bits >> 52) & 0x7ff) != 0x7ff;
     const long long kd = dkey(d);
-    int keep;
+    int keep, c = CHOL_ALL;
     if (!finite) {
         keep = 0;
-        *code = decide ? CHOL_UNCERTAIN : CHOL_FAIL;
+        c = decide ? CHOL_UNCERTAIN : CHOL_FAIL;
     } else if (decide) {
-        if (kd < klo[j]) { keep = 0; *code = CHOL_BELOW; }
+        if (kd < klo[j]) { keep = 0; c = CHOL_BELOW; }
         else if (kd > khi[j] && kd > krg[j]) keep = 1;
-        else { keep = 0; *code = CHOL_UNCERTAIN; }
+        else { keep = 0; c = CHOL_UNCERTAIN; }
     } else {
         keep = kd > 0 ? 1 : 0;
-        if (!keep) *code = CHOL_FAIL;
+        if (!keep) c = CHOL_FAIL;
     }
-    if (keep) {
-        dv[j] = d;
-        *rd = ((bits >> 52) & 0x7ff) != 0 ? recip_pos(d) : 1.0 / d;   // subnormal: plain division
-    } else {
-        *p_out = j;
+    const double r = recip_pos(d);
+    if (writer) {
+        if (keep) {
+            dv[j] = d;
+            *rd = r;
+        } else {
+            *p_out = j;
+            *code = c;
+        }
+        *go = keep;
     }
-    *go = keep;
 }
 
 // One CTA of 256 threads: G + shift I = L D L^T (unit lower L, no square
@@ -137,7 +145,7 @@ __global__ void __launch_bounds__(256) chol_small_kernel(const double *__restric
         code_sh = CHOL_ALL;
     }
     __syncthreads();
-    if (tid == 0) ldl_pivot(S, w, 0, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh);
+    if (tid < 32) ldl_pivot(S, w, 0, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh, tid == 0);
     __syncthreads();
 
     for (int j = 0; j < w; ++j) {
@@ -154,12 +162,18 @@ __global__ void __launch_bounds__(256) chol_small_kernel(const double *__restric
         }
         __syncthreads();
         if (!next) break;
-        if (tid == 0) {
-            ldl_pivot(S, w, j + 1, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh);
-        } else if (tid >= 32) {
+        if (tid < 32) {
+            // the whole warp computes the pivot (no divergence on the
+            // critical path; FP64 costs a warp the same for 1 or 32 lanes),
+            // lane 0 publishes it
+            ldl_pivot(S, w, j + 1, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh, tid == 0);
+        } else if (tid >= 32 && (tid >> 5) != 4) {
+            // warps 1-3 and 5-7: warp 4 shares warp 0's sub-partition, whose
+            // FP64 pipe (64 cycles per warp instruction) stays free for the pivot
             if (tid == 32) S[(j + 1) + j * w] = u1 * rd;
             const int cnt = (w - 2 - j) * (w - 1 - j) / 2;
-            for (int e = tid - 32; e < cnt; e += blockDim.x - 32) {
+            const int me = tid - 32 - ((tid >> 5) > 4 ? 32 : 0);
+            for (int e = me; e < cnt; e += blockDim.x - 64) {
                 const int pr = pairs[e];
                 const int ii = pr & 0xff, ll = pr >> 8;
                 S[ii + ll * w] = fma(-S[ii + j * w], u[ll], S[ii + ll * w]);
