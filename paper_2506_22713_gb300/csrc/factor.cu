@@ -214,14 +214,28 @@ static eod_status trsm_panels(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, i
     return EOD_OK;
 }
 
-// G (p x p, upper, FP64) = W^T W: the skinny kernel for p <= 128, else a
-// tiled one (FP64 DFMA for FP64 data, exact-product FP32 sums for FP32 data).
+// G (p x p, upper, FP64) = W^T W: the skinny kernel for p <= 128, else the
+// FP64 GEMM (tensor-core emulation for large products; FP32 data is widened
+// to FP64 first, exactly), else for FP32 data the exact-product FP32 sums.
 template <typename T>
 static eod_status gram_full(const T *W, int64_t rows, int64_t p, int64_t ldw, double *G, const GemmExtra &sym,
                             Scratch *ws, cudaStream_t s) {
-    if (p <= 128) EOD_CU(gram_skinny<T>(W, rows, (int)p, ldw, G, p, ws, s));
-    else if (std::is_same<T, float>::value) EOD_CU(gram_tiled_f32((const float *)W, rows, p, ldw, G, p, ws, s));
-    else EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, G, p, sym, ws, s)));
+    if (p <= 128) {
+        EOD_CU(gram_skinny<T>(W, rows, (int)p, ldw, G, p, ws, s));
+    } else if (std::is_same<T, double>::value) {
+        EOD_CU((gemm<T, T, double, double>(true, false, p, p, rows, 1.0, W, ldw, W, ldw, 0.0, G, p, sym, ws, s)));
+    } else if (fp64_use_emulated(p, p, rows)) {
+        double *Wd = nullptr;
+        EOD_CU(lib_malloc_async((void **)&Wd, sizeof(double) * (size_t)rows * p, s));
+        cudaError_t e = copy_matrix<T, double>(W, ldw, Wd, rows, rows, p, false, s);
+        if (e == cudaSuccess)
+            e = gemm<double, double, double, double>(true, false, p, p, rows, 1.0, Wd, rows, Wd, rows, 0.0, G, p, sym,
+                                                     ws, s);
+        cudaFreeAsync(Wd, s);
+        EOD_CU(e);
+    } else {
+        EOD_CU(gram_tiled_f32((const float *)W, rows, p, ldw, G, p, ws, s));
+    }
     return EOD_OK;
 }
 
