@@ -148,14 +148,29 @@ __global__ void __launch_bounds__(GT) gram_partial_kernel(const T *__restrict__ 
     }
 }
 
-__global__ void gram_reduce_kernel(const double *__restrict__ part, int nparts, int w, double *G, int64_t ldg) {
+// Sum of the per-CTA partial Grams, upper triangle: a block takes 32
+// consecutive entries, its 8 warps each sum every 8th partial (in order), and
+// the 8 warp sums are added in order: the FP64 adds of one entry are spread
+// over 8 warps and the result does not depend on timing.
+__global__ void __launch_bounds__(256) gram_reduce_kernel(const double *__restrict__ part, int nparts, int w,
+                                                          double *G, int64_t ldg) {
+    __shared__ double red[8][33];
     const int total = w * w;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
+    double sum = 0.0;
+    if (e < total && e % w <= e / w)
+        for (int z = g; z < nparts; z += 8) sum += part[(int64_t)z * total + e];
+    red[g][lane] = sum;
+    __syncthreads();
+    if (g == 0 && e < total) {
         const int i = e % w, j = e / w;
-        if (i > j) continue;
-        double s = 0.0;
-        for (int z = 0; z < nparts; ++z) s += part[(int64_t)z * total + e];
-        G[i + (int64_t)j * ldg] = s;
+        if (i <= j) {
+            double t = red[0][lane];
+#pragma unroll
+            for (int q = 1; q < 8; ++q) t += red[q][lane];
+            G[i + (int64_t)j * ldg] = t;
+        }
     }
 }
 
@@ -288,7 +303,7 @@ cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, in
     count_launch(2);
     gram_partial_kernel<T><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
     EOD_CUDA_TRY(cudaGetLastError());
-    gram_reduce_kernel<<<(w * w + 255) / 256, 256, 0, s>>>(part, (int)ctas, w, G, ldg);
+    gram_reduce_kernel<<<(w * w + 31) / 32, 256, 0, s>>>(part, (int)ctas, w, G, ldg);
     EOD_CUDA_TRY(cudaGetLastError());
     ws->release(mark);
     return cudaSuccess;

@@ -352,12 +352,17 @@ __device__ __forceinline__ int exp_of_bits(unsigned long long a) {
     return ex;
 }
 
-// e[r] = exponent of max_k |X(r, k)| (frexp convention: max < 2^e), by
-// atomicMax over blocks that each cover 32 rows x a K range; rows that stay
-// all zero keep the sentinel value (< -1100) the caller stored.  Integer
-// compares of the bit patterns: no FP64 arithmetic.
+constexpr int kExpZero = -2000000000;   // exponent of an all-zero row (< -1100)
+constexpr int kMaxExpSplit = 16;        // K ranges of the row-exponent pass
+
+// ep[z][r] = exponent of max |X(r, k)| over the z-th K range (frexp
+// convention: max < 2^e), kExpZero if that range of the row is zero; blocks
+// cover 32 rows x one K range, so every entry is written once (no atomics,
+// no initialisation pass).  Integer compares of the bit patterns: no FP64
+// arithmetic.
 __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
-                              int64_t kper, int tri, int *e) {
+                              int64_t kper, int tri, int *ep) {
+    int *e = ep + (int64_t)blockIdx.y * R;
     __shared__ unsigned long long red[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
     const int64_t r0 = (int64_t)blockIdx.x * 32;
@@ -374,7 +379,7 @@ __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K
                     if (!tri_zero(tri, r, k)) m = max(m, abs_bits(X[r * sr + k]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (tx == 0 && r < R && m > 0ull) atomicMax(&e[r], exp_of_bits(m));
+            if (tx == 0 && r < R) e[r] = m > 0ull ? exp_of_bits(m) : kExpZero;
         }
         return;
     }
@@ -390,7 +395,7 @@ __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K
         unsigned long long m = red[0][tx];
 #pragma unroll
         for (int i = 1; i < 8; ++i) m = max(m, red[i][tx]);
-        if (m > 0ull) atomicMax(&e[r], exp_of_bits(m));
+        e[r] = m > 0ull ? exp_of_bits(m) : kExpZero;
     }
 }
 
@@ -400,12 +405,26 @@ __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K
 // is split into 8 balanced base-128 digits q_s in [-64, 64] (digit s has
 // weight 2^(49 - 7 s)), so x = sign 2^(e - 55) sum_s q_s 2^(49 - 7 s) up to
 // 2^(e - 56); every q_s is exact in BF16.
+// The row exponents come from the nsplit partial ones of rowexp_kernel (the
+// blocks of the first K column also store them in e_out for the product), or
+// every row takes fixed_e when ep is null.
 __global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
-                             int tri, const int *__restrict__ e, int fixed_e, __nv_bfloat16 *__restrict__ out,
-                             int64_t ldk, int64_t slice_stride) {
+                             int tri, const int *__restrict__ ep, int nsplit, int *__restrict__ e_out, int fixed_e,
+                             __nv_bfloat16 *__restrict__ out, int64_t ldk, int64_t slice_stride) {
     __shared__ double tile[32][33];
+    __shared__ int erow[32];
     const int64_t r0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    if (ty == 0) {
+        const int64_t r = r0 + tx;
+        int er = fixed_e;
+        if (ep && r < R) {
+            er = kExpZero;
+            for (int z = 0; z < nsplit; ++z) er = max(er, ep[(int64_t)z * R + r]);
+            if (blockIdx.x == 0 && e_out) e_out[r] = er;
+        }
+        erow[tx] = er;
+    }
     for (int i = ty; i < 32; i += 8) {
         int64_t r, k;
         if (sk == 1) { r = r0 + i; k = k0 + tx; } else { r = r0 + tx; k = k0 + i; }
@@ -416,7 +435,7 @@ __global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K,
     for (int i = ty; i < 32; i += 8) {
         const int64_t r = r0 + i, k = k0 + tx;
         if (r >= R || k >= K) continue;
-        const int er = e ? e[r] : fixed_e;
+        const int er = erow[i];
         const unsigned long long bits = (unsigned long long)__double_as_longlong(tile[i][tx]);
         const bool neg = (bits >> 63) != 0;
         int E = (int)((bits >> 52) & 0x7ff);
@@ -466,23 +485,34 @@ struct Slices {
 cudaError_t slice_into(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, __nv_bfloat16 *q, int *e,
                        int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s, int tri = 0) {
     if (R <= 0 || K <= 0) return cudaSuccess;
+    int *ep = nullptr;
+    int64_t ksplit = 1;
     if (e) {
-        count_launch();
-        // every exponent starts at a large negative sentinel (bytes 0x80)
-        EOD_CUDA_TRY(cudaMemsetAsync(e, 0x80, sizeof(int) * (size_t)R, s));
         const int64_t rblocks = (R + 31) / 32;
-        int64_t ksplit = (4 * kNumSMs + rblocks - 1) / rblocks;
+        ksplit = (4 * kNumSMs + rblocks - 1) / rblocks;
         const int64_t kmax = (K + 255) / 256;
         if (ksplit > kmax) ksplit = kmax;
+        if (ksplit > kMaxExpSplit) ksplit = kMaxExpSplit;
         if (ksplit < 1) ksplit = 1;
         const int64_t kper = (K + ksplit - 1) / ksplit;
-        rowexp_kernel<<<dim3((unsigned)rblocks, (unsigned)ksplit), 256, 0, s>>>(X, R, K, sr, sk, kper, tri, e);
-        EOD_CUDA_TRY(cudaGetLastError());
+        ksplit = (K + kper - 1) / kper;
+        ep = e;   // one range: the partial exponents are the exponents
+        if (ksplit > 1) EOD_CUDA_TRY(lib_malloc_async((void **)&ep, sizeof(int) * (size_t)ksplit * R, s));
+        count_launch();
+        rowexp_kernel<<<dim3((unsigned)rblocks, (unsigned)ksplit), 256, 0, s>>>(X, R, K, sr, sk, kper, tri, ep);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) {
+            if (ep != e) cudaFreeAsync(ep, s);
+            return le;
+        }
     }
     count_launch();
     dim3 grid((unsigned)((K + 31) / 32), (unsigned)((R + 31) / 32));
-    slice_kernel<<<grid, dim3(32, 8), 0, s>>>(X, R, K, sr, sk, tri, e, fixed_e, q, ldk, slice_stride);
-    return cudaGetLastError();
+    slice_kernel<<<grid, dim3(32, 8), 0, s>>>(X, R, K, sr, sk, tri, ep, (int)ksplit, (ep && ep != e) ? e : nullptr,
+                                               fixed_e, q, ldk, slice_stride);
+    cudaError_t le = cudaGetLastError();
+    if (ep && ep != e) cudaFreeAsync(ep, s);
+    return le;
 }
 
 cudaError_t make_slices(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, Slices &sl, cudaStream_t s,
