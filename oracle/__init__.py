@@ -59,7 +59,7 @@ def configure(lib):
     lib.orc_basis_ext.restype = ctypes.c_int
     lib.orc_eod_abe.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                 ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
-                                ctypes.c_uint64, _f64p, _f64p, _f64p, _f64p, _f64p, _i64p,
+                                ctypes.c_uint64, ctypes.c_int64, _f64p, _f64p, _f64p, _f64p, _f64p, _i64p,
                                 _f64p, _f64p, _i64p]
     lib.orc_eod_abe.restype = ctypes.c_int
     lib.orc_storage_entries.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
@@ -163,8 +163,9 @@ def basis_ext(A, eps: float, k: int = 32, seed: int = 0, batch: int = 0, max_blo
     return Q[:, : r.value].copy(order="F"), td[: nt.value].copy()
 
 
-def eod_abe(A, tol: float, tol_mode: int = 0, k: int = 32, seed: int = 0, batch: int = 0) -> dict:
-    """Alg. 2 with tau = 0 plus the reconstruction error.
+def eod_abe(A, tol: float, tol_mode: int = 0, k: int = 32, seed: int = 0, batch: int = 0, tau: int = 0) -> dict:
+    """Alg. 2 (tau subspace iterations, 0 = power-free) plus the
+    reconstruction error.
 
     tol_mode 0 uses eps = tol; tol_mode 1 uses eps = tol * ||A||_F.
     Returns a dict with r, U, D, V, Q, C, rel_err, norm_a, eps, tdiag.
@@ -182,7 +183,7 @@ def eod_abe(A, tol: float, tol_mode: int = 0, k: int = 32, seed: int = 0, batch:
     res = np.zeros(3)
     r = ctypes.c_int64(0)
     nt = ctypes.c_int64(0)
-    st = lib.orc_eod_abe(_ptr(A), m, n, m, tol, tol_mode, k, seed, batch, _ptr(U), _ptr(D), _ptr(V),
+    st = lib.orc_eod_abe(_ptr(A), m, n, m, tol, tol_mode, k, seed, batch, int(tau), _ptr(U), _ptr(D), _ptr(V),
                          _ptr(Q), _ptr(C), ctypes.byref(r), _ptr(res), _ptr(td), ctypes.byref(nt))
     if st:
         raise MemoryError("oracle allocation failed")

@@ -1,6 +1,7 @@
 /*
- * EOD-ABE oracle: a plain, slow, FP64 CPU statement of the power-free
- * (tau = 0) EOD-ABE method of Xu, Shen, Liu and Jia, "A Novel Adaptive
+ * EOD-ABE oracle: a plain, slow, FP64 CPU statement of the EOD-ABE method
+ * (power-free, tau = 0, and with tau subspace iterations) of Xu, Shen, Liu
+ * and Jia, "A Novel Adaptive
  * Low-Rank Matrix Approximation Method for Image Compression and
  * Reconstruction" (arXiv 2506.22713).
  *
@@ -23,7 +24,10 @@
  *                       rank revealed), k-independence, QtQ = I
  *   orc_eod_abe         Eckart-Young optimum from a full SVD on tiny inputs,
  *                       A_hat = Q C = U D V^T, V = Q-factor of C^T (LAPACK),
- *                       D = R-factor of R^T (LAPACK), eps-monotonicity
+ *                       D = R-factor of R^T (LAPACK), eps-monotonicity;
+ *                       with tau > 0: range(Q_tau) = range((A A^T)^tau Q_0)
+ *                       (matrix powers, numpy), the rank unchanged, RelErr
+ *                       above the Eckart-Young optimum and converging to it
  *   orc_storage_entries worked example of Sec. 1 (72284 of 145200 entries)
  */
 #include <math.h>
@@ -293,7 +297,34 @@ int orc_basis_ext(const double *A, int64_t m, int64_t n, int64_t lda, double eps
 }
 
 /* ------------------------------------------------------------------------ */
-/* Alg. 2 with tau = 0: BasisExt, then                                      */
+/* Alg. 2 steps 2-7, tau times on Q (m x r, ld m), in place: the rank r is   */
+/* the one BasisExt found; each pass forms Yt = A^T Q and its QR Yt = Qt Rt, */
+/* then Y = A Qt and its QR Y = Q R (positive diagonals, Householder).       */
+/* ------------------------------------------------------------------------ */
+static int subspace_iteration(const double *A, int64_t m, int64_t n, int64_t lda, double *Q, int64_t r,
+                              int64_t tau)
+{
+    if (tau <= 0 || r == 0) return 0;
+    double *Yt = (double *)malloc(sizeof(double) * (size_t)n * (size_t)r);
+    double *Qt = (double *)malloc(sizeof(double) * (size_t)n * (size_t)r);
+    double *Y = (double *)malloc(sizeof(double) * (size_t)m * (size_t)r);
+    double *R = (double *)malloc(sizeof(double) * (size_t)r * (size_t)r);
+    if (!Yt || !Qt || !Y || !R) {
+        free(Yt); free(Qt); free(Y); free(R);
+        return 2;
+    }
+    for (int64_t j = 1; j <= tau; ++j) {
+        mat_tmul(m, n, r, A, lda, Q, m, Yt, n);          /* step 3: Yt_j = A^T Q_{j-1}   */
+        orc_householder_qr(n, r, Yt, n, Qt, n, R, r);    /* step 4: Yt_j = Qt_j Rt_j     */
+        mat_mul(m, r, n, A, lda, Qt, n, Y, m);           /* step 5: Y_j = A Qt_j         */
+        orc_householder_qr(m, r, Y, m, Q, m, R, r);      /* step 6: Y_j = Q_j R_j        */
+    }
+    free(Yt); free(Qt); free(Y); free(R);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg. 2: BasisExt, tau subspace iterations (above), then                   */
 /*   step 8   C = Q^T A                       (r x n)                        */
 /*   step 9   C^T = V R      (QR, n x r)                                     */
 /*   step 10  R^T = Qh Dh    (QR, r x r)                                     */
@@ -308,7 +339,7 @@ int orc_basis_ext(const double *A, int64_t m, int64_t n, int64_t lda, double eps
 /* res[1] = ||A||_F, res[2] = eps used.                                      */
 /* ------------------------------------------------------------------------ */
 int orc_eod_abe(const double *A, int64_t m, int64_t n, int64_t lda, double tol,
-                int tol_mode, int64_t k, uint64_t seed, uint64_t batch,
+                int tol_mode, int64_t k, uint64_t seed, uint64_t batch, int64_t tau,
                 double *U, double *D, double *V, double *Q, double *C,
                 int64_t *r_out, double *res, double *tdiag, int64_t *ntd)
 {
@@ -325,6 +356,9 @@ int orc_eod_abe(const double *A, int64_t m, int64_t n, int64_t lda, double tol,
         res[0] = (norm_a > 0.0) ? 1.0 : 0.0;
         return 0;
     }
+    /* steps 2-7 */
+    st = subspace_iteration(A, m, n, lda, Q, r, tau);
+    if (st) return st;
     /* step 8 */
     mat_tmul(m, r, n, Q, m, A, lda, C, cap);
     /* step 9: QR of C^T (n x r) */

@@ -269,3 +269,70 @@ def test_storage_worked_example():
     bound = oracle.storage_rank_bound(m, n)
     for r in range(1, 200):
         assert (oracle.storage_entries(m, n, r) < m * n) == (r < bound)
+
+
+# --------------------------------------------------------------------------
+# Alg. 2 steps 2-7: tau subspace iterations
+# --------------------------------------------------------------------------
+
+def _gapped(m=48, n=36, r=6, seed=21):
+    """U diag(s) V^T + a small tail: r leading values in [0.3, 1], the rest
+    at 1e-3 and below, so BasisExt at eps = 0.05 ||A||_F keeps about r columns."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, min(m, n))))
+    V, _ = np.linalg.qr(rng.standard_normal((n, min(m, n))))
+    s = np.concatenate([np.linspace(1.0, 0.3, r), 1e-3 * np.geomspace(1.0, 0.1, min(m, n) - r)])
+    return np.asfortranarray((U * s) @ V.T), s
+
+
+@pytest.mark.parametrize("tau", [1, 2, 3])
+def test_subspace_iteration_spans_power_of_a_at(tau):
+    """range(Q_tau) = range((A A^T)^tau Q_0): the alternating QRs of
+    Alg. 2 steps 3-6 against matrix powers and an SVD basis (numpy)."""
+    A, _ = _gapped()
+    r0 = oracle.eod_abe(A, 0.05, 1, k=4, seed=3, tau=0)
+    rt = oracle.eod_abe(A, 0.05, 1, k=4, seed=3, tau=tau)
+    assert rt["r"] == r0["r"] and r0["r"] > 0
+    Q0, Qt = r0["Q"], rt["Q"]
+    M = Q0.copy()
+    for _ in range(tau):
+        M = A @ (A.T @ M)
+    Ub, _, _ = np.linalg.svd(M, full_matrices=False)
+    P_ref = Ub @ Ub.T
+    assert np.linalg.norm(Qt.T @ Qt - np.eye(Qt.shape[1])) <= 1e-12
+    assert np.linalg.norm(Qt @ Qt.T - P_ref) <= 1e-9
+
+
+def test_subspace_iteration_error_bounds_and_convergence():
+    """The rank stays BasisExt's; RelErr never beats the Eckart-Young optimum
+    of that rank, does not grow with tau here (gap 300x), and approaches the
+    optimum: tau = 6 is within 1e-6 of it."""
+    A, s = _gapped()
+    errs = []
+    for tau in range(0, 7):
+        res = oracle.eod_abe(A, 0.05, 1, k=4, seed=3, tau=tau)
+        r = res["r"]
+        opt = np.sqrt(np.sum(s[r:] ** 2)) / np.linalg.norm(A)
+        assert res["rel_err"] >= opt * (1 - 1e-12)
+        # A_hat = Q C with C = Q^T A: the reported error is that projection's
+        Q = res["Q"]
+        assert abs(np.linalg.norm(A - Q @ (Q.T @ A)) / np.linalg.norm(A) - res["rel_err"]) <= 1e-13
+        errs.append((res["rel_err"], opt, r))
+    assert len({e[2] for e in errs}) == 1
+    for a, b in zip(errs, errs[1:]):
+        assert b[0] <= a[0] * (1 + 1e-12)
+    assert errs[-1][0] <= errs[-1][1] * (1 + 1e-6)
+    assert errs[0][0] > errs[0][1] * (1 + 1e-4)        # tau = 0 is measurably above it
+
+
+def test_subspace_iteration_core_factors():
+    """With tau > 0 the core factors still satisfy A_hat = U D V^T = Q C,
+    U^T U = I, V^T V = I, D upper triangular with a positive diagonal."""
+    A, _ = _gapped(seed=5)
+    res = oracle.eod_abe(A, 0.05, 1, k=4, seed=7, tau=2)
+    U, D, V, Q, C = res["U"], res["D"], res["V"], res["Q"], res["C"]
+    r = res["r"]
+    assert np.allclose(np.tril(D, -1), 0.0) and np.all(np.diag(D) > 0)
+    assert np.linalg.norm(U.T @ U - np.eye(r)) <= 1e-12
+    assert np.linalg.norm(V.T @ V - np.eye(r)) <= 1e-12
+    assert np.linalg.norm(U @ D @ V.T - Q @ C) <= 1e-12 * np.linalg.norm(A)

@@ -24,6 +24,9 @@ PINS = [
     pins.test_error_identity_with_projection_norm,
     pins.test_householder_qr_zero_and_dependent_columns,
     lambda: pins.test_householder_qr_matches_lapack(40, 40),
+    lambda: pins.test_subspace_iteration_spans_power_of_a_at(1),
+    pins.test_subspace_iteration_error_bounds_and_convergence,
+    pins.test_subspace_iteration_core_factors,
 ]
 
 MUTANTS = {
@@ -41,6 +44,9 @@ MUTANTS = {
     "core_R_not_transposed": ("Rt[IX(j, i, r)] = R[IX(i, j, r)];", "Rt[IX(i, j, r)] = R[IX(i, j, r)];"),
     "relerr_not_normalised": ("res[0] = (norm_a > 0.0) ? sqrt(e2) / norm_a : 0.0;", "res[0] = sqrt(e2);"),
     "projection_uses_omega_block_zero": ("orc_omega(n, kept, f, seed, batch, Om);", "orc_omega(n, 0, f, seed, batch, Om);"),
+    "subspace_skips_a_transpose": ("mat_mul(m, r, n, A, lda, Qt, n, Y, m);", "mat_mul(m, r, n, A, lda, Yt, n, Y, m);"),
+    "subspace_one_pass_short": ("for (int64_t j = 1; j <= tau; ++j) {", "for (int64_t j = 2; j <= tau; ++j) {"),
+    "subspace_result_discarded": ("orc_householder_qr(m, r, Y, m, Q, m, R, r);      /* step 6", "orc_householder_qr(m, r, Y, m, Y, m, R, r);      /* step 6"),
 }
 
 
