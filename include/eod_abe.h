@@ -42,7 +42,7 @@ extern "C" {
 typedef enum {
     EOD_OK = 0,
     EOD_EINVAL = 1,        /* bad argument: sizes, lda, tol <= 0 or not finite,
-                              power_iters != 0, unknown enum value, NULL pointer */
+                              power_iters outside 0..16, unknown enum value, NULL pointer */
     EOD_ENOMEM = 2,        /* device or pinned host allocation failed */
     EOD_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     EOD_ENONFINITE = 4,    /* A holds a NaN or an infinity */
@@ -80,7 +80,12 @@ typedef struct {
     int32_t precision;     /* eod_precision */
     int32_t tol_mode;      /* eod_tol_mode */
     int32_t block_k;       /* block size k of Alg. 1 (1..128); 0 selects 32 */
-    int32_t power_iters;   /* tau of Alg. 2; only 0 (power-free) is accepted */
+    int32_t power_iters;   /* tau of Alg. 2 (0..16): subspace iterations after
+                              BasisExt, steps 2-7 (Y~ = A^T Q, QR, Y = A Q~, QR),
+                              on the rank BasisExt found; 0 = power-free.  The
+                              QRs are CholQR2 with positive diagonals, so Q_tau
+                              and the factors are unique given Omega; in the
+                              mixed form A^T Q uses the BF16 split and A Q~ FP32 */
     int32_t compute_err;   /* nonzero: compute RelErr (one more pass over A) */
     void *stream;          /* cudaStream_t */
     uint64_t batch_index;  /* third counter word of the Omega draw (Philox) */

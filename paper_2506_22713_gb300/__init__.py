@@ -1,5 +1,6 @@
 """Python binding of libeodabe.so, the GB300 (sm_103a) implementation of
-power-free EOD-ABE (arXiv 2506.22713, Alg. 1 and Alg. 2 with tau = 0).
+EOD-ABE (arXiv 2506.22713, Alg. 1 and Alg. 2; power-free or with tau
+subspace iterations).
 
 This module only marshals arguments: every step of the factorisation runs in
 the library's CUDA kernels.  PyTorch supplies device memory and streams.
@@ -176,7 +177,7 @@ _TOLM = {"abs": EOD_TOL_ABS, "rel": EOD_TOL_REL_FRO}
 
 
 def make_opts(dtype=EOD_F64, precision="plain", tol_mode="abs", block_k=0, compute_err=True,
-              stream=None, batch_index=0) -> EodOpts:
+              stream=None, batch_index=0, power_iters=0) -> EodOpts:
     o = EodOpts()
     _lib.eod_opts_default(ctypes.byref(o))
     o.a_dtype = dtype
@@ -188,6 +189,7 @@ def make_opts(dtype=EOD_F64, precision="plain", tol_mode="abs", block_k=0, compu
         stream = torch.cuda.current_stream()
     o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
     o.batch_index = int(batch_index)
+    o.power_iters = int(power_iters)
     return o
 
 
@@ -277,14 +279,15 @@ class Factors:
 
 
 def factor(A: torch.Tensor, tol: float, seed: int = 0, *, precision="plain", tol_mode="abs", block_k=0,
-           compute_err=True, stream=None, batch_index=0) -> Factors:
-    """Alg. 2 (tau = 0) on a column-major CUDA matrix (float64 or float32)."""
+           compute_err=True, stream=None, batch_index=0, power_iters=0) -> Factors:
+    """Alg. 2 (power_iters = tau subspace iterations, 0 = power-free) on a
+    column-major CUDA matrix (float64 or float32)."""
     if not A.is_cuda:
         raise ValueError("A must live on the GPU; use factor_host for host matrices")
     if A.dtype not in _DT:
         raise ValueError("A must be float64 or float32")
     lda = _colmajor_ld(A)
-    o = make_opts(_DT[A.dtype], precision, tol_mode, block_k, compute_err, stream, batch_index)
+    o = make_opts(_DT[A.dtype], precision, tol_mode, block_k, compute_err, stream, batch_index, power_iters)
     out = ctypes.POINTER(EodFactors)()
     st = _lib.eod_abe_factor_ex(ctypes.c_void_p(A.data_ptr()), A.shape[0], A.shape[1], lda, float(tol),
                                 int(seed), ctypes.byref(o), ctypes.byref(out))
@@ -294,7 +297,7 @@ def factor(A: torch.Tensor, tol: float, seed: int = 0, *, precision="plain", tol
 
 
 def factor_host(A: torch.Tensor, tol: float, seed: int = 0, *, precision="plain", tol_mode="abs", block_k=0,
-                compute_err=True, stream=None, U_out=None, D_out=None, V_out=None):
+                compute_err=True, stream=None, U_out=None, D_out=None, V_out=None, power_iters=0):
     """Host matrix in, host factors out (through eod_abe_factor_host).
     Returns (rank, rel_err)."""
     if A.is_cuda:
@@ -302,7 +305,7 @@ def factor_host(A: torch.Tensor, tol: float, seed: int = 0, *, precision="plain"
     lda = _colmajor_ld(A)
     m, n = A.shape
     cap = min(m, n)
-    o = make_opts(_DT[A.dtype], precision, tol_mode, block_k, compute_err, stream)
+    o = make_opts(_DT[A.dtype], precision, tol_mode, block_k, compute_err, stream, 0, power_iters)
     rank = ctypes.c_int64(0)
     rel = ctypes.c_double(0.0)
 
@@ -317,7 +320,7 @@ def factor_host(A: torch.Tensor, tol: float, seed: int = 0, *, precision="plain"
 
 
 def factor_batched(mats, tol: float, seed: int = 0, *, precision="plain", tol_mode="abs", block_k=0,
-                   compute_err=True, stream=None):
+                   compute_err=True, stream=None, power_iters=0):
     """Factors a list of column-major CUDA matrices of one dtype; returns
     (list of Factors or None, list of statuses)."""
     count = len(mats)
@@ -328,7 +331,7 @@ def factor_batched(mats, tol: float, seed: int = 0, *, precision="plain", tol_mo
     Ls = (ctypes.c_int64 * count)(*[_colmajor_ld(a) for a in mats])
     outs = (ctypes.POINTER(EodFactors) * count)()
     stat = (ctypes.c_int32 * count)()
-    o = make_opts(_DT[dt], precision, tol_mode, block_k, compute_err, stream)
+    o = make_opts(_DT[dt], precision, tol_mode, block_k, compute_err, stream, 0, power_iters)
     _lib.eod_abe_factor_batched(P, Ms, Ns, Ls, count, float(tol), int(seed), ctypes.byref(o), outs, stat)
     res = [Factors(outs[i]) if stat[i] == EOD_OK else None for i in range(count)]
     return res, [int(s) for s in stat]

@@ -192,17 +192,27 @@ __global__ void __launch_bounds__(256) chol_small_kernel(const double *__restric
     if (!Rinv) return;
     __syncthreads();
     for (int j = tid; j < p; j += blockDim.x) sq[j] = 1.0 / sq[j];
-    // Z = L^{-1} in place of L (strictly lower part): at step k the entries
-    // (i > k, c < k) take Z(i,c) -= L(i,k) Z(k,c), then column k becomes
-    // Z(i,k) = -L(i,k) (its first term; later steps add the rest)
-    for (int k = 0; k < p; ++k) {
+    // Z = L^{-1} in place of L (strictly lower part).  With M = -L stored
+    // first, step k takes Z(i,c) += M(i,k) Z(k,c) for i > k, c < k; column k
+    // still holds M(i,k) = Z(i,k)'s first term when step k reads it, so one
+    // barrier per step suffices.
+    for (int c = ty; c < p; c += 16)
+        for (int i = tx; i < p; i += 16)
+            if (i > c) S[i + c * w] = -S[i + c * w];
+    __syncthreads();
+    for (int k = 1; k < p - 1; ++k) {
         const int rows = p - 1 - k, cnt = rows * k;
+        // entry e = c * rows + (i - k - 1), i fastest (conflict-free column
+        // accesses); advanced by the block size without a division per entry
+        const int dc = (int)blockDim.x / rows, di = (int)blockDim.x - dc * rows;
+        int c = tid / rows, io = tid - c * rows;
         for (int e = tid; e < cnt; e += blockDim.x) {
-            const int i = k + 1 + e % rows, c = e / rows;   // i fastest: conflict-free column accesses
-            S[i + c * w] = fma(-S[i + k * w], S[k + c * w], S[i + c * w]);
+            const int i = k + 1 + io;
+            S[i + c * w] = fma(S[i + k * w], S[k + c * w], S[i + c * w]);
+            c += dc;
+            io += di;
+            if (io >= rows) { io -= rows; ++c; }
         }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < p; i += blockDim.x) S[i + k * w] = -S[i + k * w];
         __syncthreads();
     }
     // R^{-1}(i, c) = Z(c, i) / sqrt(d_c) for i < c, 1/sqrt(d_c) on the diagonal

@@ -67,6 +67,9 @@ struct HostMirror {
 
 inline int64_t round_up8(int64_t x) { return (x + 7) / 8 * 8; }
 
+// largest tau (subspace iterations of Alg. 2) accepted
+constexpr int kMaxPowerIters = 16;
+
 // smallest eps / ||A||_F the FP32-data paths accept (see factor_impl)
 constexpr double kMixedFloor = 1e-5;
 constexpr double kF32Floor = 1e-5;
@@ -563,19 +566,65 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(ar.get(&Rt, (size_t)r * r));
     EOD_TRY(ar.get(&D, (size_t)r * r));
     EOD_TRY(ar.get(&Rc, (size_t)r * r));
-    {
-        Phase ph("eod.projection");
+    // work space of the CholQR passes (subspace iteration and core)
+    CoreWork<T> cw;
+    cw.pcap = r;
+    const int64_t nblk = (r + kNB - 1) / kNB;
+    EOD_TRY(ar.get(&cw.G, (size_t)r * r));
+    EOD_TRY(ar.get(&cw.R, (size_t)r * r));
+    EOD_TRY(ar.get(&cw.Rp, (size_t)kNB * kNB + (size_t)r * r));
+    EOD_TRY(ar.get(&cw.Inv, (size_t)nblk * kNB * kNB));
+    EOD_TRY(ar.get(&cw.RiD, (size_t)((r + kPB - 1) / kPB) * kPB * kPB));
+    EOD_TRY(ar.get(&cw.RiT, (size_t)kPB * kPB));
+    EOD_TRY(ar.get(&cw.trace, 1));
+    EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kPB) * kPB));
+    EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kPB));
+    EOD_TRY(ar.get(&cw.info, (size_t)2 * nblk));
+
+    // Ct (n x r) = A^T Q: Alg. 2 step 8 (transposed), and step 3 of each
+    // subspace iteration
+    auto project = [&]() -> eod_status {
         if (mixed) {
             EOD_TRY(mx.project(Qb, r, Ct, s));
+        } else if (oz.on) {
+            const OzOperand acol{oz.Acol, oz.eAcol, 0, oz.m8, n * oz.m8};
+            const OzOperand qc{oz.Qc, oz.eQc, 0, oz.m8, cap * oz.m8};
+            EOD_CU(oz_gemm_ops(acol, qc, n, r, m, 1.0, 0.0, (double *)Ct, n, ex, ws.err_flag, s));
         } else {
-            if (oz.on) {
-                const OzOperand acol{oz.Acol, oz.eAcol, 0, oz.m8, n * oz.m8};
-                const OzOperand qc{oz.Qc, oz.eQc, 0, oz.m8, cap * oz.m8};
-                EOD_CU(oz_gemm_ops(acol, qc, n, r, m, 1.0, 0.0, (double *)Ct, n, ex, ws.err_flag, s));
-            } else {
-                EOD_CU((gemm<T, T, T, T>(true, false, n, r, m, 1.0, A, lda, Qb, m, 0.0, Ct, n, ex, &ws, s)));
-            }
+            EOD_CU((gemm<T, T, T, T>(true, false, n, r, m, 1.0, A, lda, Qb, m, 0.0, Ct, n, ex, &ws, s)));
         }
+        return EOD_OK;
+    };
+
+    // ---- Alg. 2 steps 2-7: tau subspace iterations on the rank-r basis ----
+    if (o.power_iters > 0) {
+        Phase ph("eod.subspace_iteration");
+        uint16_t *qts = nullptr;
+        int *eqt = nullptr;
+        const int64_t n8 = round_up8(n);
+        if (oz.on) {
+            EOD_TRY(ar.get(&qts, (size_t)kOzSlices * r * n8));
+            EOD_TRY(ar.get(&eqt, (size_t)r));
+        }
+        for (int it = 0; it < o.power_iters; ++it) {
+            EOD_TRY(project());                                          // step 3: Yt = A^T Q
+            EOD_TRY(cholqr2(cw, Ct, n, n, r, Rc, hm, &ws, s));            // step 4: Yt = Qt Rt
+            if (oz.on) {                                                 // step 5: Y = A Qt
+                // B operand Qt: rows = its r columns, K = n
+                EOD_CU(oz_slice((const double *)Ct, r, n, n, 1, qts, eqt, 0, n8, r * n8, s));
+                const OzOperand qto{qts, eqt, 0, n8, r * n8};
+                EOD_CU(oz_gemm_ops(oz.arow(), qto, m, r, n, 1.0, 0.0, (double *)Qb, m, ex, ws.err_flag, s));
+            } else {
+                EOD_CU((gemm<T, T, T, T>(false, false, m, r, n, 1.0, A, lda, Ct, n, 0.0, Qb, m, ex, &ws, s)));
+            }
+            EOD_TRY(cholqr2(cw, Qb, m, m, r, Rc, hm, &ws, s));            // step 6: Y = Q R
+            EOD_CU(oz_append(0, r));                                     // slices of the new Q
+        }
+    }
+
+    {
+        Phase ph("eod.projection");
+        EOD_TRY(project());
     }
 
     // ---- reconstruction error: || A - Q C ||_F / ||A||_F ----
@@ -612,19 +661,6 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     }
 
     // ---- steps 9-11 ----
-    CoreWork<T> cw;
-    cw.pcap = r;
-    const int64_t nblk = (r + kNB - 1) / kNB;
-    EOD_TRY(ar.get(&cw.G, (size_t)r * r));
-    EOD_TRY(ar.get(&cw.R, (size_t)r * r));
-    EOD_TRY(ar.get(&cw.Rp, (size_t)kNB * kNB + (size_t)r * r));
-    EOD_TRY(ar.get(&cw.Inv, (size_t)nblk * kNB * kNB));
-    EOD_TRY(ar.get(&cw.RiD, (size_t)((r + kPB - 1) / kPB) * kPB * kPB));
-    EOD_TRY(ar.get(&cw.RiT, (size_t)kPB * kPB));
-    EOD_TRY(ar.get(&cw.trace, 1));
-    EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kPB) * kPB));
-    EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kPB));
-    EOD_TRY(ar.get(&cw.info, (size_t)2 * nblk));
     Phase ph_core("eod.core");
     EOD_CU((copy_matrix<T, T>(Ct, n, V, n, n, r, false, s)));
     EOD_TRY(cholqr2(cw, V, n, n, r, Rc, hm, &ws, s));                 // C^T = V R
@@ -668,7 +704,7 @@ eod_status factor_mixed_from_f64(const double *A, int64_t m, int64_t n, int64_t 
 static eod_status validate(const void *A, int64_t m, int64_t n, int64_t lda, double tol, const eod_opts &o) {
     if (!A || m < 1 || n < 1 || lda < m) return EOD_EINVAL;
     if (!(tol > 0.0) || !std::isfinite(tol)) return EOD_EINVAL;
-    if (o.power_iters != 0) return EOD_EINVAL;
+    if (o.power_iters < 0 || o.power_iters > kMaxPowerIters) return EOD_EINVAL;
     if (o.a_dtype != EOD_F64 && o.a_dtype != EOD_F32) return EOD_EINVAL;
     if (o.precision != EOD_PLAIN && o.precision != EOD_MIXED_BF16) return EOD_EINVAL;
     if (o.tol_mode != EOD_TOL_ABS && o.tol_mode != EOD_TOL_REL_FRO) return EOD_EINVAL;

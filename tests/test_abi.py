@@ -68,7 +68,7 @@ def test_factor_rejects_null_and_bad_options(eod):
     out = ctypes.POINTER(eod.EodFactors)()
     assert eod.eod_abe_factor(None, 4, 4, 4, 1e-3, 1, ctypes.byref(out)) == eod.EOD_EINVAL
     dummy = ctypes.c_void_p(0x1000)
-    for field, val in [("power_iters", 1), ("a_dtype", 7), ("precision", 9), ("tol_mode", 3), ("block_k", 129),
+    for field, val in [("power_iters", -1), ("power_iters", 17), ("a_dtype", 7), ("precision", 9), ("tol_mode", 3), ("block_k", 129),
                        ("block_k", -1)]:
         o = eod.EodOpts()
         eod.eod_opts_default(ctypes.byref(o))
