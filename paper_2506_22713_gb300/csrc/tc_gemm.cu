@@ -66,13 +66,16 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;          // 16 KB
     static constexpr int B_BYTES = BN_ * BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = (BN_ >= 256) ? 4 : (BN_ >= 128 ? 6 : 8);
+    // The fused error epilogue reads a tile of A after the MMAs; two stages
+    // leave room for a second CTA on the SM, whose MMAs overlap that read.
+    static constexpr int STAGES = (EPI == EPI_ERR) ? 2 : ((BN_ >= 256) ? 4 : (BN_ >= 128 ? 6 : 8));
     static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
     static constexpr uint32_t TMEM_COLS = BN_ < 32 ? 32 : BN_;
 };
 
 template <bool A_MN, int BN_, int EPI>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_gemm_kernel(const __grid_constant__ Maps maps, Params p) {
+__global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kernel(const __grid_constant__ Maps maps,
+                                                                                   Params p) {
     using C = Cfg<A_MN, BN_, EPI>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
