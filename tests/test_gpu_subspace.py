@@ -94,3 +94,20 @@ def test_batched_subspace_iteration_equals_single_calls(eod):
         assert torch.equal(f.U, res[i].U) and torch.equal(f.D, res[i].D)
         f.close()
         res[i].close()
+
+
+def test_subspace_iteration_edge_cases(eod):
+    """A zero matrix keeps rank 0 with tau > 0; a wide matrix (m < n) and
+    a rank-1 matrix go through the iterations and match the oracle."""
+    Z = torch.zeros((30, 40), dtype=torch.float64, device="cuda").t()
+    f = eod.factor(Z, 1e-6, 1, power_iters=2)
+    assert f.rank == 0 and f.rel_err == 0.0
+    f.close()
+    rng = np.random.default_rng(12)
+    for A in (np.asfortranarray(rng.standard_normal((60, 9)) @ rng.standard_normal((9, 150))),
+              np.asfortranarray(np.outer(rng.standard_normal(70), rng.standard_normal(50)))):
+        ref = oracle.eod_abe(A, 1e-9, 1, k=4, seed=3, tau=1)
+        f = eod.factor(torch.from_numpy(A).cuda(), 1e-9, 3, block_k=4, tol_mode="rel", power_iters=1)
+        assert f.rank == ref["r"]
+        assert abs(f.rel_err - ref["rel_err"]) <= 1e-10
+        f.close()

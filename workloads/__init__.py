@@ -113,6 +113,23 @@ def pixel_batch(count: int = 256, lo: int = 256, hi: int = 2048, rlo: int = 8, r
                     meta={"r_signal": ranks})
 
 
+def rgb_image(m: int = 220, n: int = 220, ranks=(50, 52, 53), seed: int = 6) -> Workload:
+    """Synthetic colour image: three nonnegative channels of exact ranks
+    `ranks` (products of nonnegative uniform factors), scaled to [0, 255],
+    FP64 storage -- the shape of the toy example of Sec. 1 (220 x 220,
+    ranks 50, 52, 53).  Relative tol 1e-10 reveals the exact ranks."""
+    rng = np.random.default_rng(seed)
+    chans = []
+    for r in ranks:
+        W = rng.uniform(0.0, 1.0, (m, r))
+        H = rng.uniform(0.0, 1.0, (r, n))
+        C = W @ H
+        chans.append(np.asfortranarray(255.0 * C / C.max()))
+    return Workload(f"rgb_{m}x{n}", chans, "f64", 1e-10, 1, seed,
+                    note="3 nonnegative channels, exact ranks " + ",".join(str(r) for r in ranks),
+                    meta={"r_signal": list(ranks)})
+
+
 def hyperspectral(pixels: int = 512 * 512, bands: int = 224, endmembers: int = 12, seed: int = 5,
                   tol: float = 0.047, snr_db: float = 30.0) -> Workload:
     """Unfolded hyperspectral cube (pixels x bands) = abundances (Dirichlet
