@@ -92,17 +92,47 @@ __global__ void omega_kernel(int64_t n, int64_t col0, int64_t ncols, uint64_t se
 template <typename T>
 __global__ void sumsq_kernel(const T *__restrict__ A, int64_t m, int64_t n, int64_t lda,
                              double *partials, int *flags) {
+    // Tasks are (column, chunk of 4 x blockDim rows): one 64-bit division per
+    // task, coalesced rows inside it.  Non-finite entries are found on the
+    // exponent bits.  FP64 data: FP64 FMA per entry.  FP32 data: the square
+    // is formed exactly as p + e (p = x*x, e = fma(x, x, -p)) and summed with
+    // TwoSum in FP32, the errors in a second FP32 accumulator, both widened
+    // to FP64 at the end (about 2^-48 relative): the FP64 pipe, 64 cycles per
+    // warp instruction on this GPU, stays out of the per-entry work.
     __shared__ double red[32];
-    double acc = 0.0;
+    constexpr int U = 4;
+    const int64_t chunk = (int64_t)blockDim.x * U;
+    const int64_t nch = (m + chunk - 1) / chunk;
+    const int64_t tasks = nch * n;
     int bad = 0;
-    const int64_t total = m * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % m, j = e / m;
-        const double v = (double)A[i + j * lda];
-        if (!isfinite(v)) bad = 1;
-        acc = fma(v, v, acc);
+    double dacc = 0.0;
+    float s = 0.f, c = 0.f;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const int64_t j = t / nch, i0 = (t - j * nch) * chunk;
+        const T *col = A + j * lda;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * (int64_t)blockDim.x + threadIdx.x;
+            if (i < m) {
+                const T x = col[i];
+                if (sizeof(T) == 8) {
+                    const unsigned long long b = (unsigned long long)__double_as_longlong((double)x);
+                    bad |= ((b >> 52) & 0x7ff) == 0x7ff;
+                    dacc = fma((double)x, (double)x, dacc);
+                } else {
+                    const float xf = (float)x;
+                    bad |= ((__float_as_uint(xf) >> 23) & 0xff) == 0xff;
+                    const float pr = xf * xf;
+                    const float er = fmaf(xf, xf, -pr);
+                    const float tt = s + pr;
+                    const float z = tt - s;
+                    c += ((s - (tt - z)) + (pr - z)) + er;
+                    s = tt;
+                }
+            }
+        }
     }
+    const double acc = (sizeof(T) == 8) ? dacc : (double)s + (double)c;
     const double tot = block_sum(acc, red);
     bad = __syncthreads_or(bad);
     if (threadIdx.x == 0) {

@@ -261,23 +261,40 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
 __global__ void split_norm_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                                   __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
                                   __nv_bfloat16 *__restrict__ x3, int64_t ldo, double *partials, int *flags) {
+    // (column, chunk of 4 x blockDim rows) tasks: one 64-bit division per
+    // task; the sum of squares compensated in FP32 (exact squares p + e,
+    // TwoSum), widened to FP64 per thread; non-finite entries on the bits
     __shared__ double red[32];
-    double acc = 0.0;
+    constexpr int U = 4;
+    const int64_t chunk = (int64_t)blockDim.x * U;
+    const int64_t nch = (rows + chunk - 1) / chunk;
+    const int64_t tasks = nch * cols;
     int bad = 0;
-    const int64_t total = rows * cols;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % rows, j = e / rows;
-        const float x = X[i + j * ldx];
-        if (!isfinite(x)) bad = 1;
-        acc = fma((double)x, (double)x, acc);
-        __nv_bfloat16 h, l;
-        split_bf16(x, h, l);
-        hi[i + j * ldo] = h;
-        lo[i + j * ldo] = l;
-        if (x3) x3[i + j * ldo] = __float2bfloat16_rn((x - __bfloat162float(h)) - __bfloat162float(l));
+    float sacc = 0.f, cacc = 0.f;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const int64_t j = t / nch, i0 = (t - j * nch) * chunk;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * (int64_t)blockDim.x + threadIdx.x;
+            if (i < rows) {
+                const float x = X[i + j * ldx];
+                bad |= ((__float_as_uint(x) >> 23) & 0xff) == 0xff;
+                const float pr = x * x;
+                const float er = fmaf(x, x, -pr);
+                const float tt = sacc + pr;
+                const float z = tt - sacc;
+                cacc += ((sacc - (tt - z)) + (pr - z)) + er;
+                sacc = tt;
+                __nv_bfloat16 h, l;
+                split_bf16(x, h, l);
+                hi[i + j * ldo] = h;
+                lo[i + j * ldo] = l;
+                if (x3) x3[i + j * ldo] = __float2bfloat16_rn((x - __bfloat162float(h)) - __bfloat162float(l));
+            }
+        }
     }
     if (partials) {
-        const double tot = block_sum(acc, red);
+        const double tot = block_sum((double)sacc + (double)cacc, red);
         bad = __syncthreads_or(bad);
         if (threadIdx.x == 0) {
             partials[blockIdx.x] = tot;
