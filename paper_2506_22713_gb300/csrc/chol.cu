@@ -31,10 +31,11 @@ __device__ __forceinline__ long long dkey(double x) {
 }
 
 // 1/d for finite d > 0: FP32 reciprocal of the mantissa as the seed (the
-// exponent handled on the integer bits), then two Newton steps
-// r <- r + r (1 - d r) in FP64, each doubling the 23 correct bits.  No FP64
-// division anywhere (each FP64 instruction costs a warp 64 cycles here):
-// a subnormal d gives +inf, a d near the top of the range 0.
+// exponent handled on the integer bits, relative error e below 2^-22), then
+// one third-order step r <- r (1 + e + e^2), e = 1 - d r, in three dependent
+// FP64 FMAs (the error left is e^3, far below 2^-53).  No FP64 division
+// anywhere (each FP64 instruction costs a warp 64 cycles here): a subnormal d
+// gives +inf, a d near the top of the range 0.
 __device__ __forceinline__ double recip_pos(double d) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const int E = (int)(b >> 52);                                  // biased exponent
@@ -43,23 +44,23 @@ __device__ __forceinline__ double recip_pos(double d) {
     const unsigned int rb = __float_as_uint(rf);
     const long long re = (long long)((rb >> 23) & 0xff) - 127 + 1023 - (E - 1023);
     const long long rbits = (re << 52) | ((long long)(rb & 0x7fffffu) << 29);
-    double r = __longlong_as_double(rbits);
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
+    const double r0 = __longlong_as_double(rbits);
+    const double e = fma(-d, r0, 1.0);
+    const double r = fma(r0, fma(e, e, e), r0);
     const double inf = __longlong_as_double(0x7ff0000000000000ll);
     return (E == 0 || re >= 2047) ? inf : (re <= 0 ? 0.0 : r);
 }
 
-// Pivot decision for column j (one thread) on the integer keys: the rank test
+// Pivot decision for column j (one warp, lane 0 publishes): the rank test
 // when `decide` (thresholds precomputed per column), else positivity.  A
 // non-finite pivot is undecided (rank test) or a failure.  On acceptance
-// *rd = 1/d.
-__device__ __forceinline__ void ldl_pivot(const double *S, int w, int j, const long long *klo, const long long *khi,
-                                          const long long *krg, int decide, double *dv, int *go, double *rd,
-                                          int *p_out, int *code, bool writer) {
-    const double d = S[j + j * w];
+// *rd = 1/d_j and *mt = -L(j+1, j), the multiplier the next column update
+// needs.
+__device__ __forceinline__ void ldl_pivot(const double *S, int ld, int w, int j, const long long *klo,
+                                          const long long *khi, const long long *krg, int decide, double *dv,
+                                          int *go, double *rd, double *mt, int *p_out, int *code, bool writer) {
+    const double d = S[j + j * ld];
+    const double below = (j + 1 < w) ? S[(j + 1) + j * ld] : 0.0;
     const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
     const bool finite = ((bits >> 52) & 0x7ff) != 0x7ff;
     const long long kd = dkey(d);
@@ -76,10 +77,12 @@ __device__ __forceinline__ void ldl_pivot(const double *S, int w, int j, const l
         if (!keep) c = CHOL_FAIL;
     }
     const double r = recip_pos(d);
+    const double t = below * r;
     if (writer) {
         if (keep) {
             dv[j] = d;
             *rd = r;
+            *mt = -t;
         } else {
             *p_out = j;
             *code = c;
@@ -88,42 +91,80 @@ __device__ __forceinline__ void ldl_pivot(const double *S, int w, int j, const l
     }
 }
 
-// One CTA of 256 threads: G + shift I = L D L^T (unit lower L, no square
-// roots on the critical path), R = D^{1/2} L^T, and optionally
-// R^{-1} = L^{-T} D^{-1/2}.  Step j, once pivot j is accepted:
-//   (A) every thread takes rows i > j: keeps u_i = S(i,j), stores
-//       L(i,j) = u_i / d_j, and updates column j+1: S(i,j+1) -= L(i,j) u_{j+1};
-//   (B) warp 0 decides pivot j+1 (integer compares, reciprocal by Newton)
-//       while warps 1-7 apply S(ii,ll) -= L(ii,j) u_ll to the rest of the
-//       trailing triangle, spread evenly over the threads through a table of
-//       (row, column) pairs ordered by column from the right (the entries of
-//       columns > c form a prefix of it).
+constexpr int kLeafThreads = 256;
+
+size_t leaf_smem_bytes(int w) {
+    return sizeof(double) * ((size_t)w * (w + 1) + 4 * (size_t)w) + sizeof(long long) * 3 * (size_t)w +
+           sizeof(uint16_t) * (size_t)((w - 1) * (w - 2) / 2 + 1);
+}
+
+// One CTA: G + shift I = L D L^T (unit lower L, no square roots on the
+// critical path), R = D^{1/2} L^T and, in the same steps, Z = L^{-1} (so
+// R^{-1} = L^{-T} D^{-1/2}) by Gauss-Jordan: once L(:,j) is known, every row
+// r > j takes S(r, c) += M(r) S(j, c) with M = -L(:, j), for the trailing
+// columns j+2 <= c <= r (the Schur update) and for c < j (the rows of Z).
+// Storage, one w x (w+1) array (odd stride: rows and columns are both read
+// without bank conflicts): the trailing lower triangle; Z in the strict lower
+// part of the finished columns; row j of the upper part holds u = column j
+// before scaling (R's row j up to 1/sqrt(d_j)).  Step j, pivot j accepted:
+//   (A) column j+1 takes its update (threads 0-127), the u row and M are
+//       staged (threads 128-255, rows 0-63 on warps 6-7 so that the two
+//       FP64 instructions of a row run on different sub-partitions);
+//   (B) warp 0 decides pivot j+1 (integer compares, reciprocal by a
+//       third-order step) and computes -L(j+2, j+1); warp 4 stores M as
+//       Z's column j; warps 1-3 and 5-7 apply the updates, spread evenly
+//       through a table of (row, k) pairs ordered by row from the bottom
+//       (row r holds r-1 entries, so the rows > j form a prefix).
+// Warp 4 shares warp 0's sub-partition and issues no FP64 work, leaving that
+// FP64 pipe (64 cycles per warp instruction) to the pivot chain.
 // The rank test reads the pivots d_j = T(j,j)^2 exactly as the Cholesky form
 // would; R differs from a square-root Cholesky only by rounding.
-__global__ void __launch_bounds__(256) chol_small_kernel(const double *__restrict__ G, int64_t ldg, int w,
-                                                         int decide, double eps2, double delta_coef, double rho,
-                                                         double shift, double *__restrict__ R,
-                                                         double *__restrict__ Rinv, int64_t ldr, int *info) {
+__global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *__restrict__ G, int64_t ldg, int w,
+                                                                  int decide, double eps2, double delta_coef,
+                                                                  double rho, double shift, double *__restrict__ R,
+                                                                  double *__restrict__ Rinv, int64_t ldr,
+                                                                  int *info) {
+    constexpr int NT = kLeafThreads;
     extern __shared__ double sh[];
-    double *S = sh;                                    // w x w, lower triangle
-    double *u = S + w * w;                             // unscaled column of the step
-    double *dv = u + w;                                // pivots d_j
-    double *sq = dv + w;                               // sqrt(d_j), then 1/sqrt(d_j)
-    long long *klo = (long long *)(sq + w);            // keys of eps^2 - delta_j, eps^2 + delta_j, rho G(j,j)
+    const int ld = w + 1;
+    double *S = sh;                                    // w x ld
+    double *mcol = S + w * ld;                         // M = -L(:, j) of the current step
+    double *dv = mcol + w;                             // pivots d_j
+    double *sq = dv + w;                               // sqrt(d_j)
+    double *rs = sq + w;                               // 1 / sqrt(d_j)
+    long long *klo = (long long *)(rs + w);            // keys of eps^2 - delta_j, eps^2 + delta_j, rho G(j,j)
     long long *khi = klo + w;
     long long *krg = khi + w;
-    uint16_t *pairs = (uint16_t *)(krg + w);           // w (w - 1) / 2 entries: row | column << 8
+    uint16_t *ent = (uint16_t *)(krg + w);             // (w-1)(w-2)/2 entries: row | k << 8
     __shared__ int p_sh, code_sh, go_sh;
-    __shared__ double rd_sh;
-    const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    __shared__ double rd_sh, mt_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // S(i, c) = G(c, i) for i >= c (G's upper triangle, transposed)
-    for (int c = ty; c < w; c += 16)
-        for (int i = tx; i < w; i += 16)
-            S[i + c * w] = (i >= c) ? G[c + (int64_t)i * ldg] + (i == c ? shift : 0.0) : 0.0;
+    // S(i, c) = G(c, i) for i >= c: G's upper triangle read along its columns
+    // (coalesced), eight loads in flight per thread
+    {
+        const int tot = w * w, di = NT / w, dc = NT - di * w;
+        int i = tid / w, c = tid - i * w;
+        for (int e0 = tid; e0 < tot; e0 += 8 * NT) {
+            double v[8];
+            int ii[8], cc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                ii[q] = i;
+                cc[q] = c;
+                v[q] = (e0 + q * NT < tot && c <= i) ? G[c + (int64_t)i * ldg] : 0.0;
+                c += dc;
+                i += di;
+                if (c >= w) { c -= w; ++i; }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (e0 + q * NT < tot && cc[q] <= ii[q])
+                    S[ii[q] + cc[q] * ld] = v[q] + (ii[q] == cc[q] ? shift : 0.0);
+        }
+    }
     if (decide) {
-        for (int j = tid; j < w; j += blockDim.x) {
+        for (int j = tid; j < w; j += NT) {
             const double g0 = G[j + (int64_t)j * ldg];
             const double delta = delta_coef * g0;
             klo[j] = dkey(eps2 - delta);
@@ -131,94 +172,91 @@ __global__ void __launch_bounds__(256) chol_small_kernel(const double *__restric
             krg[j] = dkey(rho * g0);
         }
     }
-    const int npairs = w * (w - 1) / 2;
-    for (int e = tid; e < npairs; e += blockDim.x) {
-        // column ll = w - 1 - c holds c + 1 entries; columns w-1 .. ll hold (c+1)(c+2)/2
-        int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while ((c + 1) * (c + 2) / 2 <= e) ++c;
-        while (c * (c + 1) / 2 > e) --c;
-        const int ll = w - 1 - c, ii = ll + (e - c * (c + 1) / 2);
-        pairs[e] = (uint16_t)(ii | (ll << 8));
+    // row r (2 <= r < w) holds k = 0 .. r-2 (column k, or k+2 once k >= j);
+    // rows r+1 .. w-1 come before it: sum of (x - 1) for x > r
+    for (int r = w - 1 - warp; r >= 2; r -= NT / 32) {
+        const int off = ((w - 2) * (w - 1) - (r - 1) * r) / 2;
+        for (int k = lane; k < r - 1; k += 32) ent[off + k] = (uint16_t)(r | (k << 8));
     }
     if (tid == 0) {
         p_sh = w;
         code_sh = CHOL_ALL;
     }
     __syncthreads();
-    if (tid < 32) ldl_pivot(S, w, 0, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh, tid == 0);
+    if (warp == 0) ldl_pivot(S, ld, w, 0, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &mt_sh, &p_sh, &code_sh, tid == 0);
     __syncthreads();
 
+    constexpr int NW = (NT / 32 - NT / 128) * 32;          // update threads: warps not on sub-partition 0
+    const bool worker = (warp & 3) != 0;
+    const int me = (warp - (warp >> 2) - 1) * 32 + lane;
     for (int j = 0; j < w; ++j) {
         if (!go_sh) break;
-        const double rd = rd_sh;
-        const bool next = j + 1 < w;
-        const double u1 = next ? S[(j + 1) + j * w] : 0.0;   // row j+1 is scaled in (B)
-        for (int i = j + 1 + tid; i < w; i += blockDim.x) {
-            const double ui = S[i + j * w];
-            const double lij = ui * rd;
-            u[i] = ui;
-            if (i > j + 1) S[i + j * w] = lij;
-            S[i + (j + 1) * w] = fma(-lij, u1, S[i + (j + 1) * w]);
+        const double rd = rd_sh, mt = mt_sh;
+        // (A)
+        if (tid < 128) {
+            const int i = j + 1 + tid;
+            if (i < w) S[i + (j + 1) * ld] = fma(S[i + j * ld], mt, S[i + (j + 1) * ld]);
+        } else {
+            const int i = j + 1 + ((tid - 64) & 127);
+            if (i < w) {
+                const double ui = S[i + j * ld];
+                S[j + i * ld] = ui;
+                mcol[i] = -(ui * rd);
+            }
         }
         __syncthreads();
-        if (!next) break;
-        if (tid < 32) {
-            // the whole warp computes the pivot (no divergence on the
-            // critical path; FP64 costs a warp the same for 1 or 32 lanes),
-            // lane 0 publishes it
-            ldl_pivot(S, w, j + 1, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &p_sh, &code_sh, tid == 0);
-        } else if (tid >= 32 && (tid >> 5) != 4) {
-            // warps 1-3 and 5-7: warp 4 shares warp 0's sub-partition, whose
-            // FP64 pipe (64 cycles per warp instruction) stays free for the pivot
-            if (tid == 32) S[(j + 1) + j * w] = u1 * rd;
-            const int cnt = (w - 2 - j) * (w - 1 - j) / 2;
-            const int me = tid - 32 - ((tid >> 5) > 4 ? 32 : 0);
-            for (int e = me; e < cnt; e += blockDim.x - 64) {
-                const int pr = pairs[e];
-                const int ii = pr & 0xff, ll = pr >> 8;
-                S[ii + ll * w] = fma(-S[ii + j * w], u[ll], S[ii + ll * w]);
+        if (j + 1 >= w) break;
+        // (B)
+        if (warp == 0) {
+            ldl_pivot(S, ld, w, j + 1, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &mt_sh, &p_sh, &code_sh, tid == 0);
+        } else if (warp == 4) {
+            for (int i = j + 1 + lane; i < w; i += 32) S[i + j * ld] = mcol[i];
+        } else if (worker) {
+            const int cnt = ((w - 2) * (w - 1) - j * (j - 1)) / 2;
+            int e = me;
+            for (; e + NW < cnt; e += 2 * NW) {   // two entries in flight
+                const int pa = ent[e], pb = ent[e + NW];
+                const int ra = pa & 0xff, ka = pa >> 8, rb = pb & 0xff, kb = pb >> 8;
+                const int ca = ka < j ? ka : ka + 2, cb = kb < j ? kb : kb + 2;
+                const double ma = mcol[ra], mb = mcol[rb];
+                const double xa = S[j + ca * ld], xb = S[j + cb * ld];
+                const double sa = S[ra + ca * ld], sb = S[rb + cb * ld];
+                S[ra + ca * ld] = fma(ma, xa, sa);
+                S[rb + cb * ld] = fma(mb, xb, sb);
+            }
+            if (e < cnt) {
+                const int pa = ent[e];
+                const int ra = pa & 0xff, ka = pa >> 8;
+                const int ca = ka < j ? ka : ka + 2;
+                S[ra + ca * ld] = fma(mcol[ra], S[j + ca * ld], S[ra + ca * ld]);
             }
         }
         __syncthreads();
     }
     const int p = p_sh;
-    for (int j = tid; j < p; j += blockDim.x) sq[j] = sqrt(dv[j]);
-    __syncthreads();
-    // R(i, c) = sqrt(d_i) L(c, i) for i < c, sqrt(d_i) on the diagonal
-    for (int c = ty; c < p; c += 16)
-        for (int i = tx; i < p; i += 16)
-            R[i + (int64_t)c * ldr] = (i < c) ? sq[i] * S[c + i * w] : (i == c ? sq[i] : 0.0);
-    if (tid == 0) { info[0] = p; info[1] = code_sh; }
-    if (!Rinv) return;
-    __syncthreads();
-    for (int j = tid; j < p; j += blockDim.x) sq[j] = 1.0 / sq[j];
-    // Z = L^{-1} in place of L (strictly lower part).  With M = -L stored
-    // first, step k takes Z(i,c) += M(i,k) Z(k,c) for i > k, c < k; column k
-    // still holds M(i,k) = Z(i,k)'s first term when step k reads it, so one
-    // barrier per step suffices.
-    for (int c = ty; c < p; c += 16)
-        for (int i = tx; i < p; i += 16)
-            if (i > c) S[i + c * w] = -S[i + c * w];
-    __syncthreads();
-    for (int k = 1; k < p - 1; ++k) {
-        const int rows = p - 1 - k, cnt = rows * k;
-        // entry e = c * rows + (i - k - 1), i fastest (conflict-free column
-        // accesses); advanced by the block size without a division per entry
-        const int dc = (int)blockDim.x / rows, di = (int)blockDim.x - dc * rows;
-        int c = tid / rows, io = tid - c * rows;
-        for (int e = tid; e < cnt; e += blockDim.x) {
-            const int i = k + 1 + io;
-            S[i + c * w] = fma(S[i + k * w], S[k + c * w], S[i + c * w]);
-            c += dc;
-            io += di;
-            if (io >= rows) { io -= rows; ++c; }
-        }
-        __syncthreads();
+    for (int j = tid; j < p; j += NT) {
+        const double s = sqrt(dv[j]);
+        sq[j] = s;
+        rs[j] = 1.0 / s;
     }
+    __syncthreads();
+    // R(i, c) = u_i(c) / sqrt(d_i) for i < c, sqrt(d_i) on the diagonal;
     // R^{-1}(i, c) = Z(c, i) / sqrt(d_c) for i < c, 1/sqrt(d_c) on the diagonal
-    for (int c = ty; c < p; c += 16)
-        for (int i = tx; i < p; i += 16)
-            Rinv[i + (int64_t)c * ldr] = (i < c) ? S[c + i * w] * sq[c] : (i == c ? sq[c] : 0.0);
+    if (p > 0) {
+        const int tot = p * p, dc = NT / p, di = NT - dc * p;
+        int c = tid / p, i = tid - c * p;
+        for (int e = tid; e < tot; e += NT) {
+            R[i + (int64_t)c * ldr] = (i < c) ? S[i + c * ld] * rs[i] : (i == c ? sq[i] : 0.0);
+            if (Rinv) Rinv[i + (int64_t)c * ldr] = (i < c) ? S[c + i * ld] * rs[c] : (i == c ? rs[c] : 0.0);
+            c += dc;
+            i += di;
+            if (i >= p) { i -= p; ++c; }
+        }
+    }
+    if (tid == 0) {
+        info[0] = p;
+        info[1] = code_sh;
+    }
 }
 
 __global__ void tdiag_kernel(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
@@ -242,14 +280,11 @@ cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double e
                        double rho, double shift, double *R, double *Rinv, int64_t ldr, int *info,
                        cudaStream_t s) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
-    auto bytes = [](int n) {
-        return sizeof(double) * ((size_t)n * n + 4 * (size_t)n) + sizeof(long long) * 3 * (size_t)n +
-               sizeof(uint16_t) * (size_t)(n * (n - 1) / 2);
-    };
-    EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)bytes(128)));
+    EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)leaf_smem_bytes(128)));
     ProfScope prof(PROF_CHOL, (double)w * w * w * (Rinv ? 2.0 : 1.0) / 3.0, sizeof(double) * 3.0 * w * w, s);
     count_launch();
-    chol_small_kernel<<<1, 256, bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R, Rinv, ldr, info);
+    chol_small_kernel<<<1, kLeafThreads, leaf_smem_bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R,
+                                                                  Rinv, ldr, info);
     return cudaGetLastError();
 }
 

@@ -6,11 +6,11 @@
 // of the core (steps 9-11) and the reconstruction Q C with its fused
 // Frobenius error (Sec. 4.1).
 //
-// Tile TS x TS x 16 (TS = 64, or 32 for products too small to fill the 152
-// SMs with 64-tiles), 256 threads, (TS/16)^2 outputs per thread with the row
-// index fastest across lanes so that column-major stores coalesce.  When the
-// tile grid is smaller than two waves of the SMs the K range is split and the
-// partial tiles are summed by a second kernel in a fixed order.  FP64 runs at
+// Tile TS x TS x 16 (TS = 64, 32 or 16: the smaller tiles spread products too
+// small to fill the 152 SMs with 64-tiles), 256 threads, (TS/16)^2 outputs
+// per thread with the row index fastest across lanes so that column-major
+// stores coalesce.  The K range may be split as well, the partial tiles then
+// summed by a second kernel in a fixed order.  FP64 runs at
 // a few DFMA per clock per SM here, so small FP64 products are only fast when
 // they are spread over every SM.
 #include "common.cuh"
@@ -233,26 +233,40 @@ cudaError_t launch_gemv(bool ta, int64_t M, int64_t K, double alpha, const TA *A
     return cudaSuccess;
 }
 
-// tile grid and K split for tile size ts
+// Tile size and K split: FP64 issue (a few DFMA per clock per SM) bounds
+// every tile, so the plan minimises the DFMA count of the busiest SM,
+// ceil(CTAs / SMs) * TS^2 * kchunk, plus the second launch and the partial
+// traffic a split costs; smaller tiles carry a small penalty for their lower
+// reuse of shared operands, so that large products keep the 64-tiles.
 struct SimtPlan {
+    int ts;
     int64_t gm, gn, S;
 };
 
-inline SimtPlan simt_plan(int ts, int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
-    SimtPlan p;
-    p.gm = (M + ts - 1) / ts;
-    p.gn = (N + ts - 1) / ts;
-    int64_t tiles = p.gm * p.gn;
-    if (x.upper_only) tiles = (tiles + p.gm) / 2 + 1;
-    const int64_t target = 2 * kNumSMs;
-    p.S = 1;
-    if (tiles < target && K > 2 * BK) {
-        p.S = (target + tiles - 1) / tiles;
-        const int64_t kmax = (K + 2 * BK - 1) / (2 * BK);
-        if (p.S > kmax) p.S = kmax;
-        if (p.S > x.max_split) p.S = x.max_split;
+inline SimtPlan simt_plan(int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
+    SimtPlan best{64, 0, 0, 1};
+    double best_cost = -1.0;
+    for (int ts = 64; ts >= 16; ts /= 2) {
+        const int64_t gm = (M + ts - 1) / ts, gn = (N + ts - 1) / ts;
+        if (gn > 65535) continue;
+        int64_t tiles = gm * gn;
+        if (x.upper_only) tiles = (tiles + gm) / 2 + 1;
+        for (int64_t kc = BK;; kc *= 2) {
+            const int64_t kch = K > 0 ? std::min<int64_t>(kc, K) : 1;
+            const int64_t S = K > 0 ? (K + kch - 1) / kch : 1;
+            if (S <= x.max_split && S <= 65535) {
+                const int64_t waves = (tiles * S + kNumSMs - 1) / kNumSMs;
+                double cost = (double)waves * ts * ts * (double)kch * 0.5 * (1.0 + 0.05 * (64 / ts - 1));
+                if (S > 1) cost += 3000.0 + 2.0 * (double)M * (double)N * (double)S * 8.0 / 2400.0;
+                if (best_cost < 0.0 || cost < best_cost) {
+                    best_cost = cost;
+                    best = {ts, gm, gn, S};
+                }
+            }
+            if (kc >= K) break;
+        }
     }
-    return p;
+    return best;
 }
 
 template <typename TA, typename TB, typename TC, typename Acc, bool TRA, bool TRB, int TS>
@@ -303,7 +317,6 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
 {
     const int flags = (x.upper_only ? F_UPPER_ONLY : 0) | (x.a_upper ? F_A_UPPER : 0) |
                       (x.b_upper ? F_B_UPPER : 0);
-    if ((N + 31) / 32 > 65535) return cudaErrorInvalidValue;
     double frac = 1.0;
     if (x.upper_only) frac *= 0.5;
     if (x.a_upper && x.b_upper) frac /= 6.0;
@@ -313,6 +326,7 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
     if (beta != 0.0 || x.epilogue == EPI_ERR) bytes += (double)sizeof(TC) * M * N;
     ProfScope prof(PROF_GEMM_SIMT, flops, bytes, s);
     if (x.epilogue == EPI_ERR) {
+        if ((N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
         count_launch();
         dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), 1);
         gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_ERR, false, 64><<<grid, NT, 0, s>>>(
@@ -320,14 +334,16 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
             (const TC *)x.ref, x.ldref, x.err_partials);
         return cudaGetLastError();
     }
-    // 64-tiles unless they leave most SMs idle
-    const SimtPlan p64 = simt_plan(64, M, N, K, x);
-    if (p64.gm * p64.gn * p64.S >= kNumSMs)
-        return launch_store<TA, TB, TC, Acc, TRA, TRB, 64>(p64, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
-                                                            flags, x, ws, s);
-    const SimtPlan p32 = simt_plan(32, M, N, K, x);
-    return launch_store<TA, TB, TC, Acc, TRA, TRB, 32>(p32, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags,
-                                                        x, ws, s);
+    const SimtPlan pl = simt_plan(M, N, K, x);
+    if (pl.gm == 0) return cudaErrorInvalidValue;
+    if (pl.ts == 64)
+        return launch_store<TA, TB, TC, Acc, TRA, TRB, 64>(pl, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags,
+                                                            x, ws, s);
+    if (pl.ts == 32)
+        return launch_store<TA, TB, TC, Acc, TRA, TRB, 32>(pl, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags,
+                                                            x, ws, s);
+    return launch_store<TA, TB, TC, Acc, TRA, TRB, 16>(pl, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags, x,
+                                                        ws, s);
 }
 
 }  // namespace

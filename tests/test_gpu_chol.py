@@ -94,3 +94,20 @@ def test_not_positive_definite_stops(eod):
     G[12, 12] = -1.0
     p, code, _, _ = _run(eod, G, inverse=False)
     assert code == 3 and p <= 12
+
+
+def test_stopped_factorisation_keeps_its_inverse(eod):
+    """A rank-test stop at pivot p leaves the leading p x p factor and its
+    inverse: R^T R = G(:p, :p) and R^{-1} R = I (the inverse is built in the
+    same steps as the factor, so it must stop with it)."""
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((200, 64))
+    X[:, 40] *= 1e-8
+    G = X.T @ X
+    coef = 64.0 * (16 + np.sqrt(1000.0)) * U64
+    p, code, R, Ri = _run(eod, G, decide=1, eps2=1e-10, coef=coef, rho=1e-10)
+    assert (p, code) == (40, 1)
+    Gp = G[:40, :40]
+    assert np.linalg.norm(R.T @ R - Gp) <= 20 * 40 * U64 * np.linalg.norm(Gp)
+    assert np.allclose(np.tril(Ri, -1), 0.0)
+    assert np.linalg.norm(Ri @ R - np.eye(40)) <= 1e-12

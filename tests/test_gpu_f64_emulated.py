@@ -222,3 +222,34 @@ def test_matrix_vector_products(eod, ta, M, K):
     assert st == eod.EOD_OK, eod.status_string(st)
     scale = opA.abs() @ x.abs() + 0.5 * C0.abs()
     assert ((C - ref).abs() <= 1e-13 * scale + 1e-300).all()
+
+
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("M,N,K,flags", [(64, 192, 64, 0), (64, 64, 64, 32), (128, 128, 128, 64), (5, 3, 7, 0),
+                                         (17, 33, 100, 0), (2048, 64, 64, 64), (64, 64, 192, 0),
+                                         (245, 245, 256, 16), (192, 64, 2048, 0)])
+def test_simt_small_products(eod, ta, tb, M, N, K, flags):
+    """The SIMT kernel on the small products of the panel factorisation
+    (16- and 32-tiles, K splits with the fixed-order reduction), with the
+    triangular-operand and upper-only flags."""
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 7 * K + flags + 2 * ta + tb)
+    A = torch.randn((K, M) if ta else (M, K), generator=g, device="cuda", dtype=torch.float64)
+    B = torch.randn((N, K) if tb else (K, N), generator=g, device="cuda", dtype=torch.float64)
+    opA = A.t() if ta else A
+    opB = B.t() if tb else B
+    if flags & 32:
+        opA = torch.triu(opA)
+    if flags & 64:
+        opB = torch.triu(opB)
+    A = _cm((opA.t() if ta else opA).contiguous())
+    B = _cm((opB.t() if tb else opB).contiguous())
+    C0 = _cm(torch.randn((M, N), generator=g, device="cuda", dtype=torch.float64))
+    C = C0.clone()
+    _run(eod, flags, ta, tb, A, B, C, -1.0, 1.0, M, N, K)
+    ref = C0 - opA @ opB
+    tol = 1e-13 * (opA.abs() @ opB.abs() + C0.abs()) + 1e-300
+    if flags & 16:
+        keep = torch.triu(torch.ones((M, N), dtype=torch.bool, device="cuda"))
+        assert ((C - ref).abs()[keep] <= tol[keep]).all()
+    else:
+        assert ((C - ref).abs() <= tol).all()
