@@ -292,7 +292,9 @@ EOD_API eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w, i
  * upper triangle of C is wanted (the emulation stores row <= col only, the
  * SIMT kernel whole tiles that touch it), 32 = op(A) upper triangular,
  * 64 = op(B) upper triangular (the zero part is then not read by the
- * emulation; the SIMT kernel expects it to hold zeros).  Returns after
+ * emulation; the SIMT kernel expects it to hold zeros), 128 = a SIMT K split
+ * is summed by a separate reduction kernel instead of by the last CTA of
+ * each tile (same order, same result).  Returns after
  * synchronising `stream`; EOD_EINVAL for bad sizes or leading dimensions,
  * EOD_ETIMEOUT if a bounded device wait ran out. */
 EOD_API eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,

@@ -91,7 +91,7 @@ __device__ __forceinline__ void ldl_pivot(const double *S, int ld, int w, int j,
     }
 }
 
-constexpr int kLeafThreads = 256;
+constexpr int kLeafThreads = 512;
 
 size_t leaf_smem_bytes(int w) {
     return sizeof(double) * ((size_t)w * (w + 1) + 4 * (size_t)w) + sizeof(long long) * 3 * (size_t)w +
@@ -108,22 +108,25 @@ size_t leaf_smem_bytes(int w) {
 // part of the finished columns; row j of the upper part holds u = column j
 // before scaling (R's row j up to 1/sqrt(d_j)).  Step j, pivot j accepted:
 //   (A) column j+1 takes its update (threads 0-127), the u row and M are
-//       staged (threads 128-255, rows 0-63 on warps 6-7 so that the two
-//       FP64 instructions of a row run on different sub-partitions);
+//       staged (the last 128 threads, rows 0-63 on the last two warps, on
+//       other sub-partitions than the first two);
 //   (B) warp 0 decides pivot j+1 (integer compares, reciprocal by a
 //       third-order step) and computes -L(j+2, j+1); warp 4 stores M as
-//       Z's column j; warps 1-3 and 5-7 apply the updates, spread evenly
-//       through a table of (row, k) pairs ordered by row from the bottom
-//       (row r holds r-1 entries, so the rows > j form a prefix).
-// Warp 4 shares warp 0's sub-partition and issues no FP64 work, leaving that
-// FP64 pipe (64 cycles per warp instruction) to the pivot chain.
+//       Z's column j; the warps off sub-partition 0 apply the updates,
+//       spread evenly through a table of (row, k) pairs ordered by row from
+//       the bottom (row r holds r-1 entries, so the rows > j form a prefix).
+// The SM's FP64 unit is shared by its sub-partitions (a dependent DFMA
+// chain takes 68 cycles per op alone, 135 beside six streaming warps on the
+// other sub-partitions, 362 with one more on its own: probe), so sub-partition
+// 0 carries no FP64 work besides the pivot chain; 16 warps rather than 8
+// hide more of the update loop's latency (61 vs 70 us at w = 64).
 // The rank test reads the pivots d_j = T(j,j)^2 exactly as the Cholesky form
 // would; R differs from a square-root Cholesky only by rounding.
 __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *__restrict__ G, int64_t ldg, int w,
                                                                   int decide, double eps2, double delta_coef,
                                                                   double rho, double shift, double *__restrict__ R,
-                                                                  double *__restrict__ Rinv, int64_t ldr,
-                                                                  int *info) {
+                                                                  int64_t ldr, double *__restrict__ Rinv,
+                                                                  int64_t ldinv, int *info) {
     constexpr int NT = kLeafThreads;
     extern __shared__ double sh[];
     const int ld = w + 1;
@@ -196,8 +199,8 @@ __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *
         if (tid < 128) {
             const int i = j + 1 + tid;
             if (i < w) S[i + (j + 1) * ld] = fma(S[i + j * ld], mt, S[i + (j + 1) * ld]);
-        } else {
-            const int i = j + 1 + ((tid - 64) & 127);
+        } else if (tid >= NT - 128) {
+            const int i = j + 1 + ((tid - (NT - 128) + 64) & 127);
             if (i < w) {
                 const double ui = S[i + j * ld];
                 S[j + i * ld] = ui;
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *
         int c = tid / p, i = tid - c * p;
         for (int e = tid; e < tot; e += NT) {
             R[i + (int64_t)c * ldr] = (i < c) ? S[i + c * ld] * rs[i] : (i == c ? sq[i] : 0.0);
-            if (Rinv) Rinv[i + (int64_t)c * ldr] = (i < c) ? S[c + i * ld] * rs[c] : (i == c ? rs[c] : 0.0);
+            if (Rinv) Rinv[i + (int64_t)c * ldinv] = (i < c) ? S[c + i * ld] * rs[c] : (i == c ? rs[c] : 0.0);
             c += dc;
             i += di;
             if (i >= p) { i -= p; ++c; }
@@ -277,14 +280,14 @@ __global__ void trace_kernel(const double *G, int64_t ldg, int64_t p, double *ou
 }  // namespace
 
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2, double delta_coef,
-                       double rho, double shift, double *R, double *Rinv, int64_t ldr, int *info,
+                       double rho, double shift, double *R, int64_t ldr, double *Rinv, int64_t ldinv, int *info,
                        cudaStream_t s) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
     EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)leaf_smem_bytes(128)));
     ProfScope prof(PROF_CHOL, (double)w * w * w * (Rinv ? 2.0 : 1.0) / 3.0, sizeof(double) * 3.0 * w * w, s);
     count_launch();
     chol_small_kernel<<<1, kLeafThreads, leaf_smem_bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R,
-                                                                  Rinv, ldr, info);
+                                                                  ldr, Rinv, ldinv, info);
     return cudaGetLastError();
 }
 
@@ -312,7 +315,7 @@ extern "C" eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w
     using namespace eod;
     if (!G || !R || !info || w < 1 || w > 128 || ldg < w || ldr < w) return EOD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = chol_small(G, ldg, w, decide ? 1 : 0, eps2, delta_coef, rho, shift, R, Rinv, ldr, info, s);
+    cudaError_t e = chol_small(G, ldg, w, decide ? 1 : 0, eps2, delta_coef, rho, shift, R, ldr, Rinv, ldr, info, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -82,10 +82,17 @@ template <typename T> __device__ __forceinline__ double to_f64(T x) { return (do
 // --------------------------------------------------------------------------
 // Bump allocator over one device buffer (the per-call workspace).
 // --------------------------------------------------------------------------
+// counters a workspace holds for in-kernel K-split folding (one per tile)
+constexpr int64_t kTileCounters = 65536;
+
 struct Scratch {
     char *base = nullptr;
     size_t size = 0, used = 0, high = 0;
     int *err_flag = nullptr;   // device flag set by a kernel whose bounded wait ran out
+    // zeroed counters, one per output tile, for K splits folded in-kernel
+    // (each product leaves them zero again); null: a separate reduction
+    unsigned *tile_count = nullptr;
+    int64_t tile_count_n = 0;
     void *take(size_t bytes) {
         size_t off = (used + 255) & ~size_t(255);
         if (off + bytes > size) return nullptr;
@@ -245,8 +252,8 @@ enum CholCode { CHOL_ALL = 0, CHOL_BELOW = 1, CHOL_UNCERTAIN = 2, CHOL_FAIL = 3 
 // R (p x p upper, ld ldr) and its inverse Rinv (ld ldr); the original
 // diagonal of G is used for the rounding margin.
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2,
-                       double delta_coef, double rho, double shift, double *R,
-                       double *Rinv, int64_t ldr, int *info, cudaStream_t s);
+                       double delta_coef, double rho, double shift, double *R, int64_t ldr,
+                       double *Rinv, int64_t ldinv, int *info, cudaStream_t s);
 // tdiag[j] = |R1(j,j) * R2(j,j)|, j < p
 cudaError_t tdiag_product(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
                           double *tdiag, cudaStream_t s);

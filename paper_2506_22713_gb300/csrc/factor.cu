@@ -91,7 +91,7 @@ template <> struct Traits<float> { static constexpr int dtype = EOD_F32; static 
 // ---------------------------------------------------------------------------
 template <typename T>
 struct CoreWork {
-    double *G = nullptr, *R = nullptr, *Rp = nullptr, *Inv = nullptr, *RiD = nullptr, *RiT = nullptr,
+    double *G = nullptr, *R = nullptr, *Rp = nullptr, *RiD = nullptr, *RiT = nullptr,
            *trace = nullptr;
     T *InvT = nullptr, *Tmp = nullptr;
     int *info = nullptr;
@@ -103,39 +103,34 @@ static constexpr int kPB = 256;   // panel width of the core Cholesky and triang
 
 template <typename T>
 static eod_status chol_panel_leaves(CoreWork<T> &w, int64_t p, int64_t j0, int64_t pe, double shift, Scratch *ws,
-                                    cudaStream_t s, double *Rout) {
+                                    cudaStream_t s, double *Rout, double *RiJ) {
     GemmExtra ex;
     for (int64_t l0 = j0; l0 < pe; l0 += kNB) {
         const int64_t lb = std::min<int64_t>(kNB, pe - l0), L = l0 / kNB;
+        double *RiL = RiJ + (l0 - j0) * (1 + kPB);   // the leaf's inverse, on the diagonal of R_JJ^{-1}
         if (l0 > j0)   // G(l, l:pe) -= R(j0:l0, l)^T R(j0:l0, l:pe)
             EOD_CU((gemm<double, double, double, double>(true, false, lb, pe - l0, l0 - j0, -1.0, Rout + j0 + l0 * p,
                                                           p, Rout + j0 + l0 * p, p, 1.0, w.G + l0 + l0 * p, p, ex,
                                                           ws, s)));
-        EOD_CU(chol_small(w.G + l0 + l0 * p, p, (int)lb, 0, 0.0, 0.0, 0.0, shift, w.Rp, w.Inv + L * kNB * kNB, kNB,
+        EOD_CU(chol_small(w.G + l0 + l0 * p, p, (int)lb, 0, 0.0, 0.0, 0.0, shift, Rout + l0 + l0 * p, p, RiL, kPB,
                           w.info + 2 * L, s));
-        EOD_CU(copy_matrix<double, double>(w.Rp, kNB, Rout + l0 + l0 * p, p, lb, lb, false, s));
         if (l0 + lb < pe)   // R(l, l+1:pe) = R_ll^{-T} G(l, l+1:pe)
-            EOD_CU((gemm<double, double, double, double>(true, false, lb, pe - l0 - lb, lb, 1.0,
-                                                          w.Inv + L * kNB * kNB, kNB, w.G + l0 + (l0 + lb) * p, p,
-                                                          0.0, Rout + l0 + (l0 + lb) * p, p, ex, ws, s)));
+            EOD_CU((gemm<double, double, double, double>(true, false, lb, pe - l0 - lb, lb, 1.0, RiL, kPB,
+                                                          w.G + l0 + (l0 + lb) * p, p, 0.0, Rout + l0 + (l0 + lb) * p,
+                                                          p, ex, ws, s)));
     }
     return EOD_OK;
 }
 
 // RiJ (jb x jb, ld kPB) = R_JJ^{-1} for the diagonal panel at j0, from its
-// leaves' inverses by doubling: inv([A B; 0 C]) = [A^-1, -A^-1 B C^-1; 0, C^-1].
+// leaves' inverses (already on its diagonal) by doubling:
+// inv([A B; 0 C]) = [A^-1, -A^-1 B C^-1; 0, C^-1].
 template <typename T>
 static eod_status panel_inverse(CoreWork<T> &w, int64_t p, int64_t j0, int64_t jb, const double *Rout, double *RiJ,
                                 Scratch *ws, cudaStream_t s) {
     GemmExtra au, bu;
     au.a_upper = true;
     bu.b_upper = true;
-    EOD_CU(fill_zero<double>(RiJ, jb, jb, kPB, s));
-    for (int64_t l0 = 0; l0 < jb; l0 += kNB) {
-        const int64_t lb = std::min<int64_t>(kNB, jb - l0);
-        EOD_CU(copy_matrix<double, double>(w.Inv + ((j0 + l0) / kNB) * kNB * kNB, kNB, RiJ + l0 + l0 * kPB, kPB, lb,
-                                           lb, false, s));
-    }
     for (int64_t h = kNB; h < jb; h *= 2) {
         for (int64_t a0 = 0; a0 + h < jb; a0 += 2 * h) {
             const int64_t b0 = a0 + h, bl = std::min<int64_t>(h, jb - b0);
@@ -160,7 +155,8 @@ static eod_status chol_panels(CoreWork<T> &w, int64_t p, double shift, HostMirro
     for (int64_t j0 = 0; j0 < p; j0 += kPB) {
         const int64_t pe = std::min<int64_t>(p, j0 + kPB), jb = pe - j0;
         double *RiJ = w.RiD + (j0 / kPB) * kPB * kPB;   // ld kPB
-        EOD_TRY(chol_panel_leaves(w, p, j0, pe, shift, ws, s, Rout));
+        EOD_CU(fill_zero<double>(RiJ, jb, jb, kPB, s));
+        EOD_TRY(chol_panel_leaves(w, p, j0, pe, shift, ws, s, Rout, RiJ));
         EOD_TRY(panel_inverse(w, p, j0, jb, Rout, RiJ, ws, s));
         if (pe < p) {
             // R(J, pe:p) = R_JJ^{-T} G(J, pe:p);  G(pe:p, pe:p) -= R(J, pe:p)^T R(J, pe:p)
@@ -256,7 +252,7 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
     double shift = 0.0;
     for (int pass = 0; pass < passes; ++pass) {
         EOD_TRY(gram_full(W, rows, p, ldw, w.G, sym, ws, s));
-        double *Rpass = (pass == 0) ? Rout : w.Rp + kNB * kNB;  // pass factor storage
+        double *Rpass = (pass == 0) ? Rout : w.Rp;  // pass factor storage
         eod_status st = chol_panels(w, p, shift, hm, ws, s, Rpass);
         if (st == EOD_EPRECISION && pass == 0 && shift == 0.0) {
             // shifted CholQR: shift = 11 (rows p + p (p+1)) u ||W||_2^2, ||W||_2^2 <= trace(G)
@@ -326,6 +322,9 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     ws.size = ws_bytes;
     EOD_TRY(ar.get(&ws.err_flag, 1));
     EOD_CU(cudaMemsetAsync(ws.err_flag, 0, sizeof(int), s));
+    ws.tile_count_n = kTileCounters;
+    EOD_TRY(ar.get(&ws.tile_count, (size_t)kTileCounters));
+    EOD_CU(cudaMemsetAsync(ws.tile_count, 0, sizeof(unsigned) * kTileCounters, s));
 
     T *Qb, *Om, *Y, *S, *T1, *RinvT;
     double *G, *R1, *R1i, *R2, *R2i, *tdiag_d, *dsc;
@@ -465,7 +464,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
             }
             // step 5 (pass 1) + steps 6-11: Gram, Cholesky with the rank test
             EOD_CU(gram_skinny<T>(Yc, m, (int)wdt, m, G, k, &ws, s));
-            EOD_CU(chol_small(G, k, (int)wdt, 1, eps2, delta_coef, Traits<T>::rho, 0.0, R1, R1i, k, info, s));
+            EOD_CU(chol_small(G, k, (int)wdt, 1, eps2, delta_coef, Traits<T>::rho, 0.0, R1, k, R1i, k, info, s));
             EOD_CU(cudaMemcpyAsync(hm.info, info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
             EOD_CU(cudaStreamSynchronize(s));
             const int p = hm.info[0], code = hm.info[1];
@@ -478,7 +477,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 }
                 EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, Yc, m, Ri, k, 0.0, T1, m, bup, &ws, s)));
                 EOD_CU(gram_skinny<T>(T1, m, p, m, G, k, &ws, s));
-                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, R2i, k, info, s));
+                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, k, R2i, k, info, s));
                 const T *Ri2 = (const T *)R2i;
                 if (!std::is_same<T, double>::value) {
                     EOD_CU((copy_matrix<double, T>(R2i, k, RinvT, k, p, p, false, s)));
@@ -572,8 +571,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     const int64_t nblk = (r + kNB - 1) / kNB;
     EOD_TRY(ar.get(&cw.G, (size_t)r * r));
     EOD_TRY(ar.get(&cw.R, (size_t)r * r));
-    EOD_TRY(ar.get(&cw.Rp, (size_t)kNB * kNB + (size_t)r * r));
-    EOD_TRY(ar.get(&cw.Inv, (size_t)nblk * kNB * kNB));
+    EOD_TRY(ar.get(&cw.Rp, (size_t)r * r));
     EOD_TRY(ar.get(&cw.RiD, (size_t)((r + kPB - 1) / kPB) * kPB * kPB));
     EOD_TRY(ar.get(&cw.RiT, (size_t)kPB * kPB));
     EOD_TRY(ar.get(&cw.trace, 1));

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(NT)
 gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restrict__ A, int64_t lda,
                  const TB *__restrict__ B, int64_t ldb, Acc beta, TC *C, int64_t ldc, int64_t kchunk,
                  Acc *__restrict__ part, int flags, const TC *__restrict__ ref, int64_t ldref,
-                 double *__restrict__ errp)
+                 double *__restrict__ errp, unsigned *__restrict__ tile_count)
 {
     constexpr int BM = TS, BN = TS, TPT = TS / 16;   // outputs per thread along each axis
     __shared__ Acc As[BK][BM + 1];
@@ -106,6 +106,37 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
             for (int i = 0; i < TPT; ++i) {
                 const int64_t row = m0 + tx + 16 * i;
                 if (row < M) dst[row + col * M] = acc[i][j];
+            }
+        }
+        if (!tile_count) return;
+        // The last of the tile's S CTAs to finish sums the partials in split
+        // order (the same order as the separate reduction) and stores C; it
+        // also resets the tile's counter for the next product on the stream.
+        __shared__ int last_sh;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const int64_t t = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+            const unsigned prev = atomicAdd(&tile_count[t], 1u);
+            last_sh = (prev + 1 == gridDim.z);
+            if (last_sh) tile_count[t] = 0u;
+        }
+        __syncthreads();
+        if (!last_sh) return;
+        __threadfence();
+#pragma unroll
+        for (int j = 0; j < TPT; ++j) {
+            const int64_t col = n0 + ty + 16 * j;
+            if (col >= N) continue;
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) {
+                const int64_t row = m0 + tx + 16 * i;
+                if (row >= M) continue;
+                Acc sum = Acc(0);
+                for (unsigned z = 0; z < gridDim.z; ++z) sum += __ldcg(part + (int64_t)z * M * N + row + col * M);
+                Acc v = alpha * sum;
+                if (beta != Acc(0)) v = fma(beta, (Acc)C[row + col * ldc], v);
+                C[row + col * ldc] = (TC)v;
             }
         }
         return;
@@ -289,24 +320,29 @@ cudaError_t launch_store(const SimtPlan &pl, int64_t M, int64_t N, int64_t K, do
     }
     dim3 grid((unsigned)pl.gm, (unsigned)pl.gn, (unsigned)S);
     if (S > 1) {
-        count_launch(2);
+        // the split's partial sums are folded by the tile's last CTA when the
+        // workspace has a counter per tile, else by a second kernel
+        unsigned *cnt = (ws && ws->tile_count && pl.gm * pl.gn <= ws->tile_count_n) ? ws->tile_count : nullptr;
+        count_launch(cnt ? 1 : 2);
         gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, true, TS><<<grid, NT, 0, s>>>(
             M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, part, flags, nullptr, 0,
-            nullptr);
+            nullptr, cnt);
         EOD_CUDA_TRY(cudaGetLastError());
-        int64_t total = M * N;
-        int blocks = (int)((total + 255) / 256);
-        if (blocks > 4 * kNumSMs * 8) blocks = 4 * kNumSMs * 8;
-        splitk_reduce_kernel<TC, Acc><<<blocks, 256, 0, s>>>(M, N, (int)S, part, (Acc)alpha, (Acc)beta,
-                                                             C, ldc, x.upper_only ? 1 : 0, TS);
-        EOD_CUDA_TRY(cudaGetLastError());
+        if (!cnt) {
+            int64_t total = M * N;
+            int blocks = (int)((total + 255) / 256);
+            if (blocks > 4 * kNumSMs * 8) blocks = 4 * kNumSMs * 8;
+            splitk_reduce_kernel<TC, Acc><<<blocks, 256, 0, s>>>(M, N, (int)S, part, (Acc)alpha, (Acc)beta,
+                                                                 C, ldc, x.upper_only ? 1 : 0, TS);
+            EOD_CUDA_TRY(cudaGetLastError());
+        }
         ws->release(mark);
         return cudaSuccess;
     }
     count_launch();
     gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, false, TS><<<grid, NT, 0, s>>>(
         M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, nullptr, flags, nullptr, 0,
-        nullptr);
+        nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -331,7 +367,7 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
         dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), 1);
         gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_ERR, false, 64><<<grid, NT, 0, s>>>(
             M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, K > 0 ? K : 1, nullptr, flags,
-            (const TC *)x.ref, x.ldref, x.err_partials);
+            (const TC *)x.ref, x.ldref, x.err_partials, nullptr);
         return cudaGetLastError();
     }
     const SimtPlan pl = simt_plan(M, N, K, x);
@@ -413,7 +449,7 @@ extern "C" eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t t
     x.upper_only = (mode & 16) != 0;
     x.a_upper = (mode & 32) != 0;
     x.b_upper = (mode & 64) != 0;
-    if ((mode & 3) > 1 || (mode & ~(3 | 16 | 32 | 64)) != 0) return EOD_EINVAL;
+    if ((mode & 3) > 1 || (mode & ~(3 | 16 | 32 | 64 | 128)) != 0) return EOD_EINVAL;
     cudaError_t e;
     if ((mode & 3) == 1) {
         int *flag = nullptr;
@@ -434,9 +470,19 @@ extern "C" eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t t
     Scratch ws;
     if (cudaMallocAsync((void **)&ws.base, (size_t)48 << 20, s) != cudaSuccess) { cudaGetLastError(); return EOD_ENOMEM; }
     ws.size = (size_t)48 << 20;
+    if (!(mode & 128)) {   // K splits folded in-kernel (else by the separate reduction)
+        if (cudaMallocAsync((void **)&ws.tile_count, sizeof(unsigned) * kTileCounters, s) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeAsync(ws.base, s);
+            return EOD_ENOMEM;
+        }
+        cudaMemsetAsync(ws.tile_count, 0, sizeof(unsigned) * kTileCounters, s);
+        ws.tile_count_n = kTileCounters;
+    }
     e = gemm<double, double, double, double>(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, x, &ws, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFreeAsync(ws.base, s);
+    if (ws.tile_count) cudaFreeAsync(ws.tile_count, s);
     if (e != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
     return EOD_OK;
 }

@@ -227,11 +227,13 @@ def test_matrix_vector_products(eod, ta, M, K):
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
 @pytest.mark.parametrize("M,N,K,flags", [(64, 192, 64, 0), (64, 64, 64, 32), (128, 128, 128, 64), (5, 3, 7, 0),
                                          (17, 33, 100, 0), (2048, 64, 64, 64), (64, 64, 192, 0),
-                                         (245, 245, 256, 16), (192, 64, 2048, 0)])
+                                         (245, 245, 256, 16), (192, 64, 2048, 0), (64, 192, 64, 128),
+                                         (245, 245, 256, 16 | 128), (192, 64, 2048, 128)])
 def test_simt_small_products(eod, ta, tb, M, N, K, flags):
     """The SIMT kernel on the small products of the panel factorisation
-    (16- and 32-tiles, K splits with the fixed-order reduction), with the
-    triangular-operand and upper-only flags."""
+    (16- and 32-tiles, K splits summed in split order by each tile's last CTA,
+    or by the separate reduction: flag 128), with the triangular-operand and
+    upper-only flags."""
     g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 7 * K + flags + 2 * ta + tb)
     A = torch.randn((K, M) if ta else (M, K), generator=g, device="cuda", dtype=torch.float64)
     B = torch.randn((N, K) if tb else (K, N), generator=g, device="cuda", dtype=torch.float64)
@@ -246,6 +248,12 @@ def test_simt_small_products(eod, ta, tb, M, N, K, flags):
     C0 = _cm(torch.randn((M, N), generator=g, device="cuda", dtype=torch.float64))
     C = C0.clone()
     _run(eod, flags, ta, tb, A, B, C, -1.0, 1.0, M, N, K)
+    if flags & 128:   # the two ways of summing a K split give the same bits
+        C2 = C0.clone()
+        _run(eod, flags & ~128, ta, tb, A, B, C2, -1.0, 1.0, M, N, K)
+        keep = torch.triu(torch.ones((M, N), dtype=torch.bool, device="cuda")) if flags & 16 else torch.ones(
+            (M, N), dtype=torch.bool, device="cuda")
+        assert torch.equal(C[keep], C2[keep])
     ref = C0 - opA @ opB
     tol = 1e-13 * (opA.abs() @ opB.abs() + C0.abs()) + 1e-300
     if flags & 16:
