@@ -51,7 +51,7 @@ def _measured_peaks():
         return 1.9e6, 6800.0, "fallback"
 L2_BYTES = 129 * 1024 * 1024
 # kernel kinds of the library's profile counters, in PROF_* order
-KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm"]
+KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm", "oz_slice"]
 # BF16 slice-pair products per emulated FP64 multiply-add (8 slices, s + t <= 7)
 OZ_PAIRS = 36
 

@@ -209,7 +209,8 @@ EOD_API void eod_abe_debug_fail_alloc_after(int32_t n);
  * kernel launch, grouped by kind: 0 SIMT GEMM, 1 one-CTA Cholesky / rank
  * test, 2 Omega generation, 3 streaming (norms, copies, splitting),
  * 4 tcgen05 tensor-core GEMM (mixed path), 5 FP64 GEMM emulated on tcgen05
- * (plain FP64 path); eod_abe_debug_profile(0) stops it and clears.
+ * (plain FP64 path), 6 slicing of FP64 operands into the BF16 digits of that
+ * emulation; eod_abe_debug_profile(0) stops it and clears.
  * eod_abe_debug_profile_read() waits for the recorded events of one kind and
  * returns the launch count, the summed device time (ms) and the summed
  * algorithmic flops and bytes of those launches; EOD_EINVAL for an unknown
@@ -294,7 +295,8 @@ EOD_API eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w, i
  * 64 = op(B) upper triangular (the zero part is then not read by the
  * emulation; the SIMT kernel expects it to hold zeros), 128 = a SIMT K split
  * is summed by a separate reduction kernel instead of by the last CTA of
- * each tile (same order, same result).  Returns after
+ * each tile (same order, same result; the emulation always uses its own
+ * reduction kernel).  Returns after
  * synchronising `stream`; EOD_EINVAL for bad sizes or leading dimensions,
  * EOD_ETIMEOUT if a bounded device wait ran out. */
 EOD_API eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,

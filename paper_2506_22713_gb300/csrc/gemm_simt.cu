@@ -124,6 +124,25 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
         __syncthreads();
         if (!last_sh) return;
         __threadfence();
+        // splits outer, the thread's outputs inner (their loads in flight
+        // together); each sum still runs in split order
+        Acc sum[TPT][TPT];
+#pragma unroll
+        for (int j = 0; j < TPT; ++j)
+#pragma unroll
+            for (int i = 0; i < TPT; ++i) sum[i][j] = Acc(0);
+        for (unsigned z = 0; z < gridDim.z; ++z) {
+            const Acc *src = part + (int64_t)z * M * N;
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                const int64_t col = n0 + ty + 16 * j;
+#pragma unroll
+                for (int i = 0; i < TPT; ++i) {
+                    const int64_t row = m0 + tx + 16 * i;
+                    if (row < M && col < N) sum[i][j] += __ldcg(src + row + col * M);
+                }
+            }
+        }
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
             const int64_t col = n0 + ty + 16 * j;
@@ -132,9 +151,7 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
             for (int i = 0; i < TPT; ++i) {
                 const int64_t row = m0 + tx + 16 * i;
                 if (row >= M) continue;
-                Acc sum = Acc(0);
-                for (unsigned z = 0; z < gridDim.z; ++z) sum += __ldcg(part + (int64_t)z * M * N + row + col * M);
-                Acc v = alpha * sum;
+                Acc v = alpha * sum[i][j];
                 if (beta != Acc(0)) v = fma(beta, (Acc)C[row + col * ldc], v);
                 C[row + col * ldc] = (TC)v;
             }
@@ -321,8 +338,11 @@ cudaError_t launch_store(const SimtPlan &pl, int64_t M, int64_t N, int64_t K, do
     dim3 grid((unsigned)pl.gm, (unsigned)pl.gn, (unsigned)S);
     if (S > 1) {
         // the split's partial sums are folded by the tile's last CTA when the
-        // workspace has a counter per tile, else by a second kernel
-        unsigned *cnt = (ws && ws->tile_count && pl.gm * pl.gn <= ws->tile_count_n) ? ws->tile_count : nullptr;
+        // workspace has a counter per tile and that CTA's share is small
+        // (at most 64 K partial values), else by a second kernel
+        unsigned *cnt = (ws && ws->tile_count && pl.gm * pl.gn <= ws->tile_count_n && (int64_t)TS * TS * S <= 65536)
+                            ? ws->tile_count
+                            : nullptr;
         count_launch(cnt ? 1 : 2);
         gemm_simt_kernel<TA, TB, TC, Acc, TRA, TRB, EPI_STORE, true, TS><<<grid, NT, 0, s>>>(
             M, N, K, (Acc)alpha, A, lda, B, ldb, (Acc)beta, C, ldc, kchunk, part, flags, nullptr, 0,

@@ -13,7 +13,8 @@ enum ProfKind {
     PROF_STREAM = 3,      // norms, copies, scaling, splitting
     PROF_TC_GEMM = 4,     // tcgen05 tensor-core contractions (mixed path)
     PROF_OZ_GEMM = 5,     // FP64 contractions emulated on tcgen05 (plain FP64 path)
-    PROF_KINDS = 6
+    PROF_OZ_SLICE = 6,    // FP64 operands cut into BF16 digit slices for those contractions
+    PROF_KINDS = 7
 };
 
 void count_launch(int n = 1);

@@ -399,6 +399,33 @@ __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K
     }
 }
 
+// The eight BF16 digits of x 2^-er into o[s * slice_stride] (see below).
+__device__ __forceinline__ void write_slices(double x, int er, __nv_bfloat16 *o, int64_t slice_stride) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (bits >> 63) != 0;
+    int E = (int)((bits >> 52) & 0x7ff);
+    unsigned long long M = bits & 0xfffffffffffffull;
+    if (E == 0x7ff) M = 0;               // non-finite: not representable, taken as zero
+    else if (E == 0) E = 1;              // subnormal: M 2^(1 - 1075)
+    else M |= 1ull << 52;                // |x| = M 2^(E - 1075)
+    long long v = 0;
+    const int sh = E - 1020 - er;        // v = M 2^sh; sh <= 2 since |x| < 2^er
+    if (er >= -1100 && M != 0) {
+        if (sh >= 0) v = (long long)(M << sh);
+        else if (sh > -63) v = (long long)((M >> (-sh)) + ((M >> (-sh - 1)) & 1ull));
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int w = 49 - 7 * s;
+        long long q;
+        if (w > 0) q = (v + (1ll << (w - 1))) >> w;   // balanced digit: |q| <= 64
+        else q = v;
+        v -= q << w;
+        const float qf = (float)(neg ? -q : q);
+        o[s * slice_stride] = __float2bfloat16_rn(qf);
+    }
+}
+
 // out[s][r * ldk + k] = slice s of X(r, k) 2^-e[r]; 32 x 32 tiles through
 // shared memory so reads follow X's contiguous axis and writes follow k.
 // Integer arithmetic on the bit pattern: v = round(|x| 2^(55 - e)) < 2^55 + 1
@@ -435,31 +462,41 @@ __global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K,
     for (int i = ty; i < 32; i += 8) {
         const int64_t r = r0 + i, k = k0 + tx;
         if (r >= R || k >= K) continue;
-        const int er = erow[i];
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(tile[i][tx]);
-        const bool neg = (bits >> 63) != 0;
-        int E = (int)((bits >> 52) & 0x7ff);
-        unsigned long long M = bits & 0xfffffffffffffull;
-        if (E == 0x7ff) M = 0;               // non-finite: not representable, taken as zero
-        else if (E == 0) E = 1;              // subnormal: M 2^(1 - 1075)
-        else M |= 1ull << 52;                // |x| = M 2^(E - 1075)
-        long long v = 0;
-        const int sh = E - 1020 - er;        // v = M 2^sh; sh <= 2 since |x| < 2^er
-        if (er >= -1100 && M != 0) {
-            if (sh >= 0) v = (long long)(M << sh);
-            else if (sh > -63) v = (long long)((M >> (-sh)) + ((M >> (-sh - 1)) & 1ull));
-        }
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int w = 49 - 7 * s;
-            long long q;
-            if (w > 0) q = (v + (1ll << (w - 1))) >> w;   // balanced digit: |q| <= 64
-            else q = v;
-            v -= q << w;
-            const float qf = (float)(neg ? -q : q);
-            out[s * slice_stride + r * ldk + k] = __float2bfloat16_rn(qf);
-        }
+        write_slices(tile[i][tx], erow[i], out + r * ldk + k, slice_stride);
     }
+}
+
+// Rows with K contiguous (sk == 1) and their own exponents, one CTA per row:
+// the row maximum (as in rowexp_kernel) and then the slices (as in
+// slice_kernel), in one launch; the second read of the row hits L1 / L2.
+__global__ void __launch_bounds__(256) slice_rows_kernel(const double *__restrict__ X, int64_t K, int64_t sr,
+                                                         int tri, int *__restrict__ e_out,
+                                                         __nv_bfloat16 *__restrict__ out, int64_t ldk,
+                                                         int64_t slice_stride) {
+    __shared__ unsigned long long red[8];
+    __shared__ int er_sh;
+    const int64_t r = blockIdx.x;
+    const double *x = X + r * sr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long m = 0ull;
+    for (int64_t k = tid; k < K; k += 256)
+        if (!tri_zero(tri, r, k)) m = max(m, abs_bits(x[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long t = red[0];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) t = max(t, red[i]);
+        const int er = t > 0ull ? exp_of_bits(t) : kExpZero;
+        er_sh = er;
+        e_out[r] = er;
+    }
+    __syncthreads();
+    const int er = er_sh;
+    __nv_bfloat16 *o = out + r * ldk;
+    for (int64_t k = tid; k < K; k += 256) write_slices(tri_zero(tri, r, k) ? 0.0 : x[k], er, o + k, slice_stride);
 }
 
 __global__ void split_sum_kernel(const double *__restrict__ part, int S, int64_t M, int64_t N, double alpha,
@@ -485,6 +522,12 @@ struct Slices {
 cudaError_t slice_into(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, __nv_bfloat16 *q, int *e,
                        int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s, int tri = 0) {
     if (R <= 0 || K <= 0) return cudaSuccess;
+    ProfScope prof(PROF_OZ_SLICE, 0.0, 8.0 * (double)R * K + 2.0 * NS * (double)R * K, s);
+    if (e && sk == 1 && (R >= kNumSMs || K <= 8192)) {
+        count_launch();
+        slice_rows_kernel<<<(unsigned)R, 256, 0, s>>>(X, K, sr, tri, e, q, ldk, slice_stride);
+        return cudaGetLastError();
+    }
     int *ep = nullptr;
     int64_t ksplit = 1;
     if (e) {
