@@ -220,6 +220,21 @@ __global__ void gemv_n_kernel(int64_t M, int64_t K, Acc alpha, const TA *__restr
     }
 }
 
+// y partials over K ranges (A M x K): a thread per row and range,
+// coalesced along the rows; gemv_t_reduce_kernel sums the ranges in order.
+template <typename TA, typename TB, typename Acc>
+__global__ void __launch_bounds__(256) gemv_n_partial_kernel(int64_t M, int64_t K, int64_t chunk,
+                                                             const TA *__restrict__ A, int64_t lda,
+                                                             const TB *__restrict__ x, Acc *__restrict__ part) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t k0 = (int64_t)blockIdx.y * chunk;
+    const int64_t k1 = k0 + chunk < K ? k0 + chunk : K;
+    Acc acc = Acc(0);
+    for (int64_t k = k0; k < k1; ++k) acc = fma((Acc)A[i + k * lda], (Acc)x[k], acc);
+    part[(int64_t)blockIdx.y * M + i] = acc;
+}
+
 template <typename TA, typename TB, typename Acc>
 __global__ void __launch_bounds__(256) gemv_t_partial_kernel(int64_t M, int64_t K, int64_t chunk,
                                                              const TA *__restrict__ A, int64_t lda,
@@ -255,10 +270,34 @@ cudaError_t launch_gemv(bool ta, int64_t M, int64_t K, double alpha, const TA *A
                         double beta, TC *y, Scratch *ws, cudaStream_t s) {
     ProfScope prof(PROF_GEMM_SIMT, 2.0 * (double)M * K, (double)sizeof(TA) * M * K, s);
     if (!ta) {
-        count_launch();
-        const int64_t blocks = std::min<int64_t>((M + 255) / 256, 8LL * kNumSMs);
-        gemv_n_kernel<TA, TB, TC, Acc><<<(unsigned)blocks, 256, 0, s>>>(M, K, (Acc)alpha, A, lda, x, (Acc)beta, y);
-        return cudaGetLastError();
+        // K split so that about four CTAs per SM work (a row's FMAs form one
+        // dependent chain per range), ranges of at least 16
+        const int64_t rblocks = (M + 255) / 256;
+        int64_t S = (4 * kNumSMs + rblocks - 1) / rblocks;
+        const int64_t smax = (K + 15) / 16;
+        if (S > smax) S = smax;
+        if (S > 65535) S = 65535;
+        Acc *part = nullptr;
+        size_t mark = ws ? ws->mark() : 0;
+        if (S > 1) part = ws ? (Acc *)ws->take(sizeof(Acc) * (size_t)S * (size_t)M) : nullptr;
+        if (S <= 1 || !part || rblocks > 2147483647LL) {
+            count_launch();
+            const int64_t blocks = std::min<int64_t>(rblocks, 8LL * kNumSMs);
+            gemv_n_kernel<TA, TB, TC, Acc><<<(unsigned)blocks, 256, 0, s>>>(M, K, (Acc)alpha, A, lda, x, (Acc)beta,
+                                                                             y);
+            return cudaGetLastError();
+        }
+        const int64_t chunk = (K + S - 1) / S;
+        S = (K + chunk - 1) / chunk;
+        count_launch(2);
+        gemv_n_partial_kernel<TA, TB, Acc><<<dim3((unsigned)rblocks, (unsigned)S), 256, 0, s>>>(M, K, chunk, A, lda,
+                                                                                                  x, part);
+        EOD_CUDA_TRY(cudaGetLastError());
+        const int64_t blocks = std::min<int64_t>(rblocks, 8LL * kNumSMs);
+        gemv_t_reduce_kernel<TC, Acc><<<(unsigned)blocks, 256, 0, s>>>(M, (int)S, part, (Acc)alpha, (Acc)beta, y);
+        EOD_CUDA_TRY(cudaGetLastError());
+        ws->release(mark);
+        return cudaSuccess;
     }
     // K split so that about four CTAs per SM work, chunks of at least 2048
     int64_t S = (4 * kNumSMs + M - 1) / M;
