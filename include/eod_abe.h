@@ -61,11 +61,18 @@ typedef enum {
     EOD_PLAIN = 0,         /* every contraction in the storage type of A
                               (FP64 DFMA for EOD_F64, FP32 FFMA for EOD_F32);
                               Gram/Cholesky/rank test/core in FP64 */
-    EOD_MIXED_BF16 = 1     /* sketch, projection and reconstruction on tcgen05
+    EOD_MIXED_BF16 = 1,    /* sketch, projection and reconstruction on tcgen05
                               tensor cores with FP32 accumulation: A split into
                               three BF16 terms for the sketch (exact for FP32
                               data), two for the projection and the error;
                               Gram/Cholesky/rank test/core in FP64 */
+    EOD_MIXED_TF32 = 2     /* the same contractions with tcgen05 kind::tf32:
+                              A, Q and C split into two TF32 terms (hi = the
+                              value with 13 low significand bits cleared,
+                              lo = the exact rest; dropped terms ~2^-21
+                              relative, against ~2^-16 for the BF16 form), at
+                              half the BF16 MMA rate and twice its operand
+                              bytes; FP32 data as for EOD_MIXED_BF16 */
 } eod_precision;
 
 typedef enum {
@@ -85,7 +92,7 @@ typedef struct {
                               on the rank BasisExt found; 0 = power-free.  The
                               QRs are CholQR2 with positive diagonals, so Q_tau
                               and the factors are unique given Omega; in the
-                              mixed form A^T Q uses the BF16 split and A Q~ FP32 */
+                              mixed forms A^T Q uses their split and A Q~ FP32 */
     int32_t compute_err;   /* nonzero: compute RelErr (one more pass over A) */
     void *stream;          /* cudaStream_t */
     uint64_t batch_index;  /* third counter word of the Omega draw (Philox) */
@@ -231,6 +238,10 @@ EOD_API int64_t eod_abe_debug_launch_count(void);
  *   form 2 (reconstruction):  *err_out (device double) = ||D - X Y^T||_F
  *                             with X M x K, Y N x K and D the M x N
  *                             reference (ld ldd); D is not written.
+ *   form | 8:                 the same contraction in the TF32 form of
+ *                             EOD_MIXED_TF32 (X and Y split into two TF32
+ *                             terms; form 8 reads X through a transposed
+ *                             copy and expects TF32-exact Y).
  * Returns after synchronising `stream`; EOD_ETIMEOUT if a bounded device
  * wait ran out, EOD_EINVAL for bad sizes or leading dimensions. */
 EOD_API eod_status eod_abe_debug_tc_gemm(int32_t form, int64_t M, int64_t N, int64_t K, const float *X,

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_PKG, "libeodabe.so")
 
 EOD_OK, EOD_EINVAL, EOD_ENOMEM, EOD_ECUDA, EOD_ENONFINITE, EOD_ETIMEOUT, EOD_EPRECISION, EOD_EUNSUPPORTED = range(8)
 EOD_F64, EOD_F32 = 0, 1
-EOD_PLAIN, EOD_MIXED_BF16 = 0, 1
+EOD_PLAIN, EOD_MIXED_BF16, EOD_MIXED_TF32 = 0, 1, 2
 EOD_TOL_ABS, EOD_TOL_REL_FRO = 0, 1
 
 EXPORTED = [
@@ -173,7 +173,7 @@ def library() -> ctypes.CDLL:
 # ------------------------------------------------------------ conveniences --
 _DT = {torch.float64: EOD_F64, torch.float32: EOD_F32}
 _TORCH = {EOD_F64: torch.float64, EOD_F32: torch.float32}
-_PREC = {"plain": EOD_PLAIN, "mixed": EOD_MIXED_BF16, "mixed_bf16": EOD_MIXED_BF16}
+_PREC = {"plain": EOD_PLAIN, "mixed": EOD_MIXED_BF16, "mixed_bf16": EOD_MIXED_BF16, "mixed_tf32": EOD_MIXED_TF32}
 _TOLM = {"abs": EOD_TOL_ABS, "rel": EOD_TOL_REL_FRO}
 
 

@@ -310,7 +310,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     const int64_t cap = std::min(m, n);
     int64_t k = o.block_k > 0 ? o.block_k : 32;
     if (k > cap) k = cap;
-    const bool mixed = (o.precision == EOD_MIXED_BF16);
+    const bool mixed = (o.precision == EOD_MIXED_BF16 || o.precision == EOD_MIXED_TF32);
 
     HostMirror hm;
     EOD_TRY(hm.init());
@@ -370,7 +370,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     F->block_k = k;
 
     MixedOps<T> mx;
-    if (mixed) EOD_TRY(mx.prepare(A, m, n, lda, k, ar, &ws, s));
+    if (mixed) EOD_TRY(mx.prepare(A, m, n, lda, k, ar, &ws, s, o.precision == EOD_MIXED_TF32));
 
     OzCache oz;
     oz.on = std::is_same<T, double>::value && fp64_use_emulated(m, k, n);
@@ -704,7 +704,7 @@ static eod_status validate(const void *A, int64_t m, int64_t n, int64_t lda, dou
     if (!(tol > 0.0) || !std::isfinite(tol)) return EOD_EINVAL;
     if (o.power_iters < 0 || o.power_iters > kMaxPowerIters) return EOD_EINVAL;
     if (o.a_dtype != EOD_F64 && o.a_dtype != EOD_F32) return EOD_EINVAL;
-    if (o.precision != EOD_PLAIN && o.precision != EOD_MIXED_BF16) return EOD_EINVAL;
+    if (o.precision != EOD_PLAIN && o.precision != EOD_MIXED_BF16 && o.precision != EOD_MIXED_TF32) return EOD_EINVAL;
     if (o.tol_mode != EOD_TOL_ABS && o.tol_mode != EOD_TOL_REL_FRO) return EOD_EINVAL;
     if (o.block_k < 0 || o.block_k > 128) return EOD_EINVAL;
     if (m > 0x7FFFFFFFLL || n > 0x7FFFFFFFLL) return EOD_EINVAL;

@@ -1,5 +1,6 @@
 // Tensor-core contractions of the mixed path on sm_103a: tcgen05.mma
-// (kind::f16, BF16 operands, FP32 accumulation in TMEM) fed by TMA.
+// (kind::f16 with BF16 operands, or kind::tf32 with FP32-stored TF32
+// operands; FP32 accumulation in TMEM) fed by TMA.
 //
 //   sketch          Y   = (A_hi + A_lo + A_3) Omega   Alg. 1 step 4
 //   projection      C^T = A_hi^T Q_hi + A_hi^T Q_lo + A_lo^T Q_hi    Alg. 2 step 8
@@ -11,6 +12,11 @@
 // are about 2^-16 relative.  For the sketch A gets a third term A_3 =
 // bf16(A - A_hi - A_lo), which makes the split exact for FP32 data; Omega is
 // BF16-exact, so the sketch is then as accurate as an FP32 GEMM.
+// The TF32 form splits X as X_hi = X with its 13 low significand bits
+// cleared (exact in TF32) and X_lo = X - X_hi (exact in FP32, at most 13
+// significant bits, of which TF32 keeps 11): the dropped terms are about
+// 2^-21 relative, at half the BF16 MMA rate and twice the operand bytes.
+// TF32 operands are K-major only (the sketch reads a transposed copy of A).
 //
 // One CTA computes a 128 x BN tile of D.  Warp 0 issues TMA loads into a
 // ring of shared-memory stages (128-byte swizzle), warp 1 allocates TMEM and
@@ -39,7 +45,42 @@ namespace tc {
 constexpr int BM = 128;           // MMA M (one CTA, cta_group::1)
 constexpr int BK = 64;            // K per stage: 64 BF16 = one 128-byte swizzle row
 constexpr int UMMA_K = 16;        // K per tcgen05.mma (kind::f16)
+constexpr int BK_TF32 = 32;       // K per stage in the TF32 form: 32 FP32 = one 128-byte row
 constexpr int NTHREADS = 192;
+// Both forms advance 32 bytes of K per MMA (16 BF16 or 8 TF32 elements) and
+// 128 bytes per stage, so the shared-memory layout and descriptors are shared.
+
+// Instruction descriptor of kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 2-D FP32 map, 128-byte swizzle: the BF16 map's geometry in 4-byte elements
+inline bool make_map_f32(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer, uint64_t ld,
+                         uint32_t box_in, uint32_t box_out) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    if (((uintptr_t)base & 15) || ((ld * 4) & 15)) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld * 4};
+    cuuint32_t box[2] = {box_in, box_out};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 // ---------------------------------------------------------------- kernel ----
 struct Maps {
@@ -73,9 +114,10 @@ struct Cfg {
     static constexpr uint32_t TMEM_COLS = BN_ < 32 ? 32 : BN_;
 };
 
-template <bool A_MN, int BN_, int EPI>
+template <bool A_MN, int BN_, int EPI, bool TF32>
 __global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kernel(const __grid_constant__ Maps maps,
                                                                                    Params p) {
+    static_assert(!(TF32 && A_MN), "TF32 operands are K-major");
     using C = Cfg<A_MN, BN_, EPI>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -134,7 +176,7 @@ __global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kern
                 uint8_t *sa = smem + s * C::STAGE;
                 uint8_t *sb = sa + C::A_BYTES;
                 mbar_expect_tx(&full[s], C::STAGE);
-                const int k_el = (int)(kb * BK);
+                const int k_el = (int)(kb * (TF32 ? BK_TF32 : BK));
                 if (A_MN) {
                     // A stored M-contiguous: two 64 (M) x 64 (K) boxes
                     tma_load_2d(sa, &maps.a[pair], &full[s], (int)m0, k_el);
@@ -149,7 +191,7 @@ __global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kern
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         const bool leader = elect_one();
-        constexpr uint32_t idesc = idesc_bf16(BM, BN_, A_MN, false);
+        constexpr uint32_t idesc = TF32 ? idesc_tf32(BM, BN_) : idesc_bf16(BM, BN_, A_MN, false);
         for (int64_t it = 0; it < iters; ++it) {
             const int s = (int)(it % C::STAGES);
             const uint32_t round = (uint32_t)(it / C::STAGES);
@@ -171,7 +213,8 @@ __global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kern
                     if (A_MN) ad = sdesc(sa + kk * (UMMA_K * 128), BM * BK, 1024);   // LBO: next 64-row M block
                     else ad = sdesc(sa + kk * (UMMA_K * 2), 16, 1024);
                     bd = sdesc(sb + kk * (UMMA_K * 2), 16, 1024);
-                    umma_bf16(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                    if (TF32) umma_tf32(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                    else umma_bf16(tmem, ad, bd, idesc, (it > 0 || kk > 0) ? 1u : 0u);
                 }
                 umma_commit(&empty[s]);
             }
@@ -324,23 +367,64 @@ __global__ void split_transpose_kernel(const float *__restrict__ X, int64_t rows
     }
 }
 
-template <bool A_MN, int BN_, int EPI>
+// TF32 split of one FP32 value: hi = x with its 13 low significand bits
+// cleared (exactly a TF32 value), lo = x - hi (exact in FP32).
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
+    hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+    lo = x - hi;
+}
+
+// X (rows x cols, ldx) -> X_hi, X_lo (same shape, ld ldo), FP32 storage.
+__global__ void split_tf32_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                  float *__restrict__ hi, float *__restrict__ lo, int64_t ldo) {
+    const int64_t total = rows * cols;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / rows, i = e - j * rows;
+        float h, l;
+        split_tf32(X[i + j * ldx], h, l);
+        hi[i + j * ldo] = h;
+        lo[i + j * ldo] = l;
+    }
+}
+
+// Xt_hi / Xt_lo (cols x rows, ld ldt) = TF32 split of X^T, X rows x cols (ldx).
+__global__ void split_transpose_tf32_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                            float *__restrict__ hi, float *__restrict__ lo, int64_t ldt) {
+    __shared__ float tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t i = i0 + threadIdx.x, j = j0 + dy;
+        tile[dy][threadIdx.x] = (i < rows && j < cols) ? X[i + j * ldx] : 0.f;
+    }
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+        const int64_t j = j0 + threadIdx.x, i = i0 + dy;   // output (j, i) = X(i, j)
+        if (i < rows && j < cols) {
+            float h, l;
+            split_tf32(tile[threadIdx.x][dy], h, l);
+            hi[j + i * ldt] = h;
+            lo[j + i * ldt] = l;
+        }
+    }
+}
+
+template <bool A_MN, int BN_, int EPI, bool TF32>
 cudaError_t launch_tc(const Maps &maps, Params p, int splits, cudaStream_t s) {
     using C = Cfg<A_MN, BN_, EPI>;
-    EOD_CUDA_TRY(set_smem_once(tc_gemm_kernel<A_MN, BN_, EPI>, C::SMEM));
+    EOD_CUDA_TRY(set_smem_once(tc_gemm_kernel<A_MN, BN_, EPI, TF32>, C::SMEM));
     dim3 grid((unsigned)((p.M + BM - 1) / BM), (unsigned)((p.N + BN_ - 1) / BN_), (unsigned)splits);
     count_launch();
-    tc_gemm_kernel<A_MN, BN_, EPI><<<grid, NTHREADS, C::SMEM, s>>>(maps, p);
+    tc_gemm_kernel<A_MN, BN_, EPI, TF32><<<grid, NTHREADS, C::SMEM, s>>>(maps, p);
     return cudaGetLastError();
 }
 
-template <bool A_MN, int EPI>
+template <bool A_MN, int EPI, bool TF32>
 cudaError_t launch_bn(int bn, const Maps &maps, const Params &p, int splits, cudaStream_t s) {
     switch (bn) {
-    case 32: return launch_tc<A_MN, 32, EPI>(maps, p, splits, s);
-    case 64: return launch_tc<A_MN, 64, EPI>(maps, p, splits, s);
-    case 128: return launch_tc<A_MN, 128, EPI>(maps, p, splits, s);
-    default: return launch_tc<A_MN, 256, EPI>(maps, p, splits, s);
+    case 32: return launch_tc<A_MN, 32, EPI, TF32>(maps, p, splits, s);
+    case 64: return launch_tc<A_MN, 64, EPI, TF32>(maps, p, splits, s);
+    case 128: return launch_tc<A_MN, 128, EPI, TF32>(maps, p, splits, s);
+    default: return launch_tc<A_MN, 256, EPI, TF32>(maps, p, splits, s);
     }
 }
 
@@ -358,19 +442,26 @@ cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s) {
     using namespace tc;
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     const int bn = g.bn > 0 ? g.bn : pick_bn(g.N);
+    if (g.tf32 && g.a_mn_major) return cudaErrorInvalidValue;
     Maps maps;
     std::memset(&maps, 0, sizeof(maps));
     for (int i = 0; i < g.npairs; ++i) {
         const TcOperand &a = g.a[i], &b = g.b[i];
-        bool ok = g.a_mn_major ? make_map(&maps.a[i], a.ptr, a.inner, a.outer, a.ld, 64, 64)
-                               : make_map(&maps.a[i], a.ptr, a.inner, a.outer, a.ld, 64, BM);
-        ok = ok && make_map(&maps.b[i], b.ptr, b.inner, b.outer, b.ld, 64, (uint32_t)bn);
+        bool ok;
+        if (g.tf32) {
+            ok = make_map_f32(&maps.a[i], a.ptr, a.inner, a.outer, a.ld, BK_TF32, BM) &&
+                 make_map_f32(&maps.b[i], b.ptr, b.inner, b.outer, b.ld, BK_TF32, (uint32_t)bn);
+        } else {
+            ok = g.a_mn_major ? make_map(&maps.a[i], a.ptr, a.inner, a.outer, a.ld, 64, 64)
+                              : make_map(&maps.a[i], a.ptr, a.inner, a.outer, a.ld, 64, BM);
+            ok = ok && make_map(&maps.b[i], b.ptr, b.inner, b.outer, b.ld, 64, (uint32_t)bn);
+        }
         if (!ok) return cudaErrorInvalidValue;
     }
     Params p;
     p.M = g.M;
     p.N = g.N;
-    p.kblocks = (g.K + BK - 1) / BK;
+    p.kblocks = (g.K + (g.tf32 ? BK_TF32 : BK) - 1) / (g.tf32 ? BK_TF32 : BK);
     p.npairs = g.npairs;
     p.err_flag = g.err_flag;
     p.R = g.ref;
@@ -392,7 +483,7 @@ cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s) {
     }
     p.kblocks_per_split = (p.kblocks + splits - 1) / splits;
     const double flops = 2.0 * g.M * g.N * g.K * g.npairs;
-    const double bytes = 2.0 * g.npairs * ((double)g.M * g.K + (double)g.K * g.N) +
+    const double bytes = (g.tf32 ? 4.0 : 2.0) * g.npairs * ((double)g.M * g.K + (double)g.K * g.N) +
                          (g.epilogue == EPI_ERR ? 4.0 * g.M * g.N : 4.0 * g.M * g.N);
     ProfScope prof(PROF_TC_GEMM, flops, bytes, s);
     if (splits > 1) {
@@ -405,11 +496,15 @@ cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s) {
         p.split_stride = 0;
     }
     cudaError_t e;
-    if (g.epilogue == EPI_ERR)
-        e = g.a_mn_major ? launch_bn<true, EPI_ERR>(bn, maps, p, 1, s) : launch_bn<false, EPI_ERR>(bn, maps, p, 1, s);
+    if (g.tf32)
+        e = g.epilogue == EPI_ERR ? launch_bn<false, EPI_ERR, true>(bn, maps, p, 1, s)
+                                  : launch_bn<false, EPI_STORE, true>(bn, maps, p, splits, s);
+    else if (g.epilogue == EPI_ERR)
+        e = g.a_mn_major ? launch_bn<true, EPI_ERR, false>(bn, maps, p, 1, s)
+                         : launch_bn<false, EPI_ERR, false>(bn, maps, p, 1, s);
     else
-        e = g.a_mn_major ? launch_bn<true, EPI_STORE>(bn, maps, p, splits, s)
-                         : launch_bn<false, EPI_STORE>(bn, maps, p, splits, s);
+        e = g.a_mn_major ? launch_bn<true, EPI_STORE, false>(bn, maps, p, splits, s)
+                         : launch_bn<false, EPI_STORE, false>(bn, maps, p, splits, s);
     if (e != cudaSuccess) return e;
     if (splits > 1) {
         int blocks = (int)std::min<int64_t>((g.M * g.N + 255) / 256, 4 * kNumSMs * 8);
@@ -432,6 +527,26 @@ cudaError_t split_norm(const float *X, int64_t rows, int64_t cols, int64_t ldx, 
     ProfScope prof(PROF_STREAM, 2.0 * rows * cols, (x3 ? 10.0 : 8.0) * rows * cols, s);
     count_launch();
     tc::split_norm_kernel<<<blocks, 512, 0, s>>>(X, rows, cols, ldx, hi, lo, x3, ldo, partials, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t split_tf32(const float *X, int64_t rows, int64_t cols, int64_t ldx, float *hi, float *lo, int64_t ldo,
+                       cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    ProfScope prof(PROF_STREAM, 0.0, 12.0 * rows * cols, s);
+    count_launch();
+    const int64_t blocks = std::min<int64_t>((rows * cols + 255) / 256, 8LL * kNumSMs * 4);
+    tc::split_tf32_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, rows, cols, ldx, hi, lo, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t split_transpose_tf32(const float *X, int64_t rows, int64_t cols, int64_t ldx, float *hi, float *lo,
+                                 int64_t ldt, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    ProfScope prof(PROF_STREAM, 0.0, 12.0 * rows * cols, s);
+    count_launch();
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((cols + 31) / 32));
+    tc::split_transpose_tf32_kernel<<<grid, dim3(32, 8), 0, s>>>(X, rows, cols, ldx, hi, lo, ldt);
     return cudaGetLastError();
 }
 

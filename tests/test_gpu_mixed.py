@@ -86,15 +86,61 @@ def test_tc_reconstruction_error_form(eod, M, N, K):
     assert abs(err.item() - ref) <= 1e-3 * ref
 
 
+# the TF32 hi/lo split keeps ~21 significant bits of each FP32 operand
+TF32_TOL = 1e-5
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (300, 70, 200), (1000, 256, 513), (2051, 130, 777)])
+def test_tc_tf32_sketch_form(eod, M, N, K):
+    g = torch.Generator().manual_seed(M + N + K + 8)
+    X = _colmajor(torch.randn((M, K), generator=g)).cuda()
+    Y = _colmajor(_bf16_exact((K, N), g)).cuda()   # BF16-exact values are TF32-exact
+    D = _colmajor(torch.full((M, N), float("nan"))).cuda()
+    _run(eod, 8, M, N, K, X, Y, D)
+    ref = X.double() @ Y.double()
+    scale = X.double().abs() @ Y.double().abs()
+    assert torch.isfinite(D).all()
+    assert ((D.double() - ref).abs() <= TF32_TOL * scale + 1e-30).all()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (200, 37, 300), (513, 256, 1000), (2048, 20, 4100)])
+def test_tc_tf32_projection_form(eod, M, N, K):
+    g = torch.Generator().manual_seed(7 * M + N + K + 9)
+    X = _colmajor(torch.randn((K, M), generator=g)).cuda()
+    Y = _colmajor(torch.randn((K, N), generator=g)).cuda()
+    D = _colmajor(torch.full((M, N), float("nan"))).cuda()
+    _run(eod, 9, M, N, K, X, Y, D)
+    ref = X.double().t() @ Y.double()
+    scale = X.double().abs().t() @ Y.double().abs()
+    assert torch.isfinite(D).all()
+    err = ((D.double() - ref).abs() / (scale + 1e-30)).max().item()
+    assert err <= TF32_TOL, err
+    # a single TF32 pass would be ~2^-11: the split must do far better
+    assert err <= 1e-5
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (1000, 777, 130), (257, 1030, 400)])
+def test_tc_tf32_reconstruction_error_form(eod, M, N, K):
+    g = torch.Generator().manual_seed(3 * M + N + K + 10)
+    X = _colmajor(torch.randn((M, K), generator=g)).cuda()
+    Y = _colmajor(torch.randn((N, K), generator=g)).cuda()
+    P = X.double() @ Y.double().t()
+    R = _colmajor((P + 1e-2 * torch.randn((M, N), generator=g, dtype=torch.float64).cuda()).float())
+    err = torch.zeros(1, dtype=torch.float64, device="cuda")
+    _run(eod, 10, M, N, K, X, Y, R, err)
+    ref = torch.linalg.norm(R.double() - P).item()
+    assert abs(err.item() - ref) <= 1e-3 * ref
+
+
 # --------------------------------------------------------------------------
 # mixed factorisation vs the FP64 oracle
 # --------------------------------------------------------------------------
 
-def _factor_both(eod, A32, tol, mode, k, seed, batch=0):
+def _factor_both(eod, A32, tol, mode, k, seed, batch=0, precision="mixed"):
     A64 = A32.astype(np.float64)
     ref = oracle.eod_abe(A64, tol, mode, k=k, seed=seed, batch=batch)
     At = torch.from_numpy(np.asfortranarray(A32)).cuda()
-    f = eod.factor(At, tol, seed, block_k=k, tol_mode=("rel" if mode == 1 else "abs"), precision="mixed",
+    f = eod.factor(At, tol, seed, block_k=k, tol_mode=("rel" if mode == 1 else "abs"), precision=precision,
                    batch_index=batch)
     return f, ref
 
@@ -179,3 +225,22 @@ def test_mixed_exact_rank_noise_tail_matches_fp64(eod):
         fm = eod.factor(A32, 1e-4, w.seed, block_k=32, tol_mode="rel", precision="mixed", batch_index=i)
         assert fm.rank == fp.rank
         assert abs(fm.rel_err - fp.rel_err) <= 1e-4
+
+
+@pytest.mark.parametrize("case", ["exact_rank", "image_like", "harmonic"])
+def test_mixed_tf32_factorisations(eod, case):
+    """EOD_MIXED_TF32 (kind::tf32 contractions on two-term TF32 splits)
+    against the FP64 oracle: rank exact, |dRelErr| <= 1e-4."""
+    if case == "exact_rank":
+        w = W.exact_rank(m=600, n=450, r=25, seed=11)
+        A32, tol, k, seed = w.A.astype(np.float32), 1e-4, 16, 3
+    elif case == "image_like":
+        w = W.image_like(m=512, n=384, r=60, seed=22, dtype="f32", tol=0.05)
+        A32, tol, k, seed = w.A, w.tol, 32, w.seed
+    else:
+        w = W.harmonic(m=1024, n=1024, r=400, seed=3, tol=0.03)
+        A32, tol, k, seed = w.A, w.tol, 64, w.seed
+    f, ref = _factor_both(eod, A32, tol, 1, k, seed, precision="mixed_tf32")
+    assert f.precision == eod.EOD_MIXED_TF32
+    assert f.rank == ref["r"]
+    assert abs(f.rel_err - ref["rel_err"]) <= 1e-4
