@@ -394,7 +394,8 @@ def compare_forms(eod, steps, warmup, flush):
         del w.A
         m, n = A64.shape
         res = {}
-        for form, A, prec in (("plain_f64", A64, "plain"), ("plain_f32", A32, "plain"), ("mixed_bf16", A32, "mixed")):
+        for form, A, prec in (("plain_f64", A64, "plain"), ("plain_f32", A32, "plain"), ("mixed_bf16", A32, "mixed"),
+                              ("mixed_tf32", A32, "mixed_tf32")):
             for _ in range(warmup):
                 f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
                 f.close()
@@ -426,7 +427,8 @@ def compare_forms(eod, steps, warmup, flush):
             v["rank_equal_f64"] = v["rank"] == base["rank"]
             v["d_rel_err_vs_f64"] = abs(v["rel_err"] - base["rel_err"])
         out.append({"workload": name, "m": m, "n": n, "k": k, "forms": res,
-                    "mixed_speedup_vs_f64": base["ms"] / res["mixed_bf16"]["ms"]})
+                    "mixed_speedup_vs_f64": base["ms"] / res["mixed_bf16"]["ms"],
+                    "mixed_tf32_speedup_vs_f64": base["ms"] / res["mixed_tf32"]["ms"]})
         del A64, A32
         torch.cuda.empty_cache()
     ach = tc_fl / (tc_ms / 1e3) / 1e9 if tc_ms > 0 else None

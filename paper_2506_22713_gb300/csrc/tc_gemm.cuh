@@ -1,6 +1,6 @@
 // Interface of the tensor-core (tcgen05) contractions and of the mixed
-// (BF16 split, FP32 accumulation) forms of the sketch, the projection and the
-// reconstruction error.
+// (BF16 or TF32 split, FP32 accumulation) forms of the sketch, the
+// projection and the reconstruction error.
 #pragma once
 #include "common.cuh"
 
