@@ -52,7 +52,7 @@ typedef enum {
                               (eps < 1e-5 ||A||_F with EOD_F32 storage or on
                               the mixed path), or a Cholesky factorisation
                               broke down beyond the shifted fallback's reach */
-    EOD_EUNSUPPORTED = 7   /* valid request this build does not support */
+    EOD_EUNSUPPORTED = 7   /* valid request the library does not support */
 } eod_status;
 
 typedef enum { EOD_F64 = 0, EOD_F32 = 1 } eod_dtype;
