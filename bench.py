@@ -362,6 +362,7 @@ def run_ours(args):
         out["roofline_tensor"] = troof
         out["batched_mixed_vs_plain"] = compare_batched(eod, 1, 1)
         out["paper_table_mat2_f64"] = paper_mat2(eod)
+        out["robustness_matrices_f64"] = robustness_matrices(eod)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, sample, el = oracle_sample(A_np, w.tol * float(np.linalg.norm(A_np)), 15.0)
         out["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
@@ -479,6 +480,44 @@ def paper_mat2(eod, sizes=(4000, 8000, 12000)):
             f.close()
         del A
         torch.cuda.empty_cache()
+    return out
+
+
+def robustness_matrices(eod):
+    """The four matrix classes of Sec. 4.3 at n = 1000, plain FP64, k = 32,
+    tau = 0 and 2: one timed factorisation after one warm-up each, with the
+    rank, RelErr and the largest deviation of the R-values (|diag D-hat|) from
+    the singular values, max |log10(|D(i,i)| / sigma_i)| over i <= rank."""
+    import numpy as np
+    import torch
+    import workloads as W
+
+    cases = [("I (low rank + noise, alpha 0.005)", lambda: W.low_rank_plus_noise(alpha=0.005), 1e-12, "abs"),
+             ("I (low rank + noise, alpha 0.02)", lambda: W.low_rank_plus_noise(alpha=0.02), 1e-12, "abs"),
+             ("II (devil's stairs)", lambda: W.devils_stairs(1000), 1e-5, "rel"),
+             ("III (fast decay)", W.fast_decay, 1e-8, "rel"),
+             ("IV (slow decay)", W.slow_decay, 1e-3, "rel")]
+    out = []
+    for name, make, tol, mode in cases:
+        A_np = make()
+        s = np.linalg.svd(A_np, compute_uv=False)
+        A = torch.from_numpy(np.asfortranarray(A_np)).cuda()
+        for tau in (0, 2):
+            f = eod.factor(A, tol, 5, block_k=32, tol_mode=mode, power_iters=tau)
+            f.close()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f = eod.factor(A, tol, 5, block_k=32, tol_mode=mode, power_iters=tau)
+            e1.record()
+            e1.synchronize()
+            r = f.rank
+            d = np.abs(np.diag(f.D.cpu().numpy()))
+            dev = float(np.abs(np.log10(d[:r] / s[:r])).max()) if r > 0 else None
+            out.append({"matrix": name, "n": 1000, "tol": tol, "tol_mode": mode, "tau": tau, "rank": r,
+                        "rel_err": f.rel_err, "ms": e0.elapsed_time(e1), "max_log10_rvalue_over_sigma": dev})
+            f.close()
+        del A
     return out
 
 

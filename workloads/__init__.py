@@ -164,6 +164,31 @@ def devils_stairs(n: int = 90, seed: int = 7, step: int = 15) -> np.ndarray:
     return low_rank(rng, n, n, s)
 
 
+def low_rank_plus_noise(n: int = 1000, r: int = 20, alpha: float = 0.005, seed: int = 8) -> np.ndarray:
+    """Matrix I of Sec. 4.3 as printed: U diag(sigma) V^T + alpha sigma_r E
+    with sigma_1..sigma_r linear from 1 down to 1e-25, sigma_{r+1..n} = 0, E a
+    standard Gaussian n x n matrix, Haar U, V (only their first r columns
+    meet a nonzero sigma)."""
+    rng = np.random.default_rng(seed)
+    s = np.linspace(1.0, 1e-25, r)
+    A = low_rank(rng, n, n, s)
+    return np.asfortranarray(A + alpha * s[-1] * rng.standard_normal((n, n)))
+
+
+def fast_decay(n: int = 1000, seed: int = 9) -> np.ndarray:
+    """Matrix III of Sec. 4.3: U diag(exp(-i/6)) V^T, Haar U, V."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(1, n + 1)
+    return low_rank(rng, n, n, np.exp(-i / 6.0))
+
+
+def slow_decay(n: int = 1000, seed: int = 10) -> np.ndarray:
+    """Matrix IV of Sec. 4.3: U diag(i^-2) V^T, Haar U, V."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return low_rank(rng, n, n, i ** -2.0)
+
+
 def gaussian(m: int, n: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.asfortranarray(rng.standard_normal((m, n)))
