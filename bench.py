@@ -98,6 +98,17 @@ def _args():
     return p.parse_args()
 
 
+def _max_over_ranks(x, dist, device):
+    """The largest value of a host float over the ranks (an all-reduce on
+    `device`: "cuda" under NCCL, "cpu" under gloo); x itself with one rank."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -237,12 +248,9 @@ def run_ours(args):
         if profile:
             eod.eod_abe_debug_profile(0)
         launches = eod.eod_abe_debug_launch_count() - launches0
+        total_ms = _max_over_ranks(total_ms, dist, "cuda")
         if dist:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-            if dist:
-                dist.barrier()
+            dist.barrier()
         torch.cuda.synchronize()
         return total_ms, info, prof, kinds, launches
 
@@ -301,10 +309,7 @@ def run_ours(args):
         re2e, _ = eod.factor_host(Ah, w.tol, w.seed, block_k=BLOCK_K, tol_mode="rel", U_out=Uh, D_out=Dh, V_out=Vh)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = _max_over_ranks(e2e_s, dist, "cuda")
     e2e_val = ws * args.steps * eod.model_flops(M, N, re2e, BLOCK_K, True) / e2e_s / 1e9
 
     # roofline of the dominant kernel: the FP64 GEMM emulated on tcgen05
