@@ -10,10 +10,12 @@
 //   Alg. 2 steps 8-11      gemm (C^T = A^T Q), [gemm with fused error: Q C vs A],
 //                          CholQR2 (C^T = V R), CholQR2 (R^T = Qh D), gemm (U = Q Qh)
 //
-// The kernels live in gemm_simt.cu, stream_kernels.cu and chol.cu (plain
-// path) and tc_gemm.cu (tensor-core path).  The rank test reads a pivot
-// decision back to the host once per sub-panel; everything else stays on the
-// device.
+// The kernels live in oz_gemm.cu (FP64 products emulated on tcgen05),
+// gemm_simt.cu, gram.cu, stream_kernels.cu and chol.cu (plain paths) and
+// tc_gemm.cu / mixed.cu (the BF16 and TF32 mixed paths); tau >= 1 adds Alg. 2
+// steps 2-7 (subspace iteration) between the two algorithms.  The rank test
+// reads a pivot decision back to the host once per sub-panel; everything else
+// stays on the device.
 #include "common.cuh"
 #include "tc_gemm.cuh"
 #include "instrument.cuh"
