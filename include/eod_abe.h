@@ -58,9 +58,15 @@ typedef enum {
 typedef enum { EOD_F64 = 0, EOD_F32 = 1 } eod_dtype;
 
 typedef enum {
-    EOD_PLAIN = 0,         /* every contraction in the storage type of A
-                              (FP64 DFMA for EOD_F64, FP32 FFMA for EOD_F32);
-                              Gram/Cholesky/rank test/core in FP64 */
+    EOD_PLAIN = 0,         /* every contraction at the precision of A's storage
+                              type.  EOD_F64: products of at least 2^25
+                              multiply-adds run as an exact FP64 emulation on
+                              the tcgen05 tensor cores (each operand split into
+                              eight BF16 digit slices, integer-exact partial
+                              products, FP64 accumulation; normwise error about
+                              K 2^-48 |A(i,:)| |B(:,j)|), smaller ones as FP64
+                              DFMA; EOD_F32: FP32 FFMA.  Gram/Cholesky/rank
+                              test/core in FP64 */
     EOD_MIXED_BF16 = 1,    /* sketch, projection and reconstruction on tcgen05
                               tensor cores with FP32 accumulation: A split into
                               three BF16 terms for the sketch (exact for FP32
@@ -249,29 +255,33 @@ EOD_API eod_status eod_abe_debug_tc_gemm(int32_t form, int64_t M, int64_t N, int
                                          double *err_out, void *stream);
 
 /* ||A||_F of a device matrix without allocating anything: no cudaMalloc,
- * no cudaFree and no allocating library call, for callers that cannot
- * allocate device memory (code running while another framework owns the
- * device allocator, real-time pipelines that forbid allocation after
- * start-up, or threads recording work for later replay).  The paper has no
- * counterpart; it is the S0 reduction of eod_abe_factor run on a fixed
- * scratch area.
+ * no cudaFree and no allocating library call.  It is meant for callers that
+ * cannot allocate device memory: code that runs while another framework owns
+ * the device allocator (an allocation would go around it or fail), real-time
+ * loops that forbid allocation once they are running (an allocation can
+ * block or synchronise the device), and services with a fixed memory budget.
+ * The paper has no counterpart; it is the S0 reduction of eod_abe_factor run
+ * on a fixed scratch area.
  *
  * A: device matrix, m x n, column-major, ld lda >= m, type dtype (EOD_F64 or
  * EOD_F32).  norm_out: device pointer to one double, receives ||A||_F
- * (FP64 accumulation, the same reduction order as eod_abe_factor's norm_a).
- * nonfinite_out: device pointer to one int32, receives 1 if A holds a NaN
- * or an infinity, else 0 (it is cleared by the call).  stream: cudaStream_t.
- * The call only enqueues work and returns; read the outputs after
- * synchronising the stream.
+ * (FP64 accumulation; the same kernels, grid and reduction order as
+ * eod_abe_factor's norm_a, so the same bits).  nonfinite_out: device pointer
+ * to one int32, receives 1 if A holds a NaN or an infinity, else 0 (it is
+ * cleared by the call).  stream: cudaStream_t.  The call only enqueues work
+ * and returns; read the outputs after synchronising the stream.  The call is
+ * never included in the eod_abe_debug_profile timing (that timing creates
+ * CUDA events); it does count in eod_abe_debug_launch_count.
  *
  * Scratch: the per-block partial sums live in a static device array of
  * 58,368 bytes (4864 partial sums and flags) that every GPU loading this
- * library keeps until the process exits.  The first call on each device
- * looks the array's device address up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All
- * calls share the array, which keeps the last call's partials: calls that
- * overlap on the GPU (different streams, or different host threads on the
- * same device) race on it and must be serialised by the caller.
+ * library keeps until the process exits.  The first call on each device (and
+ * the first after a cudaDeviceReset) looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array, which keeps the
+ * last call's partials: calls that overlap on the GPU (different streams, or
+ * different host threads on the same device) race on it and must be
+ * serialised by the caller.
  *
  * Errors: EOD_EINVAL for NULL pointers, m < 1, n < 1, lda < m, an unknown
  * dtype, m or n above 2^31 - 1, or m*n above 2^40 elements (the largest
@@ -313,6 +323,17 @@ EOD_API eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w, i
 EOD_API eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,
                                           double alpha, const double *A, int64_t lda, const double *B, int64_t ldb,
                                           double beta, double *C, int64_t ldc, void *stream);
+
+/* Test hook (no counterpart in the paper): exercises the bounded device-side
+ * wait every tcgen05 kernel of the library uses on its mbarriers.  One CTA
+ * waits on an mbarrier that expects one arrival, for at most budget_cycles
+ * SM clock cycles; the arrival is made first when `arrive` is nonzero.  No
+ * copy or MMA is in flight during the wait, so a wait that runs out leaves
+ * the context usable: the kernel records the time-out and returns.  Returns
+ * after synchronising `stream`: EOD_OK when the wait completed, EOD_ETIMEOUT
+ * when it ran out, EOD_EINVAL for budget_cycles outside [1, 4e9] (the
+ * library's own per-wait budget is 4e9 cycles, about 2 s). */
+EOD_API eod_status eod_abe_debug_bounded_wait(int64_t budget_cycles, int32_t arrive, void *stream);
 
 /* Build identification (static string). */
 EOD_API const char *eod_abe_version(void);

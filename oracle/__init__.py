@@ -26,13 +26,23 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 
 
+_CFLAGS = ["-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+
+
+def _compile(src: str, out: str) -> None:
+    """gcc with OpenMP (the column loops shared among threads, bit-identical
+    to one thread); without OpenMP if this compiler lacks it."""
+    base = ["gcc", *_CFLAGS]
+    res = subprocess.run(base + ["-fopenmp", "-o", out, src, "-lm"], capture_output=True, text=True)
+    if res.returncode != 0:
+        subprocess.run(base + ["-o", out, src, "-lm"], check=True)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/liboracle.so`` (no fast-math, no FMA
     contraction, so x86 and Arm hosts give the same bits)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-               "-ffp-contract=off", "-fno-fast-math", "-o", _LIB + ".tmp", _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        _compile(_SRC, _LIB + ".tmp")
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
 
@@ -66,6 +76,10 @@ def configure(lib):
     lib.orc_storage_entries.restype = ctypes.c_int64
     lib.orc_storage_rank_bound.argtypes = [ctypes.c_int64, ctypes.c_int64]
     lib.orc_storage_rank_bound.restype = ctypes.c_double
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
+    lib.orc_set_threads.restype = ctypes.c_int
+    lib.orc_get_threads.argtypes = []
+    lib.orc_get_threads.restype = ctypes.c_int
     return lib
 
 
@@ -75,8 +89,7 @@ def compile_variant(src_text: str, out_path: str) -> str:
     src = out_path + ".c"
     with open(src, "w") as fh:
         fh.write(src_text)
-    subprocess.run(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                    "-ffp-contract=off", "-fno-fast-math", "-o", out_path, src, "-lm"], check=True)
+    _compile(src, out_path)
     return out_path
 
 
@@ -91,6 +104,17 @@ def _load():
         build()
         _lib = configure(ctypes.CDLL(_LIB))
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's column loops (n <= 0: every core); returns
+    the count in effect (1 when built without OpenMP).  Results do not
+    depend on it."""
+    return int(_load().orc_set_threads(int(n)))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def _ptr(a: np.ndarray, t=_f64p):

@@ -14,6 +14,13 @@
  * dimension; every loop is the textbook one, written for a reader checking
  * it against the paper, not for speed.  All arithmetic is IEEE double.
  *
+ * Threads: when compiled with OpenMP, the loops over independent output
+ * columns (of the dense products, of the reflector updates and of Omega)
+ * are shared among threads.  Every entry is still computed by one thread in
+ * the same order as the serial loop, so the results are bit-identical for
+ * any thread count (tested); reductions over a whole matrix (norms, the
+ * error) stay serial.  orc_set_threads() picks the count.
+ *
  * Pins (what each function is checked against, outside itself):
  *   orc_philox4x32_10   published Philox4x32-10 known-answer vectors
  *   orc_omega           Gaussian moments + KS test, BF16 exactness
@@ -34,8 +41,31 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define IX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+/* Threads used by the column loops below (1 without OpenMP), one setting
+ * for the whole process whichever thread calls in.  n <= 0 selects every
+ * available core.  Returns the count now in effect. */
+static int g_threads = 0;
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return g_threads > 0 ? g_threads : omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
+
+int orc_set_threads(int n)
+{
+    g_threads = n > 0 ? n : 0;
+    return orc_get_threads();
+}
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,        */
@@ -109,6 +139,7 @@ double orc_omega_entry(uint64_t seed, uint32_t row, uint32_t col, uint32_t batch
 void orc_omega(int64_t n, int64_t col0, int64_t ncols, uint64_t seed,
                uint64_t batch, double *out)
 {
+    #pragma omp parallel for schedule(static) num_threads(orc_get_threads()) if (n * ncols > 65536)
     for (int64_t c = 0; c < ncols; ++c)
         for (int64_t i = 0; i < n; ++i)
             out[IX(i, c, n)] = orc_omega_entry(seed, (uint32_t)i,
@@ -124,6 +155,7 @@ void orc_omega(int64_t n, int64_t col0, int64_t ncols, uint64_t seed,
 static void mat_mul(int64_t m, int64_t p, int64_t q, const double *A, int64_t lda,
                     const double *B, int64_t ldb, double *C, int64_t ldc)
 {
+    #pragma omp parallel for schedule(static) num_threads(orc_get_threads()) if (m * p * q > 1000000)
     for (int64_t j = 0; j < p; ++j) {
         for (int64_t i = 0; i < m; ++i) C[IX(i, j, ldc)] = 0.0;
         for (int64_t l = 0; l < q; ++l) {
@@ -137,6 +169,7 @@ static void mat_mul(int64_t m, int64_t p, int64_t q, const double *A, int64_t ld
 static void mat_tmul(int64_t m, int64_t p, int64_t q, const double *A, int64_t lda,
                      const double *B, int64_t ldb, double *C, int64_t ldc)
 {
+    #pragma omp parallel for schedule(static) num_threads(orc_get_threads()) if (m * p * q > 1000000)
     for (int64_t j = 0; j < q; ++j)
         for (int64_t i = 0; i < p; ++i) {
             double s = 0.0;
@@ -177,6 +210,7 @@ int orc_householder_qr(int64_t m, int64_t p, double *W, int64_t ldw,
         tau[j] = (beta - x0) / beta;
         diag[j] = beta;
         /* apply H = I - tau v v^T to the trailing columns */
+        #pragma omp parallel for schedule(static) num_threads(orc_get_threads()) if ((p - j) * m > 65536)
         for (int64_t c = j + 1; c < p; ++c) {
             double s = W[IX(j, c, ldw)];
             for (int64_t i = j + 1; i < m; ++i) s += W[IX(i, j, ldw)] * W[IX(i, c, ldw)];
@@ -194,6 +228,7 @@ int orc_householder_qr(int64_t m, int64_t p, double *W, int64_t ldw,
         for (int64_t i = 0; i < m; ++i) Q[IX(i, c, ldq)] = (i == c) ? 1.0 : 0.0;
     for (int64_t j = p - 1; j >= 0; --j) {
         if (tau[j] == 0.0) continue;
+        #pragma omp parallel for schedule(static) num_threads(orc_get_threads()) if ((p - j) * m > 65536)
         for (int64_t c = j; c < p; ++c) {
             double s = Q[IX(j, c, ldq)];
             for (int64_t i = j + 1; i < m; ++i) s += W[IX(i, j, ldw)] * Q[IX(i, c, ldq)];
@@ -265,6 +300,7 @@ int orc_basis_ext(const double *A, int64_t m, int64_t n, int64_t lda, double eps
         mat_mul(m, f, n, A, lda, Om, n, Y, m);
         for (int pass = 0; pass < 2 && kept > 0; ++pass) {
             mat_tmul(m, kept, f, Q, m, Y, m, S, cap);          /* S = Q^T Y */
+            #pragma omp parallel for schedule(static) num_threads(orc_get_threads()) if (m * f * kept > 1000000)
             for (int64_t c = 0; c < f; ++c)
                 for (int64_t l = 0; l < kept; ++l) {
                     double s = S[IX(l, c, cap)];

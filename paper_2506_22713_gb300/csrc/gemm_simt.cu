@@ -1,10 +1,13 @@
-// SIMT GEMM for the plain (FP64 / FP32) path: every dense contraction of
-// Alg. 1 and Alg. 2 that is not on the tensor cores — the sketch A*Omega
-// (Alg. 1 step 4), the two block Gram-Schmidt projections Q^T Y and Y - Q S
-// (step 4, applied twice), the Gram matrices of CholQR (step 5), the
-// projection C^T = A^T Q (Alg. 2 step 8), the triangular solves and products
-// of the core (steps 9-11) and the reconstruction Q C with its fused
-// Frobenius error (Sec. 4.1).
+// SIMT GEMM of the plain (FP64 / FP32) path: the dense contractions of
+// Alg. 1 and Alg. 2 that do not go to the tensor cores.  With FP32 data that
+// is all of them but the core's large Gram matrices (widened to FP64 and
+// emulated in oz_gemm.cu): the sketch A*Omega of Alg. 1 step 4, the two block
+// Gram-Schmidt projections Q^T Y and Y - Q S of step 4, the CholQR Grams of
+// step 5, the projection C^T = A^T Q of Alg. 2 step 8, the triangular solves
+// and products of steps 9-11 and the reconstruction Q C with its fused
+// Frobenius error of Sec. 4.1.  With FP64 data only the products below 2^25
+// multiply-adds (and the CGS2 residual's matrix-vector products) run here:
+// the larger ones are the FP64 emulation on tcgen05 in oz_gemm.cu.
 //
 // Tile TS x TS x 16 (TS = 64, 32 or 16: the smaller tiles spread products too
 // small to fill the 152 SMs with 64-tiles), 256 threads, (TS/16)^2 outputs

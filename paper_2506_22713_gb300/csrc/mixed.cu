@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "instrument.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 #include <algorithm>
 
@@ -219,6 +220,41 @@ eod_status MixedOps<float>::check(cudaStream_t s) {
 }
 
 }  // namespace eod
+
+namespace eod {
+namespace {
+// One CTA waits on an mbarrier of one expected arrival, with the same bounded
+// wait the tcgen05 kernels use; the arrival is made only when `arrive` is
+// set.  No copy or MMA is in flight, so a wait that runs out leaves nothing
+// behind: the kernel records the time-out in *flag and returns.
+__global__ void bounded_wait_kernel(long long budget, int arrive, int *flag) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && arrive) tc::mbar_arrive(&bar);
+    const bool ok = tc::mbar_wait(&bar, 0, budget);
+    if (!__all_sync(0xffffffffu, ok ? 1 : 0) && threadIdx.x == 0) atomicExch(flag, 1);
+}
+}  // namespace
+}  // namespace eod
+
+// Test hook of the bounded waits (EOD_ETIMEOUT path).
+extern "C" eod_status eod_abe_debug_bounded_wait(int64_t budget_cycles, int32_t arrive, void *stream) {
+    using namespace eod;
+    if (budget_cycles < 1 || budget_cycles > tc::kWaitBudget) return EOD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Arena ar(s);
+    int *flag;
+    MX_ST(ar.get(&flag, 1));
+    MX_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    count_launch(1);
+    bounded_wait_kernel<<<1, 32, 0, s>>>((long long)budget_cycles, arrive ? 1 : 0, flag);
+    MX_TRY(cudaGetLastError());
+    int h = 0;
+    MX_TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MX_TRY(cudaStreamSynchronize(s));
+    return h ? EOD_ETIMEOUT : EOD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Test hook: one tensor-core contraction in each of the three forms.

@@ -5,6 +5,7 @@
 #include "common.cuh"
 #include "instrument.cuh"
 
+#include <cuda.h>
 #include <mutex>
 
 namespace eod {
@@ -308,21 +309,55 @@ constexpr size_t kNoAllocScratchBytes = (size_t)kNoAllocMaxBlocks * (sizeof(doub
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch per device ordinal, looked up once per
-// device (with that device current) on the first call made on it.
+// Device address of g_noalloc_scratch per device ordinal, looked up (with
+// that device current) on the first call made in each context of the device.
+// The cache is keyed on the context's unique id as well, so a call made after
+// cudaDeviceReset (which destroys the context and may move the array) looks
+// the address up again instead of using the old one.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[64] = {};
+unsigned long long g_noalloc_ctx[64] = {};
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// id of the calling thread's current context (0 if it cannot be read)
+unsigned long long current_context_id() {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 eod_status noalloc_scratch(void **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
     if (dev < 0 || dev >= 64) return EOD_EUNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_noalloc_addr[dev] || ctx == 0 || ctx != g_noalloc_ctx[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) { cudaGetLastError(); return EOD_ECUDA; }
         g_noalloc_addr[dev] = p;
+        // the lookup has made the device's primary context current if it was
+        // not yet: record its id now (0 again only if it cannot be read, in
+        // which case every call looks the address up)
+        g_noalloc_ctx[dev] = current_context_id();
     }
     *out = g_noalloc_addr[dev];
     return EOD_OK;
@@ -341,7 +376,7 @@ eod_status fro_norm_noalloc(const T *A, int64_t m, int64_t n, int64_t lda, doubl
     // the flag is OR-ed by the finalize kernel: clear it first; the partials
     // are all rewritten by this call before they are read
     if (cudaMemsetAsync(flag_out, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
-    ProfScope prof(PROF_STREAM, 2.0 * m * n, (double)sizeof(T) * m * n, s);
+    // never profiled: the per-launch timing would create CUDA events
     count_launch(2);
     sumsq_kernel<T><<<blocks, 512, 0, s>>>(A, m, n, lda, part, pf);
     if (cudaGetLastError() != cudaSuccess) return EOD_ECUDA;

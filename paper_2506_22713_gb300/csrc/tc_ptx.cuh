@@ -35,12 +35,13 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *bar, uint32_t parity
         : "memory");
     return ok;
 }
-// true when the phase with the given parity completed; false after the budget
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// true when the phase with the given parity completed; false once `budget`
+// SM clock cycles have passed without it
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget = kWaitBudget) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitBudget) return false;
+        if (clock64() - t0 > budget) return false;
     }
     return true;
 }

@@ -96,3 +96,10 @@ def test_opts_default_layout(eod):
 
 def test_free_null_is_noop(eod):
     eod.eod_abe_free(None)
+
+
+def test_bounded_wait_hook_rejects_bad_budgets(eod):
+    # checked on the host before any launch
+    assert eod.eod_abe_debug_bounded_wait(0, 1, None) == eod.EOD_EINVAL
+    assert eod.eod_abe_debug_bounded_wait(-5, 0, None) == eod.EOD_EINVAL
+    assert eod.eod_abe_debug_bounded_wait(4000000001, 0, None) == eod.EOD_EINVAL

@@ -336,3 +336,28 @@ def test_subspace_iteration_core_factors():
     assert np.linalg.norm(U.T @ U - np.eye(r)) <= 1e-12
     assert np.linalg.norm(V.T @ V - np.eye(r)) <= 1e-12
     assert np.linalg.norm(U @ D @ V.T - Q @ C) <= 1e-12 * np.linalg.norm(A)
+
+
+# --------------------------------------------------------------------------
+# Threads: the column loops shared among OpenMP threads give the same bits
+# --------------------------------------------------------------------------
+
+def test_thread_count_does_not_change_any_bit():
+    """Each output entry is computed by one thread in the serial loop's order,
+    so 1, 3 and all threads must agree bit for bit (factors, T diagonal,
+    RelErr), with and without subspace iteration."""
+    w = W.image_like(m=700, n=600, r=80, tol=1e-3)
+    before = oracle.get_threads()
+    try:
+        for tau in (0, 1):
+            res = {}
+            for t in (1, 3, 0):
+                oracle.set_threads(t)
+                res[t] = oracle.eod_abe(w.A, w.tol, 1, k=32, seed=2, tau=tau)
+            for t in (3, 0):
+                for key in ("U", "D", "V", "Q", "C", "tdiag"):
+                    assert np.array_equal(res[1][key], res[t][key]), (tau, t, key)
+                assert res[1]["rel_err"] == res[t]["rel_err"]
+                assert res[1]["r"] == res[t]["r"]
+    finally:
+        oracle.set_threads(before)

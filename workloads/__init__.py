@@ -189,6 +189,23 @@ def slow_decay(n: int = 1000, seed: int = 10) -> np.ndarray:
     return low_rank(rng, n, n, i ** -2.0)
 
 
+def mat2(n: int = 4000, r: int | None = None, seed: int | None = None, tol: float = 1e-8) -> Workload:
+    """The strictly rank-deficient test matrix of Sec. 4 (Eq. (mat2)):
+    A = U diag(sigma_1..sigma_r, 0..0) V^T, n x n, with U, V orthogonal
+    (Haar: only their first r columns meet a nonzero sigma, so those are
+    drawn as Haar n x r frames) and sigma the r draws of uniform(0, 1) sorted
+    in decreasing order; r = 0.4 n as in the paper's timing tables.  FP64,
+    absolute tol 1e-8 (between sigma_r, about 1/r, and the rounding floor
+    about 1e-12), Omega seed 7."""
+    r = int(0.4 * n) if r is None else int(r)
+    rng = np.random.default_rng(1000 + n if seed is None else seed)
+    sig = np.sort(rng.uniform(0.0, 1.0, r))[::-1]
+    A = low_rank(rng, n, n, sig)
+    return Workload(f"mat2_{n}_r{r}", A, "f64", tol, 0, 7,
+                    note="Eq. (mat2): Haar U, V, sigma = sorted uniform(0,1), r = 0.4n",
+                    meta={"r_true": r})
+
+
 def gaussian(m: int, n: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.asfortranarray(rng.standard_normal((m, n)))
@@ -201,5 +218,6 @@ def by_name(name: str, **kw) -> Workload:
         "harmonic": harmonic,
         "pixel_batch": pixel_batch,
         "hyperspectral": hyperspectral,
+        "mat2": mat2,
     }
     return table[name](**kw)
