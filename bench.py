@@ -1,15 +1,20 @@
 #!/usr/bin/env python3
 """Benchmark of power-free EOD-ABE on one GB300 (or N replicas).
 
-Workload: the image-like 2048 x 2048 matrix (rank-150 U diag(255 i^-1.5) V^T
-with Haar U, V plus Gaussian noise of std 1e-4 * 255), relative tolerance
-1e-3, FP64 storage, plain FP64 path, k = 64.  One step = one complete
-factorisation through the C ABI (Alg. 1 + Alg. 2 steps 8-11 + the
-reconstruction error), inputs resident in HBM.  The metric is GFLOP/s of the
-paper's cost model (Sec. 3.4) for tau = 0 plus the 2mnr of the
-reconstruction; the same line reports the FP32-storage plain form, the
-roofline of the dominant kernel, the host-buffer end-to-end rate and the
-FP64 oracle timed on the host cores.
+Headline workload: the harmonic 8192 x 8192 FP32 matrix (rank-400
+U diag(1/i) V^T with Haar U, V plus Gaussian noise of std 1e-6; relative
+tolerance 0.0128, twice the noise floor; the method reveals rank 455), k = 64.
+One step = one complete factorisation through the C ABI (Alg. 1 + Alg. 2
+steps 8-11 + the reconstruction error), inputs resident in HBM, L2 flushed
+between steps.  The metric is GFLOP/s of the paper's cost model (Sec. 3.4,
+tau = 0, plus the 2mnr of the reconstruction) for the mixed BF16 form, with
+the plain FP64 form timed on the same matrix (widened to FP64) beside it and
+their ratio at equal rank and |dRelErr| <= 1e-4.  The headline steps run
+with the library's instrumentation off; the roofline of the dominant kernel
+comes from a separate profiled pass.  The same line reports the host-buffer
+end-to-end rate, the other precision forms, the other workloads (image-like
+2048^2, hyperspectral 262144 x 224, the 256-matrix pixel batch), and the FP64
+oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,22 +38,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "EOD-ABE GFLOP/s & % roofline, mixed vs plain FP64 at rel-err ≤1e-4"
-WORKLOAD = "image-like 2048x2048, rank-150 s_i=255 i^-1.5 + noise 1e-4*s_1, tol 1e-3 relative"
-M = N = 2048
-BLOCK_K = 64
+WORKLOAD = ("harmonic 8192x8192 FP32: rank-400 s_i=1/i (Haar U, V) + Gaussian noise 1e-6, tol 0.0128 relative, "
+            "k=64; mixed BF16 form (plain FP64 form on the same matrix beside it)")
+HEAD_K = 64
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+FP64_SM_PEAK_GFLOPS = FP64_PEAK_GFLOPS / 152
 # FP32 (FFMA) peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
-
-
-def _measured_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            d = json.load(fh)
-        return float(d["bf16_tflops"]) * 1e3, float(d["hbm_gbs"]), "measured"
-    except Exception:
-        return 1.9e6, 6800.0, "fallback"
 L2_BYTES = 129 * 1024 * 1024
 # kernel kinds of the library's profile counters, in PROF_* order
 KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm", "oz_slice"]
@@ -56,10 +53,22 @@ KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm", "oz_slice
 OZ_PAIRS = 36
 
 
+def _measured_peaks():
+    """(bf16 burst GFLOP/s, bf16 sustained GFLOP/s, HBM GB/s, source)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return (float(d["bf16_tflops"]) * 1e3, float(d.get("bf16_tflops_sustained", d["bf16_tflops"])) * 1e3,
+                float(d["hbm_gbs"]), "measured")
+    except Exception:
+        return 1.9e6, 1.7e6, 6800.0, "fallback"
+
+
 PROFILE_CASES = {
     "image2048_f64": ("image_like", {}, "f64", "plain", 64),
     "image2048_mixed": ("image_like", {}, "f32", "mixed", 64),
     "harmonic8192_mixed": ("harmonic", {}, "f32", "mixed", 64),
+    "harmonic8192_f64": ("harmonic", {}, "f64", "plain", 64),
     "hyperspectral_mixed": ("hyperspectral", {}, "f32", "mixed", 16),
 }
 
@@ -92,7 +101,9 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-compare", action="store_true", help="skip the mixed-vs-plain comparison workloads")
+    p.add_argument("--cpu-one-core", action="store_true",
+                   help="also time the whole oracle on one host core (minutes)")
+    p.add_argument("--no-compare", action="store_true", help="skip the other workloads")
     p.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
                    help="run one warm-up and one factorisation of a named workload (for ncu) and exit")
     return p.parse_args()
@@ -117,25 +128,26 @@ def _dist():
 
 
 # ----------------------------------------------------------------- oracle --
-def oracle_sample(A_np, eps, seconds):
-    """Times the FP64 oracle's Alg. 1 on the first b blocks of the same matrix
-    (b chosen so the run takes about `seconds`); returns (GFLOP/s, sample text,
-    elapsed).  The numerator is the cost model's Alg. 1 term mnr + 4mrk
-    multiply-adds for the r = b*k columns processed."""
+def oracle_whole(A64, tol, k, seed, threads):
+    """The FP64 oracle's whole method (Alg. 1, Alg. 2 steps 8-11 and the
+    explicit reconstruction error) on `threads` host threads (0 = all cores);
+    returns (GFLOP/s of the cost model at the oracle's rank, seconds, rank,
+    threads used)."""
     import oracle
-    m, n = A_np.shape
+    used = oracle.set_threads(threads)
     t0 = time.perf_counter()
-    oracle.basis_ext(A_np, eps, k=BLOCK_K, seed=2, max_blocks=1)
-    t1 = time.perf_counter() - t0
-    b = max(1, min(int(seconds / max(t1, 1e-6)), min(m, n) // BLOCK_K))
-    t0 = time.perf_counter()
-    Q, _ = oracle.basis_ext(A_np, eps, k=BLOCK_K, seed=2, max_blocks=b)
+    ref = oracle.eod_abe(A64, tol, 1, k=k, seed=seed)
     el = time.perf_counter() - t0
-    r = Q.shape[1]
-    flops = 2.0 * (m * n * r + 4.0 * m * r * BLOCK_K)
-    sample = (f"FP64 oracle (plain C, 1 thread), Alg. 1 on the first {b} blocks (k={BLOCK_K}, {r} columns) "
-              f"of the same {m}x{n} matrix; GFLOP/s of the cost model's mnr+4mrk term")
-    return flops / el / 1e9, sample, el
+    m, n = A64.shape
+    r = ref["r"]
+    flops = 2.0 * (2.0 * m * n * r + m * r * r + 2.0 * n * r * r + 2.0 * r ** 3 + 4.0 * m * r * k) + 2.0 * m * n * r
+    return flops / el / 1e9, el, r, used
+
+
+def _oracle_sample_text(cores, r):
+    return (f"whole method (Alg. 1 + Alg. 2 steps 8-11 + explicit RelErr) of the FP64 oracle (plain C, naive "
+            f"loops, OpenMP over output columns) on the same 8192x8192 harmonic matrix widened to FP64, "
+            f"k={HEAD_K}, one run on {cores} host thread(s); rank {r}; GFLOP/s of the same cost model as value")
 
 
 # ----------------------------------------------------------------- clocks --
@@ -195,7 +207,114 @@ def _traffic_for(kind_name, source_files):
     return None
 
 
+KIND_SOURCES = {
+    "oz_gemm": ["paper_2506_22713_gb300/csrc/oz_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"],
+    "tc_gemm": ["paper_2506_22713_gb300/csrc/tc_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"],
+    "chol": ["paper_2506_22713_gb300/csrc/chol.cu"],
+    "gemm_simt": ["paper_2506_22713_gb300/csrc/gemm_simt.cu"],
+    "stream": ["paper_2506_22713_gb300/csrc/stream_kernels.cu"],
+}
+
+
+def roofline_of(kind, rec, peaks):
+    """Roofline entry of one kernel kind from its profiled launches: achieved
+    = the launches' algorithmic flops (or bytes) / their summed device time."""
+    bf16_burst, bf16_sus, hbm, src = peaks
+    ms = rec["ms"]
+    fl, by, n = rec["flops"], rec["bytes"], rec["launches"]
+    out = {"kernel_kind": kind, "launches": n, "ms": ms}
+    if kind == "tc_gemm":
+        ach = fl / (ms / 1e3) / 1e9
+        out.update(bound="tensor", achieved=ach, peak=bf16_sus, unit="GFLOP/s",
+                   peak_source=f"{src} BF16 sustained (MEASURED_PEAKS.json)",
+                   note="achieved counts one product per launch (the method's flops); the BF16 split executes "
+                        "two or three")
+    elif kind == "oz_gemm":
+        ach = fl / (ms / 1e3) / 1e9
+        out.update(bound="tensor", achieved=ach, peak=bf16_sus / OZ_PAIRS, unit="GFLOP/s",
+                   peak_source=f"{src} BF16 sustained / {OZ_PAIRS} slice-pair products per FP64 multiply-add",
+                   note="FP64 flops of the method (upper-only and triangular launches counted at their share)")
+    elif kind == "chol":
+        ach = fl / (ms / 1e3) / 1e9
+        out.update(bound="alu", achieved=ach, peak=FP64_SM_PEAK_GFLOPS, unit="GFLOP/s",
+                   peak_source="FP64 of one SM from unit counts: 2 DFMA/clk x 2 flop x 2070 MHz (the kernel is one "
+                               "CTA)")
+    elif kind == "gemm_simt":
+        ach = fl / (ms / 1e3) / 1e9
+        out.update(bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s",
+                   peak_source="FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz")
+    else:
+        ach = by / (ms / 1e3) / 1e9
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s",
+                   peak_source=f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)")
+    out["frac"] = out["achieved"] / out["peak"] if out["peak"] else None
+    out["flops_per_launch"] = fl / n if n else None
+    out["bytes_per_launch"] = by / n if n else None
+    tr = _traffic_for(kind, KIND_SOURCES.get(kind, []))
+    out["traffic"] = tr[0] if tr else None
+    out["traffic_launch"] = tr[1] if tr else None
+    return out
+
+
 # ---------------------------------------------------------------- our arm --
+class Stepper:
+    """Times whole factorisations with CUDA events on the launching stream,
+    L2 flushed (a 258 MB write) before every timed step."""
+
+    def __init__(self, eod, torch, dist, flush):
+        self.eod, self.torch, self.dist, self.flush = eod, torch, dist, flush
+        self.stream = torch.cuda.current_stream()
+
+    def run(self, fn, steps, warmup):
+        torch = self.torch
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        l0 = self.eod.eod_abe_debug_launch_count()
+        total, info = 0.0, None
+        for _ in range(steps):
+            self.flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            info = fn()
+            e1.record(self.stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        launches = self.eod.eod_abe_debug_launch_count() - l0
+        total = _max_over_ranks(total, self.dist, "cuda")
+        if self.dist:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        return total, info, launches
+
+    def profile(self, fn, steps):
+        """Per-kind launches, device ms, flops and bytes over `steps` steps."""
+        eod = self.eod
+        fn()
+        self.torch.cuda.synchronize()
+        eod.eod_abe_debug_profile(1)
+        for _ in range(steps):
+            self.flush.zero_()
+            fn()
+        self.torch.cuda.synchronize()
+        kinds = {k: eod.profile_read(i) for i, k in enumerate(KINDS)}
+        eod.eod_abe_debug_profile(0)
+        return kinds
+
+
+def _factor_fn(eod, A, w, k, prec, **kw):
+    def fn():
+        f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec, **kw)
+        out = (f.rank, f.rel_err)
+        f.close()
+        return out
+    return fn
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -210,132 +329,74 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = W.image_like()                          # same seeded matrix on every replica
-    A_np = w.A
-    A = torch.from_numpy(A_np).cuda()
-    A32 = torch.from_numpy(np.asfortranarray(A_np.astype(np.float32))).cuda()
+    peaks = _measured_peaks()
+    w = W.harmonic()                            # same seeded matrix on every replica
+    A32_np = w.A
+    m, n = A32_np.shape
+    A32 = torch.from_numpy(A32_np).cuda()
+    A64 = torch.from_numpy(np.asfortranarray(A32_np.astype(np.float64))).cuda()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
+    st = Stepper(eod, torch, dist, flush)
 
-    def step(Ain):
-        f = eod.factor(Ain, w.tol, w.seed, block_k=BLOCK_K, tol_mode="rel")
-        r, rel = f.rank, f.rel_err
-        f.close()
-        return r, rel
-
-    def timed(Ain, steps, warmup, profile=False):
-        for _ in range(warmup):
-            step(Ain)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        launches0 = eod.eod_abe_debug_launch_count()
-        if profile:
-            eod.eod_abe_debug_profile(1)
-        total_ms, info = 0.0, None
-        for _ in range(steps):
-            flush.zero_()                       # evict A from the 129 MB L2 between steps
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            info = step(Ain)
-            ev1.record(stream)
-            ev1.synchronize()
-            total_ms += ev0.elapsed_time(ev1)
-        torch.cuda.synchronize()
-        prof = eod.profile_read(eod.PROF_OZ_GEMM) if profile else None
-        kinds = {k: eod.profile_read(i) for i, k in enumerate(KINDS)} if profile else None
-        if profile:
-            eod.eod_abe_debug_profile(0)
-        launches = eod.eod_abe_debug_launch_count() - launches0
-        total_ms = _max_over_ranks(total_ms, dist, "cuda")
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        return total_ms, info, prof, kinds, launches
-
+    # ---- headline: mixed BF16, instrumentation off ----
     clocks = ClockSampler(local)
     clocks.start()
-    total_ms, (r, rel), prof, kinds, launches = timed(A, args.steps, args.warmup, profile=True)
+    t_mx, (r_mx, rel_mx), launches = st.run(_factor_fn(eod, A32, w, HEAD_K, "mixed"), args.steps, args.warmup)
     clk = clocks.stop()
-    flops = eod.model_flops(M, N, r, BLOCK_K, True)
-    value = ws * args.steps * flops / (total_ms / 1e3) / 1e9
-    ms_step = total_ms / args.steps
+    flops_mx = eod.model_flops(m, n, r_mx, HEAD_K, True)
+    value = ws * args.steps * flops_mx / (t_mx / 1e3) / 1e9
+    ms_step = t_mx / args.steps
 
-    # FP32-storage plain form on the same matrix (context)
-    t32, (r32, rel32), _, _, _ = timed(A32, max(2, args.steps // 2), 1)
-    v32 = ws * max(2, args.steps // 2) * eod.model_flops(M, N, r32, BLOCK_K, True) / (t32 / 1e3) / 1e9
+    # ---- plain FP64 on the same matrix (widened), same steps ----
+    t_64, (r_64, rel_64), _ = st.run(_factor_fn(eod, A64, w, HEAD_K, "plain"), args.steps, args.warmup)
+    ms_64 = t_64 / args.steps
+    gf_64 = ws * args.steps * eod.model_flops(m, n, r_64, HEAD_K, True) / (t_64 / 1e3) / 1e9
+    forms = {"mixed_bf16": {"gflops": value, "ms": ms_step, "rank": r_mx, "rel_err": rel_mx},
+             "plain_f64": {"gflops": gf_64, "ms": ms_64, "rank": r_64, "rel_err": rel_64}}
+    ctx_steps = max(2, args.steps // 2)
+    for name, A, prec in (("plain_f32", A32, "plain"), ("mixed_tf32", A32, "mixed_tf32")):
+        t, (r, rel), _ = st.run(_factor_fn(eod, A, w, HEAD_K, prec), ctx_steps, 1)
+        forms[name] = {"gflops": ws * ctx_steps * eod.model_flops(m, n, r, HEAD_K, True) / (t / 1e3) / 1e9,
+                       "ms": t / ctx_steps, "rank": r, "rel_err": rel}
+    for v in forms.values():
+        v["rank_equal_f64"] = v["rank"] == r_64
+        v["d_rel_err_vs_f64"] = abs(v["rel_err"] - rel_64)
+    mixed_vs_plain = {"speedup_mixed_bf16_over_plain_f64": ms_64 / ms_step,
+                      "rank_equal": r_mx == r_64, "d_rel_err": abs(rel_mx - rel_64),
+                      "parity_ok": (r_mx == r_64) and abs(rel_mx - rel_64) <= 1e-4}
 
-    # Alg. 2 with tau = 1, 2 subspace iterations on the same matrix (context;
-    # the cost model adds tau (2mnr + 2mr^2 + 2nr^2) multiply-adds, Sec. 3.4)
-    sub = {}
-    for tau in (1, 2):
-        def step_tau(Ain, tau=tau):
-            f = eod.factor(Ain, w.tol, w.seed, block_k=BLOCK_K, tol_mode="rel", power_iters=tau)
-            out = (f.rank, f.rel_err)
-            f.close()
-            return out
-        for _ in range(2):
-            step_tau(A)
-        torch.cuda.synchronize()
-        tt = 0.0
-        nst = max(2, args.steps // 2)
-        for _ in range(nst):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rt, relt = step_tau(A)
-            e1.record(stream)
-            e1.synchronize()
-            tt += e0.elapsed_time(e1)
-        mst = tt / nst
-        fl = eod.model_flops(M, N, rt, BLOCK_K, True) + 2.0 * tau * (2.0 * M * N * rt + 2.0 * M * rt * rt +
-                                                                     2.0 * N * rt * rt)
-        sub[f"tau{tau}"] = {"ms_per_step": mst, "gflops": fl / (mst / 1e3) / 1e9, "rank": rt, "rel_err": relt}
+    # ---- roofline: a separate profiled pass of the headline form ----
+    kinds = st.profile(_factor_fn(eod, A32, w, HEAD_K, "mixed"), 2)
+    prof_total = sum(v["ms"] for v in kinds.values())
+    dom = max(kinds, key=lambda k: kinds[k]["ms"])
+    roofline = roofline_of(dom, kinds[dom], peaks)
+    roofline["share_of_kernel_time"] = kinds[dom]["ms"] / prof_total if prof_total else None
+    kernel_share = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / 2,
+                        "share": (v["ms"] / prof_total if prof_total else None)} for k, v in kinds.items()}
+    roofline_tensor = roofline_of("tc_gemm", kinds["tc_gemm"], peaks) if kinds["tc_gemm"]["launches"] else None
 
-    # end to end through the host-buffer entry point
-    Ah = torch.from_numpy(A_np).pin_memory()
-    cap = min(M, N)
-    Uh = torch.empty((cap, M), dtype=torch.float64).pin_memory().t()
+    # ---- end to end through the host-buffer entry point (mixed) ----
+    Ah = torch.from_numpy(A32_np).pin_memory()
+    cap = min(m, n)
+    Uh = torch.empty((cap, m), dtype=torch.float32).pin_memory().t()
     Dh = torch.empty((cap, cap), dtype=torch.float64).pin_memory().t()
-    Vh = torch.empty((cap, N), dtype=torch.float64).pin_memory().t()
+    Vh = torch.empty((cap, n), dtype=torch.float32).pin_memory().t()
+
+    def e2e_step():
+        return eod.factor_host(Ah, w.tol, w.seed, block_k=HEAD_K, tol_mode="rel", precision="mixed",
+                               U_out=Uh, D_out=Dh, V_out=Vh)
     for _ in range(args.warmup):
-        eod.factor_host(Ah, w.tol, w.seed, block_k=BLOCK_K, tol_mode="rel", U_out=Uh, D_out=Dh, V_out=Vh)
+        e2e_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        re2e, _ = eod.factor_host(Ah, w.tol, w.seed, block_k=BLOCK_K, tol_mode="rel", U_out=Uh, D_out=Dh, V_out=Vh)
+        re2e, _ = e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = _max_over_ranks(e2e_s, dist, "cuda")
-    e2e_val = ws * args.steps * eod.model_flops(M, N, re2e, BLOCK_K, True) / e2e_s / 1e9
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_val = ws * args.steps * eod.model_flops(m, n, re2e, HEAD_K, True) / e2e_s / 1e9
 
-    # roofline of the dominant kernel: the FP64 GEMM emulated on tcgen05
-    bf16_peak, _, peak_src = _measured_peaks()
-    oz_peak = bf16_peak / OZ_PAIRS
-    achieved = prof["flops"] / (prof["ms"] / 1e3) / 1e9 if prof and prof["ms"] > 0 else None
-    tr = _traffic_for("oz_gemm", ["paper_2506_22713_gb300/csrc/oz_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"])
-    traffic = tr[0] if tr else None
-    per_launch = (prof["flops"] / prof["launches"]) if prof and prof["launches"] else None
-    roofline = {
-        "bound": "tensor",
-        "kernel": "oz_gemm (FP64 GEMM as 36 exact BF16 slice-pair products on tcgen05, FP64 accumulation)",
-        "achieved": achieved,
-        "peak": oz_peak,
-        "unit": "GFLOP/s",
-        "frac": (achieved / oz_peak) if achieved else None,
-        "peak_source": f"{peak_src} bf16 burst {bf16_peak:.0f} GFLOP/s (MEASURED_PEAKS.json) / {OZ_PAIRS} "
-                       "slice-pair products per FP64 multiply-add",
-        "achieved_bf16_equivalent": achieved * OZ_PAIRS if achieved else None,
-        "traffic": traffic,
-        "traffic_launch": tr[1] if tr else None,
-        "launches": prof["launches"] if prof else None,
-        "flops_per_launch": per_launch,
-        "share_of_step": (prof["ms"] / total_ms) if prof else None,
-        "fp64_simt_peak": FP64_PEAK_GFLOPS,
-    }
     out = {
         "metric": METRIC,
         "value": value,
@@ -347,31 +408,40 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
-        "data": "synthetic (seeded image-like low-rank + noise; no dataset)",
-        "config": {"workload": WORKLOAD + ", FP64 plain, k=64", "m": M, "n": N, "rank": r, "rel_err": rel,
-                   "parallelism": f"replicas x{ws}", "l2": "flushed between timed steps (256 MB write)"},
+        "dtype": "bf16",
+        "data": "synthetic (seeded harmonic low-rank + noise; no dataset)",
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "rank": r_mx, "rel_err": rel_mx, "block_k": HEAD_K,
+                   "form": "mixed BF16: sketch/projection/error on tcgen05 (BF16 split, FP32 accumulation); "
+                           "Gram/Cholesky/rank test/core in FP64",
+                   "parallelism": f"replicas x{ws}", "l2": "flushed between timed steps (258 MB write)",
+                   "instrumentation": "off in the timed steps; roofline from a separate profiled pass"},
+        "mixed_vs_plain": mixed_vs_plain,
+        "forms": forms,
         "roofline": roofline,
-        "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * M * N,
-                "d2h_bytes_per_step": 8 * (M * re2e + N * re2e + re2e * re2e)},
+        "roofline_tensor": roofline_tensor,
+        "kernel_share": kernel_share,
+        "e2e": {"value": e2e_val, "unit": "GFLOP/s", "h2d_bytes_per_step": 4 * m * n,
+                "d2h_bytes_per_step": 4 * (m * re2e + n * re2e) + 8 * re2e * re2e},
         "gpu_launches": int(launches),
-        "kernel_ms": {k: round(v["ms"], 3) for k, v in (kinds or {}).items()},
-        "forms": {"f32_plain": {"value": v32, "unit": "GFLOP/s", "rank": r32, "rel_err": rel32,
-                                "ms_per_step": t32 / max(2, args.steps // 2)}},
-        "subspace_iteration_f64": sub,
         "clocks": clk,
     }
+    del A64
+    torch.cuda.empty_cache()
     if not args.no_compare:
-        comp, troof = compare_forms(eod, 3, 1, flush)
-        out["mixed_vs_plain"] = comp
-        out["roofline_tensor"] = troof
+        out["workloads"] = compare_workloads(eod, st, max(2, args.steps // 2), 1)
         out["batched_mixed_vs_plain"] = compare_batched(eod, 1, 1)
+        out["subspace_iteration_f64"] = subspace_iterations(eod, st, max(2, args.steps // 2))
         out["paper_table_mat2_f64"] = paper_mat2(eod)
         out["robustness_matrices_f64"] = robustness_matrices(eod)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, sample, el = oracle_sample(A_np, w.tol * float(np.linalg.norm(A_np)), 15.0)
-        out["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
-                               "seconds": el}
+        A64_np = np.asfortranarray(A32_np.astype(np.float64))
+        v, el, r_o, cores = oracle_whole(A64_np, w.tol, HEAD_K, w.seed, 0)
+        out["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                               "sample": _oracle_sample_text(cores, r_o), "seconds": el,
+                               "rank": r_o, "rank_equal_gpu": r_o == r_mx}
+        if args.cpu_one_core:
+            v1, el1, _, _ = oracle_whole(A64_np, w.tol, HEAD_K, w.seed, 1)
+            out["cpu_baseline"]["one_core"] = {"value": v1, "seconds": el1, "cores": 1}
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -379,57 +449,31 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def compare_forms(eod, steps, warmup, flush):
-    """Mixed (BF16 split on tcgen05) against the plain FP64 path on the same
-    inputs: the image-like 2048^2 matrix, the 8192^2 harmonic matrix and the
-    262144 x 224 hyperspectral matrix.  Returns a list of result dicts and
-    the tensor-core kernel's roofline over the mixed runs."""
+def compare_workloads(eod, st, steps, warmup):
+    """The other single-matrix workloads in all four precision forms: the
+    image-like 2048^2 matrix (FP64 storage; its FP32 rounding for the FP32
+    forms) and the 262144 x 224 hyperspectral matrix."""
     import numpy as np
     import torch
     import workloads as W
 
-    bf16_peak, _, src = _measured_peaks()
-    out, tc_fl, tc_ms, tc_n = [], 0.0, 0.0, 0
-    cases = [("image-like 2048x2048 tol 1e-3 rel", lambda: W.image_like(), 64),
-             ("harmonic 8192x8192 rank-400 1/i + noise 1e-6, tol 0.0128 rel", lambda: W.harmonic(), 64),
-             ("hyperspectral 262144x224, 12 endmembers, 30 dB, tol 0.047 rel", lambda: W.hyperspectral(), 16)]
+    out = []
+    cases = [("image-like 2048x2048 rank-150 s_i=255 i^-1.5 + noise 1e-4 s_1, tol 1e-3 rel", W.image_like, 64),
+             ("hyperspectral 262144x224, 12 endmembers, 30 dB, tol 0.047 rel", W.hyperspectral, 16)]
     for name, make, k in cases:
         w = make()
         A64 = torch.from_numpy(np.asfortranarray(w.A.astype(np.float64))).cuda()
         A32 = torch.from_numpy(np.asfortranarray(w.A.astype(np.float32))).cuda()
-        del w.A
         m, n = A64.shape
         res = {}
         for form, A, prec in (("plain_f64", A64, "plain"), ("plain_f32", A32, "plain"), ("mixed_bf16", A32, "mixed"),
                               ("mixed_tf32", A32, "mixed_tf32")):
-            for _ in range(warmup):
-                f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
-                f.close()
-            torch.cuda.synchronize()
-            if prec == "mixed":
-                eod.eod_abe_debug_profile(1)
-            tot = 0.0
-            for _ in range(steps):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
-                e1.record()
-                e1.synchronize()
-                tot += e0.elapsed_time(e1)
-                r, rel = f.rank, f.rel_err
-                f.close()
-            if prec == "mixed":
-                pr = eod.profile_read(eod.PROF_TC_GEMM)
-                eod.eod_abe_debug_profile(0)
-                tc_fl += pr["flops"]
-                tc_ms += pr["ms"]
-                tc_n += pr["launches"]
-            ms = tot / steps
+            t, (r, rel), _ = st.run(_factor_fn(eod, A, w, k, prec), steps, warmup)
+            ms = t / steps
             res[form] = {"gflops": eod.model_flops(m, n, r, k, True) / (ms / 1e3) / 1e9, "ms": ms, "rank": r,
                          "rel_err": rel}
         base = res["plain_f64"]
-        for form, v in res.items():
+        for v in res.values():
             v["rank_equal_f64"] = v["rank"] == base["rank"]
             v["d_rel_err_vs_f64"] = abs(v["rel_err"] - base["rel_err"])
         out.append({"workload": name, "m": m, "n": n, "k": k, "forms": res,
@@ -437,12 +481,26 @@ def compare_forms(eod, steps, warmup, flush):
                     "mixed_tf32_speedup_vs_f64": base["ms"] / res["mixed_tf32"]["ms"]})
         del A64, A32
         torch.cuda.empty_cache()
-    ach = tc_fl / (tc_ms / 1e3) / 1e9 if tc_ms > 0 else None
-    roof = {"bound": "tensor", "kernel": "tc_gemm (tcgen05 kind::f16, BF16 split pairs)", "achieved": ach,
-            "peak": bf16_peak, "unit": "GFLOP/s", "frac": (ach / bf16_peak) if ach else None,
-            "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)", "launches": tc_n,
-            "flops_per_launch": tc_fl / tc_n if tc_n else None, "traffic": None}
-    return out, roof
+    return out
+
+
+def subspace_iterations(eod, st, steps):
+    """Alg. 2 with tau = 1, 2 subspace iterations on the image-like 2048^2
+    FP64 matrix (the cost model adds tau (2mnr + 2mr^2 + 2nr^2) multiply-adds,
+    Sec. 3.4)."""
+    import torch
+    import workloads as W
+
+    w = W.image_like()
+    A = torch.from_numpy(w.A).cuda()
+    m, n = w.A.shape
+    out = {}
+    for tau in (0, 1, 2):
+        t, (r, rel), _ = st.run(_factor_fn(eod, A, w, 64, "plain", power_iters=tau), steps, 2)
+        ms = t / steps
+        fl = eod.model_flops(m, n, r, 64, True) + 2.0 * tau * (2.0 * m * n * r + 2.0 * m * r * r + 2.0 * n * r * r)
+        out[f"tau{tau}"] = {"ms_per_step": ms, "gflops": fl / (ms / 1e3) / 1e9, "rank": r, "rel_err": rel}
+    return out
 
 
 # Alg. 2 on the paper's strictly rank-deficient test matrix (Sec. 4, Eq.
@@ -456,7 +514,9 @@ def paper_mat2(eod, sizes=(4000, 8000, 12000)):
     """One timed factorisation (after one warm-up) per size and tau, plain
     FP64, k = 64, eps = 1e-8 absolute (between sigma_r ~ 1e-4 and the
     rounding floor ~ 1e-12).  The matrices are drawn on the GPU with torch's
-    generator (seeded): at these sizes the host would take minutes."""
+    generator (seeded) from the recipe of workloads.mat2: at these sizes the
+    host would take minutes (the oracle-parity tests use the numpy generator
+    at n = 1000 and 4000)."""
     import torch
 
     out = []
@@ -572,22 +632,24 @@ def compare_batched(eod, steps, warmup):
 
 # ---------------------------------------------------------- reference arm --
 def run_reference(args):
+    """The FP64 oracle as the reference arm: each step is its whole method on
+    the headline matrix, on every host core; GFLOP/s of the same cost model."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import numpy as np
     import workloads as W
-    w = W.image_like()
-    A_np = w.A
-    eps = w.tol * float(np.linalg.norm(A_np))
+    w = W.harmonic()
+    A64 = np.asfortranarray(w.A.astype(np.float64))
+    m, n = A64.shape
     for _ in range(args.warmup):
-        oracle_sample(A_np, eps, 4.0)
-    vals, secs, sample = [], 0.0, ""
+        oracle_whole(A64, w.tol, HEAD_K, w.seed, 0)
+    secs, flops, r, cores = 0.0, 0.0, 0, 1
     for _ in range(args.steps):
-        v, sample, el = oracle_sample(A_np, eps, 6.0)
-        vals.append(v)
+        v, el, r, cores = oracle_whole(A64, w.tol, HEAD_K, w.seed, 0)
         secs += el
-    value = statistics.mean(vals)
+        flops += v * el * 1e9
+    value = flops / secs / 1e9
     out = {
         "impl": "reference",
         "metric": METRIC,
@@ -601,9 +663,11 @@ def run_reference(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded image-like low-rank + noise; no dataset)",
-        "config": {"workload": WORKLOAD + ", FP64 plain, k=64", "m": M, "n": N, "parallelism": "host, 1 thread"},
-        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic (seeded harmonic low-rank + noise; no dataset)",
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "rank": r, "block_k": HEAD_K,
+                   "parallelism": f"host, {cores} threads"},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": _oracle_sample_text(cores, r)},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))

@@ -305,6 +305,16 @@ EOD_API eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w, i
                                       double delta_coef, double rho, double shift, double *R, double *Rinv,
                                       int64_t ldr, int32_t *info, void *stream);
 
+/* Test hook (no counterpart in the paper): the reciprocal the leaf
+ * factorisation (eod_abe_debug_chol, Alg. 1 steps 5-11) takes of each pivot,
+ * applied to n device doubles d (out[i] = 1/d[i], FP64, device memory):
+ * seeded by an FP32 reciprocal of the mantissa and refined by one
+ * third-order step, within 2 ulp of 1/d for normal d whose reciprocal is
+ * normal; +inf for subnormal d and 0 for d above about 2^1022 (deliberate:
+ * the leaf only sees Gram pivots).  Returns after synchronising `stream`;
+ * EOD_EINVAL for NULL pointers or n < 1. */
+EOD_API eod_status eod_abe_debug_recip(const double *d, double *out, int64_t n, void *stream);
+
 /* Test hook (no counterpart in the paper): one FP64 GEMM C = alpha op(A)
  * op(B) + beta C on device matrices, column-major, op(X) = X^T when the
  * matching flag is nonzero; mode & 3 == 0 runs the SIMT DFMA kernel, 1 the

@@ -107,9 +107,9 @@ def _load():
 
 
 def set_threads(n: int) -> int:
-    """Threads for the oracle's column loops (n <= 0: every core); returns
-    the count in effect (1 when built without OpenMP).  Results do not
-    depend on it."""
+    """Threads for the oracle's column loops (n <= 0: the OpenMP default,
+    OMP_NUM_THREADS or every core); returns the count in effect (1 when built
+    without OpenMP).  Results do not depend on it."""
     return int(_load().orc_set_threads(int(n)))
 
 

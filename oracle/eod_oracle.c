@@ -48,14 +48,15 @@
 #define IX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
 
 /* Threads used by the column loops below (1 without OpenMP), one setting
- * for the whole process whichever thread calls in.  n <= 0 selects every
- * available core.  Returns the count now in effect. */
+ * for the whole process whichever thread calls in.  n <= 0 selects the
+ * OpenMP default (OMP_NUM_THREADS if set, else every core).  Returns the
+ * count now in effect. */
 static int g_threads = 0;
 
 int orc_get_threads(void)
 {
 #ifdef _OPENMP
-    return g_threads > 0 ? g_threads : omp_get_num_procs();
+    return g_threads > 0 ? g_threads : omp_get_max_threads();
 #else
     return 1;
 #endif

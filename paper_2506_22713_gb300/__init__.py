@@ -34,6 +34,7 @@ EXPORTED = [
     "eod_abe_debug_fail_alloc_after", "eod_abe_version", "eod_abe_debug_profile",
     "eod_abe_debug_profile_read", "eod_abe_debug_launch_count", "eod_abe_fro_norm_noalloc",
     "eod_abe_debug_tc_gemm", "eod_abe_debug_f64_gemm", "eod_abe_debug_chol", "eod_abe_debug_bounded_wait",
+    "eod_abe_debug_recip",
 ]
 
 
@@ -117,6 +118,8 @@ def _load() -> ctypes.CDLL:
     lib.eod_abe_debug_tc_gemm.restype = I32
     lib.eod_abe_debug_bounded_wait.argtypes = [I64, I32, P]
     lib.eod_abe_debug_bounded_wait.restype = I32
+    lib.eod_abe_debug_recip.argtypes = [P, P, I64, P]
+    lib.eod_abe_debug_recip.restype = I32
     lib.eod_abe_debug_f64_gemm.argtypes = [I32, I32, I32, I64, I64, I64, F64, P, I64, P, I64, F64, P, I64, P]
     lib.eod_abe_debug_f64_gemm.restype = I32
     lib.eod_abe_debug_chol.argtypes = [P, I64, I32, I32, F64, F64, F64, F64, P, P, I64, P, P]
@@ -148,6 +151,7 @@ eod_abe_debug_launch_count = _lib.eod_abe_debug_launch_count
 eod_abe_fro_norm_noalloc = _lib.eod_abe_fro_norm_noalloc
 eod_abe_debug_tc_gemm = _lib.eod_abe_debug_tc_gemm
 eod_abe_debug_bounded_wait = _lib.eod_abe_debug_bounded_wait
+eod_abe_debug_recip = _lib.eod_abe_debug_recip
 eod_abe_debug_f64_gemm = _lib.eod_abe_debug_f64_gemm
 eod_abe_debug_chol = _lib.eod_abe_debug_chol
 

@@ -645,7 +645,14 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
         p.ldc = ldc;
         p.split_stride = 0;
     }
-    ProfScope prof(PROF_OZ_GEMM, 2.0 * M * N * K, 2.0 * NS * ((double)M * K + (double)K * N) + 8.0 * 2 * M * N, s);
+    // the method's flops: an upper-only output or a triangular operand halves
+    // the multiply-adds (both triangular: a sixth), as the kernel skips them
+    double frac = 1.0;
+    if (x.upper_only) frac *= 0.5;
+    if (x.a_upper && x.b_upper) frac /= 6.0;
+    else if (x.a_upper || x.b_upper) frac *= 0.5;
+    ProfScope prof(PROF_OZ_GEMM, 2.0 * M * N * K * frac,
+                   2.0 * NS * ((double)M * K + (double)K * N) + 8.0 * 2 * M * N, s);
     if (e == cudaSuccess) {
         dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
         count_launch();

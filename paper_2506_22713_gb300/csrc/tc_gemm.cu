@@ -482,7 +482,9 @@ cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s) {
         if (!part) splits = 1;
     }
     p.kblocks_per_split = (p.kblocks + splits - 1) / splits;
-    const double flops = 2.0 * g.M * g.N * g.K * g.npairs;
+    // the method's flops: one product (the split's extra pairs are the
+    // implementation's overhead, not counted)
+    const double flops = 2.0 * g.M * g.N * g.K;
     const double bytes = (g.tf32 ? 4.0 : 2.0) * g.npairs * ((double)g.M * g.K + (double)g.K * g.N) +
                          (g.epilogue == EPI_ERR ? 4.0 * g.M * g.N : 4.0 * g.M * g.N);
     ProfScope prof(PROF_TC_GEMM, flops, bytes, s);

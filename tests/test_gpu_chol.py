@@ -111,3 +111,36 @@ def test_stopped_factorisation_keeps_its_inverse(eod):
     assert np.linalg.norm(R.T @ R - Gp) <= 20 * 40 * U64 * np.linalg.norm(Gp)
     assert np.allclose(np.tril(Ri, -1), 0.0)
     assert np.linalg.norm(Ri @ R - np.eye(40)) <= 1e-12
+
+
+def test_leaf_reciprocal_against_cuda_division(eod):
+    """The leaf's pivot reciprocal (FP32 seed, one third-order step) against
+    CUDA's correctly rounded FP64 division, over the whole exponent range
+    whose reciprocals are normal: within 2 ulp everywhere, and its two
+    deliberate edge returns (+inf for subnormal d, 0 where 1/d would be
+    subnormal)."""
+    rng = np.random.default_rng(17)
+    mant = rng.uniform(1.0, 2.0, 200_000)
+    expo = rng.integers(-1021, 1022, 200_000)
+    d = np.ldexp(mant, expo)
+    d = np.concatenate([d, [1.0, 2.0, 0.5, 1.5, np.nextafter(2.0, 0.0), 2.0 ** -1022, 2.0 ** 1021, 3.0, 7.0]])
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty_like(dd)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert eod.eod_abe_debug_recip(P(dd), P(out), dd.numel(), s) == eod.EOD_OK
+    ref = (1.0 / dd).cpu().numpy()
+    got = out.cpu().numpy()
+    ulps = np.abs(got - ref) / np.spacing(ref)
+    assert np.all(np.isfinite(got))
+    assert ulps.max() <= 2.0, ulps.max()
+    # edges: subnormal (and zero) pivots give +inf; reciprocals below the
+    # normal range give 0
+    edge = torch.tensor([5e-324, 2.0 ** -1030, 0.0, 2.0 ** 1023 * 1.5, 2.0 ** 1022 * 1.75],
+                        dtype=torch.float64, device="cuda")
+    eo = torch.empty_like(edge)
+    assert eod.eod_abe_debug_recip(P(edge), P(eo), edge.numel(), s) == eod.EOD_OK
+    e = eo.cpu().numpy()
+    assert np.isinf(e[0]) and e[0] > 0 and np.isinf(e[1]) and np.isinf(e[2])
+    assert e[3] == 0.0 and e[4] == 0.0
+    assert eod.eod_abe_debug_recip(None, P(eo), 1, s) == eod.EOD_EINVAL
