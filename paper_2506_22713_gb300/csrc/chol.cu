@@ -133,9 +133,40 @@ __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *
                                                                   int decide, double eps2, double delta_coef,
                                                                   double rho, double shift, double *__restrict__ R,
                                                                   int64_t ldr, double *__restrict__ Rinv,
-                                                                  int64_t ldinv, int *info) {
+                                                                  int64_t ldinv, int *info, double ni_tau2) {
     constexpr int NT = kLeafThreads;
     extern __shared__ double sh[];
+    // Near-identity Gram (the second pass of CholQR2, G = P^T P = I + E with
+    // P already orthonormal to first order): when ||E||_F^2 <= ni_tau2,
+    // R = I + Phi(E) and R^{-1} = I - Phi(E) (Phi = the strict upper part
+    // and half the diagonal), exact up to O(||E||^2): (I + Phi(E))^T
+    // (I + Phi(E)) = I + E + Phi(E)^T Phi(E).
+    if (ni_tau2 > 0.0) {
+        __shared__ double red[32];
+        double acc = 0.0;
+        for (int e = threadIdx.x; e < w * w; e += NT) {
+            const int i = e % w, c = e / w;
+            if (i <= c) {
+                const double v = G[i + (int64_t)c * ldg] - (i == c ? 1.0 : 0.0);
+                acc += (i == c ? 1.0 : 2.0) * v * v;
+            }
+        }
+        const double tot = block_sum(acc, red);
+        if (tot <= ni_tau2) {
+            for (int e = threadIdx.x; e < w * w; e += NT) {
+                const int i = e % w, c = e / w;
+                const double g = (i <= c) ? G[i + (int64_t)c * ldg] : 0.0;
+                const double x = (i < c) ? g : (i == c ? 0.5 * (g - 1.0) : 0.0);
+                R[i + (int64_t)c * ldr] = (i == c ? 1.0 : 0.0) + x;
+                if (Rinv) Rinv[i + (int64_t)c * ldinv] = (i == c ? 1.0 : 0.0) - x;
+            }
+            if (threadIdx.x == 0) {
+                info[0] = w;
+                info[1] = CHOL_ALL;
+            }
+            return;
+        }
+    }
     const int ld = w + 1;
     double *S = sh;                                    // w x ld
     double *mcol = S + w * ld;                         // M = -L(:, j) of the current step
@@ -281,6 +312,38 @@ __global__ void tdiag_kernel(const double *R1, const double *R2, int64_t ldr, co
         tdiag[j] = fabs(R1[j + j * ldr] * R2[j + j * ldr]);
 }
 
+// ||G - I||_F^2 of a symmetric p x p matrix from its upper triangle.
+__global__ void offidentity_kernel(const double *G, int64_t ldg, int64_t p, double *out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int64_t i = e % p, c = e / p;
+        if (i <= c) {
+            const double v = G[i + c * ldg] - (i == c ? 1.0 : 0.0);
+            acc += (i == c ? 1.0 : 2.0) * v * v;
+        }
+    }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) out[0] = tot;
+}
+
+// R = I + Phi(G - I) (p x p, upper, zeros below) and, for every diagonal
+// panel J of width pb, R_JJ^{-1} = I - Phi(G_JJ - I) at RiD + J pb^2 (ld pb):
+// the first-order Cholesky factor of a near-identity Gram and its inverse.
+__global__ void near_identity_kernel(const double *G, int64_t ldg, int64_t p, double *R, int64_t ldr, double *RiD,
+                                     int pb) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < p * p; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % p, c = e / p;
+        const double g = (i <= c) ? G[i + c * ldg] : 0.0;
+        const double x = (i < c) ? g : (i == c ? 0.5 * (g - 1.0) : 0.0);
+        R[i + c * ldr] = (i == c ? 1.0 : 0.0) + x;
+        if (i / pb == c / pb) {
+            const int64_t J = i / pb, ii = i - J * pb, cc = c - J * pb;
+            RiD[J * (int64_t)pb * pb + ii + cc * pb] = (i == c ? 1.0 : 0.0) - x;
+        }
+    }
+}
+
 __global__ void trace_kernel(const double *G, int64_t ldg, int64_t p, double *out) {
     __shared__ double red[32];
     double acc = 0.0;
@@ -293,13 +356,29 @@ __global__ void trace_kernel(const double *G, int64_t ldg, int64_t p, double *ou
 
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2, double delta_coef,
                        double rho, double shift, double *R, int64_t ldr, double *Rinv, int64_t ldinv, int *info,
-                       cudaStream_t s) {
+                       cudaStream_t s, double ni_tau2) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
+    if (decide || shift != 0.0) ni_tau2 = 0.0;
     EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)leaf_smem_bytes(128)));
     ProfScope prof(PROF_CHOL, (double)w * w * w * (Rinv ? 2.0 : 1.0) / 3.0, sizeof(double) * 3.0 * w * w, s);
     count_launch();
     chol_small_kernel<<<1, kLeafThreads, leaf_smem_bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R,
-                                                                  ldr, Rinv, ldinv, info);
+                                                                  ldr, Rinv, ldinv, info, ni_tau2);
+    return cudaGetLastError();
+}
+
+cudaError_t offidentity_sumsq(const double *G, int64_t ldg, int64_t p, double *out, cudaStream_t s) {
+    count_launch();
+    offidentity_kernel<<<1, 1024, 0, s>>>(G, ldg, p, out);
+    return cudaGetLastError();
+}
+
+cudaError_t near_identity_factor(const double *G, int64_t ldg, int64_t p, double *R, int64_t ldr, double *RiD,
+                                 int pb, cudaStream_t s) {
+    count_launch();
+    const int64_t tot = p * p;
+    near_identity_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(G, ldg, p, R, ldr, RiD,
+                                                                                                pb);
     return cudaGetLastError();
 }
 

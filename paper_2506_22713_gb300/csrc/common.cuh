@@ -251,9 +251,20 @@ enum CholCode { CHOL_ALL = 0, CHOL_BELOW = 1, CHOL_UNCERTAIN = 2, CHOL_FAIL = 3 
 //   info[0] = p (leading columns factored), info[1] = CholCode,
 // R (p x p upper, ld ldr) and its inverse Rinv (ld ldr); the original
 // diagonal of G is used for the rounding margin.
+// ni_tau2 > 0 (only with decide == 0 and shift == 0): when ||G - I||_F^2 <=
+// ni_tau2 the factor is taken to first order, R = I + Phi(G - I), R^{-1} =
+// I - Phi(G - I) (Phi: strict upper part plus half the diagonal; error
+// O(||G - I||^2)), without the factorisation.
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2,
                        double delta_coef, double rho, double shift, double *R, int64_t ldr,
-                       double *Rinv, int64_t ldinv, int *info, cudaStream_t s);
+                       double *Rinv, int64_t ldinv, int *info, cudaStream_t s, double ni_tau2 = 0.0);
+// out[0] = ||G - I||_F^2 of the symmetric p x p matrix G (upper triangle read)
+cudaError_t offidentity_sumsq(const double *G, int64_t ldg, int64_t p, double *out, cudaStream_t s);
+// the first-order factor of a near-identity G (see chol_small): R (p x p,
+// ld ldr, zeros below the diagonal) and the inverses of its diagonal panels
+// of width pb at RiD + J pb^2 (ld pb)
+cudaError_t near_identity_factor(const double *G, int64_t ldg, int64_t p, double *R, int64_t ldr, double *RiD,
+                                 int pb, cudaStream_t s);
 // tdiag[j] = |R1(j,j) * R2(j,j)|, j < p
 cudaError_t tdiag_product(const double *R1, const double *R2, int64_t ldr, const int *p_dev,
                           double *tdiag, cudaStream_t s);

@@ -72,6 +72,11 @@ inline int64_t round_up8(int64_t x) { return (x + 7) / 8 * 8; }
 // largest tau (subspace iterations of Alg. 2) accepted
 constexpr int kMaxPowerIters = 16;
 
+// Second CholQR pass on a near-identity Gram I + E: with ||E||_F <= 1e-8 the
+// first-order factor I + Phi(E) is exact to O(||E||^2) <= 1e-16 and replaces
+// the factorisation (see chol_small).
+constexpr double kNearIdTau2 = 1e-16;
+
 // smallest eps / ||A||_F the FP32-data paths accept (see factor_impl)
 constexpr double kMixedFloor = 1e-5;
 constexpr double kF32Floor = 1e-5;
@@ -255,7 +260,16 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
     for (int pass = 0; pass < passes; ++pass) {
         EOD_TRY(gram_full(W, rows, p, ldw, w.G, sym, ws, s));
         double *Rpass = (pass == 0) ? Rout : w.Rp;  // pass factor storage
-        eod_status st = chol_panels(w, p, shift, hm, ws, s, Rpass);
+        eod_status st = EOD_OK;
+        bool near_id = false;
+        if (pass > 0 && shift == 0.0) {
+            EOD_CU(offidentity_sumsq(w.G, p, p, w.trace, s));
+            EOD_CU(cudaMemcpyAsync(hm.val, w.trace, sizeof(double), cudaMemcpyDeviceToHost, s));
+            EOD_CU(cudaStreamSynchronize(s));
+            near_id = hm.val[0] <= kNearIdTau2;
+        }
+        if (near_id) EOD_CU(near_identity_factor(w.G, p, p, Rpass, p, w.RiD, kPB, s));
+        else st = chol_panels(w, p, shift, hm, ws, s, Rpass);
         if (st == EOD_EPRECISION && pass == 0 && shift == 0.0) {
             // shifted CholQR: shift = 11 (rows p + p (p+1)) u ||W||_2^2, ||W||_2^2 <= trace(G)
             EOD_CU(trace_sum(w.G, p, p, w.trace, s));
@@ -281,6 +295,56 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
         }
     }
     return EOD_OK;
+}
+
+// A non-blocking stream of the calling thread on the current device, for
+// work that overlaps the main stream of a factorisation (created once per
+// thread and device, kept for the life of the process).
+static cudaStream_t side_stream() {
+    thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams[dev] = nullptr;
+    }
+    return streams[dev];
+}
+
+// Makes `main` wait for everything queued on `side` so far, when it goes out
+// of scope (on every return path): the buffers both streams use are freed on
+// `main` afterwards.
+struct JoinOnExit {
+    cudaStream_t main = nullptr, side = nullptr;
+    ~JoinOnExit() { join(); }
+    void join() {
+        if (!side || side == main) return;
+        cudaEvent_t ev = nullptr;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            if (cudaEventRecord(ev, side) != cudaSuccess || cudaStreamWaitEvent(main, ev, 0) != cudaSuccess)
+                cudaStreamSynchronize(side);
+            cudaEventDestroy(ev);
+        } else {
+            cudaStreamSynchronize(side);
+        }
+        cudaGetLastError();
+        side = nullptr;
+    }
+};
+
+// `to` waits for the work queued on `from` so far.
+static cudaError_t stream_after(cudaStream_t to, cudaStream_t from) {
+    if (to == from) return cudaSuccess;
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    cudaEventDestroy(ev);
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -479,7 +543,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 }
                 EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, Yc, m, Ri, k, 0.0, T1, m, bup, &ws, s)));
                 EOD_CU(gram_skinny<T>(T1, m, p, m, G, k, &ws, s));
-                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, k, R2i, k, info, s));
+                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, k, R2i, k, info, s, kNearIdTau2));
                 const T *Ri2 = (const T *)R2i;
                 if (!std::is_same<T, double>::value) {
                     EOD_CU((copy_matrix<double, T>(R2i, k, RinvT, k, p, p, false, s)));
@@ -628,35 +692,50 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     }
 
     // ---- reconstruction error: || A - Q C ||_F / ||A||_F ----
+    // It needs only Q and C, so it runs on a side stream while the core
+    // (steps 9-11, a chain of small FP64 factorisations) runs on `s`.
+    JoinOnExit join;
     if (o.compute_err) {
         Phase ph("eod.reconstruction_error");
+        cudaStream_t se = side_stream();
+        if (!se) se = s;
+        join.main = s;
         if (mixed) {
-            EOD_TRY(mx.recon_error(Qb, r, Ct, d_norm, d_err, s));
+            join.side = se;
+            EOD_TRY(mx.recon_error(Qb, r, Ct, d_norm, d_err, s, se));
         } else {
             const int64_t nct = gemm_err_ctas(m, n);
             double *part;
             EOD_TRY(ar.get(&part, (size_t)nct));
-            EOD_CU(cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nct, s));
+            const bool emulated = oz.on && fp64_use_emulated(m, n, r) && r <= kOzErrMaxK;
+            uint16_t *cts = nullptr;
+            int *ects = nullptr;
+            const int64_t r8 = round_up8(r);
+            if (emulated) {
+                EOD_TRY(ar.get(&cts, (size_t)kOzSlices * n * r8));
+                EOD_TRY(ar.get(&ects, (size_t)n));
+            }
+            // the SIMT path takes split-K partials from the shared workspace:
+            // only the emulated product (no workspace use) leaves `s`
+            if (!emulated) se = s;
+            join.side = se;
+            EOD_CU(stream_after(se, s));
+            EOD_CU(cudaMemsetAsync(part, 0, sizeof(double) * (size_t)nct, se));
             GemmExtra ee;
             ee.epilogue = EPI_ERR;
             ee.ref = A;
             ee.ldref = lda;
             ee.err_partials = part;
-            if (oz.on && fp64_use_emulated(m, n, r) && r <= kOzErrMaxK) {
+            if (emulated) {
                 // B operand (C^T)^T: rows = rows of C^T (n), K = r
-                const int64_t r8 = round_up8(r);
-                uint16_t *cts;
-                int *ects;
-                EOD_TRY(ar.get(&cts, (size_t)kOzSlices * n * r8));
-                EOD_TRY(ar.get(&ects, (size_t)n));
-                EOD_CU(oz_slice((const double *)Ct, n, r, 1, n, cts, ects, 0, r8, n * r8, s));
+                EOD_CU(oz_slice((const double *)Ct, n, r, 1, n, cts, ects, 0, r8, n * r8, se));
                 const OzOperand qr{oz.Qr, nullptr, 1, oz.cap8, m * oz.cap8};
                 const OzOperand cto{cts, ects, 0, r8, n * r8};
-                EOD_CU(oz_gemm_ops(qr, cto, m, n, r, 1.0, 0.0, nullptr, m, ee, ws.err_flag, s));
+                EOD_CU(oz_gemm_ops(qr, cto, m, n, r, 1.0, 0.0, nullptr, m, ee, ws.err_flag, se));
             } else {
-                EOD_CU((gemm<T, T, T, T>(false, true, m, n, r, 1.0, Qb, m, Ct, n, 0.0, (T *)nullptr, m, ee, &ws, s)));
+                EOD_CU((gemm<T, T, T, T>(false, true, m, n, r, 1.0, Qb, m, Ct, n, 0.0, (T *)nullptr, m, ee, &ws, se)));
             }
-            EOD_CU(finalize_sqrt_sum(part, nct, d_norm, d_err, s));
+            EOD_CU(finalize_sqrt_sum(part, nct, d_norm, d_err, se));
         }
     }
 
@@ -680,6 +759,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
         EOD_CU((gemm<T, T, T, T>(false, false, m, r, r, 1.0, Qb, m, Rt, r, 0.0, U, m, ex, &ws, s)));
     }
 
+    join.join();
     if (o.compute_err) {
         EOD_CU(cudaMemcpyAsync(hm.val, d_err, sizeof(double), cudaMemcpyDeviceToHost, s));
     }

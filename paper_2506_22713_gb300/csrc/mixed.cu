@@ -171,7 +171,7 @@ eod_status MixedOps<float>::project(const float *Q, int64_t r, float *Ct, cudaSt
 }
 
 eod_status MixedOps<float>::recon_error(const float *Q, int64_t r, const float *Ct, const double *d_norm,
-                                        double *d_err, cudaStream_t s) {
+                                        double *d_err, cudaStream_t s, cudaStream_t run) {
     const int64_t r8 = round_up(r, 8);
     void *Qth, *Qtl, *Chh, *Chl;
     const size_t es = tf32 ? sizeof(float) : sizeof(__nv_bfloat16);
@@ -179,6 +179,19 @@ eod_status MixedOps<float>::recon_error(const float *Q, int64_t r, const float *
     MX_ST(ar->get((char **)&Qtl, es * (size_t)r8 * m));
     MX_ST(ar->get((char **)&Chh, es * (size_t)r8 * n));
     MX_ST(ar->get((char **)&Chl, es * (size_t)r8 * n));
+    const int64_t nct = tc_gemm_err_ctas(m, n, 256);
+    double *part;
+    MX_ST(ar->get(&part, (size_t)nct));
+    // the buffers come from `s`'s stream-ordered pool: `run` starts after them
+    if (run != s) {
+        cudaEvent_t ev = nullptr;
+        MX_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(run, ev, 0);
+        cudaEventDestroy(ev);
+        MX_TRY(e);
+        s = run;
+    }
     if (tf32) {
         MX_TRY(split_transpose_tf32(Q, m, r, m, (float *)Qth, (float *)Qtl, r8, s));    // (r x m)
         MX_TRY(split_transpose_tf32(Ct, n, r, n, (float *)Chh, (float *)Chl, r8, s));   // C = (C^T)^T, r x n
@@ -201,9 +214,6 @@ eod_status MixedOps<float>::recon_error(const float *Q, int64_t r, const float *
     g.bn = 256;
     g.ref = A;
     g.ldref = lda;
-    const int64_t nct = tc_gemm_err_ctas(m, n, g.bn);
-    double *part;
-    MX_ST(ar->get(&part, (size_t)nct));
     g.err_partials = part;
     g.err_flag = err_flag;
     MX_TRY(tc_gemm_run(g, ws, s));

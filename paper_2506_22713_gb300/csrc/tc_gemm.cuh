@@ -70,7 +70,7 @@ struct MixedOps {
     }
     eod_status sketch(int64_t, int64_t, uint64_t, uint64_t, T *, int64_t, cudaStream_t) { return EOD_EUNSUPPORTED; }
     eod_status project(const T *, int64_t, T *, cudaStream_t) { return EOD_EUNSUPPORTED; }
-    eod_status recon_error(const T *, int64_t, const T *, const double *, double *, cudaStream_t) {
+    eod_status recon_error(const T *, int64_t, const T *, const double *, double *, cudaStream_t, cudaStream_t) {
         return EOD_EUNSUPPORTED;
     }
     eod_status check(cudaStream_t) { return EOD_OK; }
@@ -98,8 +98,10 @@ struct MixedOps<float> {
                        cudaStream_t s, bool tf32);
     eod_status sketch(int64_t col0, int64_t f, uint64_t seed, uint64_t batch, float *Y, int64_t ldy, cudaStream_t s);
     eod_status project(const float *Q, int64_t r, float *Ct, cudaStream_t s);
+    // buffers from the arena on `s`; the kernels run on `run` (which may be
+    // `s`), ordered after those allocations
     eod_status recon_error(const float *Q, int64_t r, const float *Ct, const double *d_norm, double *d_err,
-                           cudaStream_t s);
+                           cudaStream_t s, cudaStream_t run);
     eod_status check(cudaStream_t s);   // EOD_ETIMEOUT if a bounded device wait ran out
 };
 
