@@ -140,7 +140,8 @@ def test_image_like_2048_fp32_storage_vs_oracle(eod, form):
     ref = _oracle(A32.astype(np.float64), w.tol, 64, w.seed)
     A = _to_dev(A32, np.float32)
     f = eod.factor(A, w.tol, w.seed, block_k=64, tol_mode="rel", precision=form.replace("plain_f32", "plain"))
-    compare(f, ref, _to_dev(A32, np.float64), form, f"image2048 {form}", signal=40)
+    # the TF32 form's looser bound leaves fewer columns determined well enough
+    compare(f, ref, _to_dev(A32, np.float64), form, f"image2048 {form}", signal=10 if form == "mixed_tf32" else 40)
     f.close()
 
 
@@ -162,7 +163,7 @@ def test_harmonic_8192_vs_oracle(eod, harmonic_case, form):
     else:
         A = _to_dev(w.A, np.float32)
         f = eod.factor(A, w.tol, w.seed, block_k=64, tol_mode="rel", precision=form.replace("plain_f32", "plain"))
-    compare(f, ref, Ad64, form, f"harmonic8192 {form}", signal=40)
+    compare(f, ref, Ad64, form, f"harmonic8192 {form}", signal=10 if form == "mixed_tf32" else 40)
     f.close()
 
 
