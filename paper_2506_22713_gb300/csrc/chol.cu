@@ -313,14 +313,16 @@ __global__ void tdiag_kernel(const double *R1, const double *R2, int64_t ldr, co
 }
 
 // ||G - I||_F^2 of a symmetric p x p matrix from its upper triangle.
+// One warp per column, lanes down the column (coalesced, no index division).
 __global__ void offidentity_kernel(const double *G, int64_t ldg, int64_t p, double *out) {
     __shared__ double red[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     double acc = 0.0;
-    for (int64_t e = threadIdx.x; e < p * p; e += blockDim.x) {
-        const int64_t i = e % p, c = e / p;
-        if (i <= c) {
-            const double v = G[i + c * ldg] - (i == c ? 1.0 : 0.0);
-            acc += (i == c ? 1.0 : 2.0) * v * v;
+    for (int64_t c = warp; c < p; c += nw) {
+        const double *col = G + c * ldg;
+        for (int64_t i = lane; i <= c; i += 32) {
+            const double v = col[i] - (i == c ? 1.0 : 0.0);
+            acc = fma(i == c ? v : 2.0 * v, v, acc);
         }
     }
     const double tot = block_sum(acc, red);

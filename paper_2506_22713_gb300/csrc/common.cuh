@@ -192,7 +192,13 @@ struct OzOperand {
     int64_t ldk = 0, slice_stride = 0;
 };
 cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64_t N, int64_t K, double alpha,
-                        double beta, double *C, int64_t ldc, const GemmExtra &x, int *err_flag, cudaStream_t s);
+                        double beta, double *C, int64_t ldc, const GemmExtra &x, int *err_flag, cudaStream_t s,
+                        float *Cf = nullptr);
+// FP32 data through the same emulation (FP32 values are exact in FP64), the
+// result rounded once to FP32: C = alpha op(A) op(B) + beta C (EPI_STORE only)
+cudaError_t oz_gemm_f32(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const float *A, int64_t lda,
+                        const float *B, int64_t ldb, double beta, float *C, int64_t ldc, const GemmExtra &x,
+                        int *err_flag, cudaStream_t s);
 // slices of op(X) (rows x K, X(r, k) at X[r*sr + k*sk]) into q (ld ldk, slices
 // slice_stride apart); per-row exponents into e, or the fixed exponent when e
 // is null (every |X| must then be below 2^fixed_e)
@@ -205,6 +211,8 @@ constexpr int64_t kOzErrMaxK = 7168;
 
 // whether gemm<double,...> sends an M x N x K product to oz_gemm
 bool fp64_use_emulated(int64_t M, int64_t N, int64_t K);
+// whether gemm<float,...> sends an M x N x K product to oz_gemm_f32
+bool fp32_use_emulated(int64_t M, int64_t N, int64_t K);
 
 // --------------------------------------------------------------------------
 // Streaming kernels

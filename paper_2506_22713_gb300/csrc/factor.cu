@@ -72,10 +72,12 @@ inline int64_t round_up8(int64_t x) { return (x + 7) / 8 * 8; }
 // largest tau (subspace iterations of Alg. 2) accepted
 constexpr int kMaxPowerIters = 16;
 
-// Second CholQR pass on a near-identity Gram I + E: with ||E||_F <= 1e-8 the
-// first-order factor I + Phi(E) is exact to O(||E||^2) <= 1e-16 and replaces
-// the factorisation (see chol_small).
-constexpr double kNearIdTau2 = 1e-16;
+// Second CholQR pass on a near-identity Gram I + E: the first-order factor
+// I + Phi(E) is exact to O(||E||^2) and replaces the factorisation (see
+// chol_small) when that is below the data's rounding: ||E||_F <= 1e-8 for
+// FP64 data (O(E^2) <= 1e-16), ||E||_F <= 3.2e-5 for FP32 data (O(E^2) <=
+// 1e-9, under the FP32 unit roundoff 6e-8).
+template <typename T> constexpr double near_id_tau2() { return std::is_same<T, double>::value ? 1e-16 : 1e-9; }
 
 // smallest eps / ||A||_F the FP32-data paths accept (see factor_impl)
 constexpr double kMixedFloor = 1e-5;
@@ -266,7 +268,7 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
             EOD_CU(offidentity_sumsq(w.G, p, p, w.trace, s));
             EOD_CU(cudaMemcpyAsync(hm.val, w.trace, sizeof(double), cudaMemcpyDeviceToHost, s));
             EOD_CU(cudaStreamSynchronize(s));
-            near_id = hm.val[0] <= kNearIdTau2;
+            near_id = hm.val[0] <= near_id_tau2<T>();
         }
         if (near_id) EOD_CU(near_identity_factor(w.G, p, p, Rpass, p, w.RiD, kPB, s));
         else st = chol_panels(w, p, shift, hm, ws, s, Rpass);
@@ -543,7 +545,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 }
                 EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, Yc, m, Ri, k, 0.0, T1, m, bup, &ws, s)));
                 EOD_CU(gram_skinny<T>(T1, m, p, m, G, k, &ws, s));
-                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, k, R2i, k, info, s, kNearIdTau2));
+                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, k, R2i, k, info, s, near_id_tau2<T>()));
                 const T *Ri2 = (const T *)R2i;
                 if (!std::is_same<T, double>::value) {
                     EOD_CU((copy_matrix<double, T>(R2i, k, RinvT, k, p, p, false, s)));

@@ -465,6 +465,21 @@ bool fp64_use_emulated(int64_t M, int64_t N, int64_t K) {
     return (double)M * (double)N * (double)K >= 33554432.0 && K >= 8 && (M >= 128 || N >= 128);
 }
 
+// FP32 products through the emulation: EOD_FP32_GEMM=simt keeps them all on
+// FFMA; otherwise those of at least 2^27 multiply-adds (the FFMA rate is 64
+// times the DFMA rate, so the emulation pays off later than for FP64).
+bool fp32_use_emulated(int64_t M, int64_t N, int64_t K) {
+    static const int mode = [] {
+        const char *v = std::getenv("EOD_FP32_GEMM");
+        if (v && std::strcmp(v, "simt") == 0) return 0;
+        if (v && std::strcmp(v, "emulated") == 0) return 2;
+        return 1;
+    }();
+    if (mode == 0) return false;
+    if (mode == 2) return M >= 1 && N >= 1 && K >= 1;
+    return (double)M * (double)N * (double)K >= 134217728.0 && K >= 8 && (M >= 128 || N >= 128);
+}
+
 template <typename TA, typename TB, typename TC, typename Acc>
 cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const TA *A,
                  int64_t lda, const TB *B, int64_t ldb, double beta, TC *C, int64_t ldc,
@@ -475,6 +490,12 @@ cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
         ws && ws->err_flag && K > 0 && fp64_use_emulated(M, N, K) && (x.epilogue != EPI_ERR || K <= kOzErrMaxK))
         return oz_gemm(ta, tb, M, N, K, alpha, (const double *)A, lda, (const double *)B, ldb, beta, (double *)C,
                        ldc, x, ws->err_flag, s);
+    // large FP32 products: the same emulation (more accurate than FP32 FFMA
+    // and far faster on this GPU), rounded once to FP32
+    if (std::is_same<TA, float>::value && std::is_same<TB, float>::value && std::is_same<TC, float>::value &&
+        ws && ws->err_flag && K > 0 && x.epilogue == EPI_STORE && fp32_use_emulated(M, N, K))
+        return oz_gemm_f32(ta, tb, M, N, K, alpha, (const float *)A, lda, (const float *)B, ldb, beta, (float *)C,
+                           ldc, x, ws->err_flag, s);
     // matrix-vector products: op(B) is one column of K contiguous values
     if (N == 1 && !tb && K > 0 && x.epilogue == EPI_STORE && !x.upper_only && !x.a_upper && !x.b_upper && ws)
         return launch_gemv<TA, TB, TC, Acc>(ta, M, K, alpha, A, lda, B, beta, C, ws, s);

@@ -74,6 +74,7 @@ struct Params {
     int ea_fixed, eb_fixed;   // then every row / column uses the fixed exponent)
     double alpha, beta;
     double *C;                // output (or split partials when split_stride > 0)
+    float *Cf;                // FP32 output instead of C (EPI_STORE without split partials)
     int64_t ldc, split_stride;
     const double *R;          // EPI_ERR reference
     int64_t ldr;
@@ -296,6 +297,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) oz_gemm_kernel(const __grid_const
                     if (EPI == EPI_STORE) {
                         if (p.split_stride > 0) {
                             p.C[(int64_t)blockIdx.z * p.split_stride + row + col * p.M] = val;
+                        } else if (p.Cf) {
+                            double out = unit_alpha ? val : p.alpha * val;
+                            if (p.beta != 0.0) out = fma(p.beta, (double)p.Cf[row + col * p.ldc], out);
+                            p.Cf[row + col * p.ldc] = (float)out;
                         } else {
                             double out = unit_alpha ? val : p.alpha * val;
                             if (p.beta != 0.0) out = fma(p.beta, p.C[row + col * p.ldc], out);
@@ -360,7 +365,8 @@ constexpr int kMaxExpSplit = 16;        // K ranges of the row-exponent pass
 // cover 32 rows x one K range, so every entry is written once (no atomics,
 // no initialisation pass).  Integer compares of the bit patterns: no FP64
 // arithmetic.
-__global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+template <typename TX>
+__global__ void rowexp_kernel(const TX *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
                               int64_t kper, int tri, int *ep) {
     int *e = ep + (int64_t)blockIdx.y * R;
     __shared__ unsigned long long red[8][33];
@@ -376,7 +382,7 @@ __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K
             unsigned long long m = 0ull;
             if (r < R)
                 for (int64_t k = kb + tx; k < ke; k += 32)
-                    if (!tri_zero(tri, r, k)) m = max(m, abs_bits(X[r * sr + k]));
+                    if (!tri_zero(tri, r, k)) m = max(m, abs_bits((double)X[r * sr + k]));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
             if (tx == 0 && r < R) e[r] = m > 0ull ? exp_of_bits(m) : kExpZero;
@@ -388,7 +394,7 @@ __global__ void rowexp_kernel(const double *__restrict__ X, int64_t R, int64_t K
     unsigned long long mx = 0ull;
     if (r < R)
         for (int64_t k = kb + ty; k < ke; k += 8)
-            if (!tri_zero(tri, r, k)) mx = max(mx, abs_bits(X[r + k * sk]));
+            if (!tri_zero(tri, r, k)) mx = max(mx, abs_bits((double)X[r + k * sk]));
     red[ty][tx] = mx;
     __syncthreads();
     if (ty == 0 && r < R) {
@@ -435,7 +441,8 @@ __device__ __forceinline__ void write_slices(double x, int er, __nv_bfloat16 *o,
 // The row exponents come from the nsplit partial ones of rowexp_kernel (the
 // blocks of the first K column also store them in e_out for the product), or
 // every row takes fixed_e when ep is null.
-__global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
+template <typename TX>
+__global__ void slice_kernel(const TX *__restrict__ X, int64_t R, int64_t K, int64_t sr, int64_t sk,
                              int tri, const int *__restrict__ ep, int nsplit, int *__restrict__ e_out, int fixed_e,
                              __nv_bfloat16 *__restrict__ out, int64_t ldk, int64_t slice_stride) {
     __shared__ double tile[32][33];
@@ -455,7 +462,7 @@ __global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K,
     for (int i = ty; i < 32; i += 8) {
         int64_t r, k;
         if (sk == 1) { r = r0 + i; k = k0 + tx; } else { r = r0 + tx; k = k0 + i; }
-        const double v = (r < R && k < K && !tri_zero(tri, r, k)) ? X[r * sr + k * sk] : 0.0;
+        const double v = (r < R && k < K && !tri_zero(tri, r, k)) ? (double)X[r * sr + k * sk] : 0.0;
         if (sk == 1) tile[i][tx] = v; else tile[tx][i] = v;   // tile[r - r0][k - k0]
     }
     __syncthreads();
@@ -469,18 +476,19 @@ __global__ void slice_kernel(const double *__restrict__ X, int64_t R, int64_t K,
 // Rows with K contiguous (sk == 1) and their own exponents, one CTA per row:
 // the row maximum (as in rowexp_kernel) and then the slices (as in
 // slice_kernel), in one launch; the second read of the row hits L1 / L2.
-__global__ void __launch_bounds__(256) slice_rows_kernel(const double *__restrict__ X, int64_t K, int64_t sr,
+template <typename TX>
+__global__ void __launch_bounds__(256) slice_rows_kernel(const TX *__restrict__ X, int64_t K, int64_t sr,
                                                          int tri, int *__restrict__ e_out,
                                                          __nv_bfloat16 *__restrict__ out, int64_t ldk,
                                                          int64_t slice_stride) {
     __shared__ unsigned long long red[8];
     __shared__ int er_sh;
     const int64_t r = blockIdx.x;
-    const double *x = X + r * sr;
+    const TX *x = X + r * sr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long m = 0ull;
     for (int64_t k = tid; k < K; k += 256)
-        if (!tri_zero(tri, r, k)) m = max(m, abs_bits(x[k]));
+        if (!tri_zero(tri, r, k)) m = max(m, abs_bits((double)x[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) red[warp] = m;
@@ -496,11 +504,13 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double *__restric
     __syncthreads();
     const int er = er_sh;
     __nv_bfloat16 *o = out + r * ldk;
-    for (int64_t k = tid; k < K; k += 256) write_slices(tri_zero(tri, r, k) ? 0.0 : x[k], er, o + k, slice_stride);
+    for (int64_t k = tid; k < K; k += 256)
+        write_slices(tri_zero(tri, r, k) ? 0.0 : (double)x[k], er, o + k, slice_stride);
 }
 
+template <typename TC>
 __global__ void split_sum_kernel(const double *__restrict__ part, int S, int64_t M, int64_t N, double alpha,
-                                 double beta, double *C, int64_t ldc, int upper_only) {
+                                 double beta, TC *C, int64_t ldc, int upper_only) {
     const int64_t total = M * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e % M, j = e / M;
@@ -508,8 +518,8 @@ __global__ void split_sum_kernel(const double *__restrict__ part, int S, int64_t
         double sum = 0.0;
         for (int z = 0; z < S; ++z) sum += part[(int64_t)z * total + e];
         double out = alpha * sum;
-        if (beta != 0.0) out = fma(beta, C[i + j * ldc], out);
-        C[i + j * ldc] = out;
+        if (beta != 0.0) out = fma(beta, (double)C[i + j * ldc], out);
+        C[i + j * ldc] = (TC)out;
     }
 }
 
@@ -519,10 +529,11 @@ struct Slices {
     int64_t R = 0, ldk = 0;
 };
 
-cudaError_t slice_into(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, __nv_bfloat16 *q, int *e,
+template <typename TX>
+cudaError_t slice_into(const TX *X, int64_t R, int64_t K, int64_t sr, int64_t sk, __nv_bfloat16 *q, int *e,
                        int fixed_e, int64_t ldk, int64_t slice_stride, cudaStream_t s, int tri = 0) {
     if (R <= 0 || K <= 0) return cudaSuccess;
-    ProfScope prof(PROF_OZ_SLICE, 0.0, 8.0 * (double)R * K + 2.0 * NS * (double)R * K, s);
+    ProfScope prof(PROF_OZ_SLICE, 0.0, (double)sizeof(TX) * R * K + 2.0 * NS * (double)R * K, s);
     if (e && sk == 1 && (R >= kNumSMs || K <= 8192)) {
         count_launch();
         slice_rows_kernel<<<(unsigned)R, 256, 0, s>>>(X, K, sr, tri, e, q, ldk, slice_stride);
@@ -558,7 +569,8 @@ cudaError_t slice_into(const double *X, int64_t R, int64_t K, int64_t sr, int64_
     return le;
 }
 
-cudaError_t make_slices(const double *X, int64_t R, int64_t K, int64_t sr, int64_t sk, Slices &sl, cudaStream_t s,
+template <typename TX>
+cudaError_t make_slices(const TX *X, int64_t R, int64_t K, int64_t sr, int64_t sk, Slices &sl, cudaStream_t s,
                         int tri = 0) {
     sl.R = R;
     sl.ldk = round_up(K, 8);
@@ -583,9 +595,11 @@ cudaError_t oz_slice(const double *X, int64_t rows, int64_t K, int64_t sr, int64
 }
 
 cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64_t N, int64_t K, double alpha,
-                        double beta, double *C, int64_t ldc, const GemmExtra &x, int *err_flag, cudaStream_t s) {
+                        double beta, double *C, int64_t ldc, const GemmExtra &x, int *err_flag, cudaStream_t s,
+                        float *Cf) {
     using namespace oz;
     if (M <= 0 || N <= 0) return cudaSuccess;
+    if (Cf && x.epilogue != EPI_STORE) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     Maps maps;
     std::memset(&maps, 0, sizeof(maps));
@@ -642,6 +656,7 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
         p.split_stride = M * N;
     } else {
         p.C = C;
+        p.Cf = Cf;
         p.ldc = ldc;
         p.split_stride = 0;
     }
@@ -663,19 +678,21 @@ cudaError_t oz_gemm_ops(const OzOperand &A, const OzOperand &B, int64_t M, int64
     if (e == cudaSuccess && splits > 1) {
         count_launch();
         const int blocks = (int)std::min<int64_t>((M * N + 255) / 256, 4LL * kNumSMs * 8);
-        split_sum_kernel<<<blocks, 256, 0, s>>>(part, (int)splits, M, N, alpha, beta, C, ldc, p.upper_only);
+        if (Cf) split_sum_kernel<float><<<blocks, 256, 0, s>>>(part, (int)splits, M, N, alpha, beta, Cf, ldc,
+                                                                 p.upper_only);
+        else split_sum_kernel<double><<<blocks, 256, 0, s>>>(part, (int)splits, M, N, alpha, beta, C, ldc,
+                                                              p.upper_only);
         e = cudaGetLastError();
     }
     if (part) cudaFreeAsync(part, s);
     return e;
 }
 
-// C = alpha op(A) op(B) + beta C (EPI_STORE) or the squared error against
-// x.ref (EPI_ERR), FP64, through the sliced tensor-core product.
-cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
-                    const double *B, int64_t ldb, double beta, double *C, int64_t ldc, const GemmExtra &x,
-                    int *err_flag, cudaStream_t s) {
-    using namespace oz;
+namespace oz {
+template <typename T>
+cudaError_t gemm_any(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const T *A, int64_t lda,
+                     const T *B, int64_t ldb, double beta, double *C, float *Cf, int64_t ldc, const GemmExtra &x,
+                     int *err_flag, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     Slices sa, sb;
     // op(A)(i, k): rows i, reduction k; op(B)(k, j) seen as rows j
@@ -688,11 +705,29 @@ cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double al
     if (e == cudaSuccess) {
         OzOperand oa{sa.q, sa.e, 0, sa.ldk, (int64_t)M * sa.ldk};
         OzOperand ob{SB.q, SB.e, 0, SB.ldk, (int64_t)N * SB.ldk};
-        e = oz_gemm_ops(oa, ob, M, N, K, alpha, beta, C, ldc, x, err_flag, s);
+        e = oz_gemm_ops(oa, ob, M, N, K, alpha, beta, C, ldc, x, err_flag, s, Cf);
     }
     free_slices(sa, s);
     if (!same) free_slices(sb, s);
     return e;
+}
+}  // namespace oz
+
+// C = alpha op(A) op(B) + beta C (EPI_STORE) or the squared error against
+// x.ref (EPI_ERR), FP64, through the sliced tensor-core product.
+cudaError_t oz_gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                    const double *B, int64_t ldb, double beta, double *C, int64_t ldc, const GemmExtra &x,
+                    int *err_flag, cudaStream_t s) {
+    return oz::gemm_any<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, nullptr, ldc, x, err_flag, s);
+}
+
+// The same product of FP32 data (exact in FP64, so sliced the same way) with
+// an FP32 result: C = alpha op(A) op(B) + beta C rounded once to FP32.
+cudaError_t oz_gemm_f32(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const float *A, int64_t lda,
+                        const float *B, int64_t ldb, double beta, float *C, int64_t ldc, const GemmExtra &x,
+                        int *err_flag, cudaStream_t s) {
+    if (x.epilogue != EPI_STORE) return cudaErrorInvalidValue;
+    return oz::gemm_any<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, nullptr, C, ldc, x, err_flag, s);
 }
 
 int64_t oz_gemm_err_ctas(int64_t M, int64_t N) { return ((M + oz::BM - 1) / oz::BM) * ((N + oz::BN - 1) / oz::BN); }
