@@ -143,23 +143,22 @@ __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *
     // (I + Phi(E)) = I + E + Phi(E)^T Phi(E).
     if (ni_tau2 > 0.0) {
         __shared__ double red[32];
+        const int wp = threadIdx.x >> 5, ln = threadIdx.x & 31;
         double acc = 0.0;
-        for (int e = threadIdx.x; e < w * w; e += NT) {
-            const int i = e % w, c = e / w;
-            if (i <= c) {
+        for (int c = wp; c < w; c += NT / 32)          // a warp per column, lanes down it
+            for (int i = ln; i <= c; i += 32) {
                 const double v = G[i + (int64_t)c * ldg] - (i == c ? 1.0 : 0.0);
-                acc += (i == c ? 1.0 : 2.0) * v * v;
+                acc = fma(i == c ? v : 2.0 * v, v, acc);
             }
-        }
         const double tot = block_sum(acc, red);
         if (tot <= ni_tau2) {
-            for (int e = threadIdx.x; e < w * w; e += NT) {
-                const int i = e % w, c = e / w;
-                const double g = (i <= c) ? G[i + (int64_t)c * ldg] : 0.0;
-                const double x = (i < c) ? g : (i == c ? 0.5 * (g - 1.0) : 0.0);
-                R[i + (int64_t)c * ldr] = (i == c ? 1.0 : 0.0) + x;
-                if (Rinv) Rinv[i + (int64_t)c * ldinv] = (i == c ? 1.0 : 0.0) - x;
-            }
+            for (int c = wp; c < w; c += NT / 32)
+                for (int i = ln; i < w; i += 32) {
+                    const double g = (i <= c) ? G[i + (int64_t)c * ldg] : 0.0;
+                    const double x = (i < c) ? g : (i == c ? 0.5 * (g - 1.0) : 0.0);
+                    R[i + (int64_t)c * ldr] = (i == c ? 1.0 : 0.0) + x;
+                    if (Rinv) Rinv[i + (int64_t)c * ldinv] = (i == c ? 1.0 : 0.0) - x;
+                }
             if (threadIdx.x == 0) {
                 info[0] = w;
                 info[1] = CHOL_ALL;
@@ -313,18 +312,28 @@ __global__ void tdiag_kernel(const double *R1, const double *R2, int64_t ldr, co
 }
 
 // ||G - I||_F^2 of a symmetric p x p matrix from its upper triangle.
-// One warp per column, lanes down the column (coalesced, no index division).
-__global__ void offidentity_kernel(const double *G, int64_t ldg, int64_t p, double *out) {
+// Partial sums of ||G - I||_F^2 (upper triangle read): CTA b takes the
+// columns c = b, b + gridDim.x, ..., a warp per column, lanes down it; the
+// partials are added in CTA order by offidentity_finish_kernel.
+__global__ void offidentity_partial_kernel(const double *G, int64_t ldg, int64_t p, double *part) {
     __shared__ double red[32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     double acc = 0.0;
-    for (int64_t c = warp; c < p; c += nw) {
+    for (int64_t c = (int64_t)blockIdx.x * nw + warp; c < p; c += (int64_t)gridDim.x * nw) {
         const double *col = G + c * ldg;
         for (int64_t i = lane; i <= c; i += 32) {
             const double v = col[i] - (i == c ? 1.0 : 0.0);
             acc = fma(i == c ? v : 2.0 * v, v, acc);
         }
     }
+    const double tot = block_sum(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void offidentity_finish_kernel(const double *part, int n, double *out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
     const double tot = block_sum(acc, red);
     if (threadIdx.x == 0) out[0] = tot;
 }
@@ -369,9 +378,11 @@ cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double e
     return cudaGetLastError();
 }
 
-cudaError_t offidentity_sumsq(const double *G, int64_t ldg, int64_t p, double *out, cudaStream_t s) {
-    count_launch();
-    offidentity_kernel<<<1, 1024, 0, s>>>(G, ldg, p, out);
+cudaError_t offidentity_sumsq(const double *G, int64_t ldg, int64_t p, double *part, double *out, cudaStream_t s) {
+    const int blocks = (int)std::min<int64_t>((p + 7) / 8, kOffIdMaxBlocks);
+    count_launch(2);
+    offidentity_partial_kernel<<<blocks, 256, 0, s>>>(G, ldg, p, part);
+    offidentity_finish_kernel<<<1, 256, 0, s>>>(part, blocks, out);
     return cudaGetLastError();
 }
 

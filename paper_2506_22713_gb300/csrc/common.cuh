@@ -266,8 +266,10 @@ enum CholCode { CHOL_ALL = 0, CHOL_BELOW = 1, CHOL_UNCERTAIN = 2, CHOL_FAIL = 3 
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2,
                        double delta_coef, double rho, double shift, double *R, int64_t ldr,
                        double *Rinv, int64_t ldinv, int *info, cudaStream_t s, double ni_tau2 = 0.0);
-// out[0] = ||G - I||_F^2 of the symmetric p x p matrix G (upper triangle read)
-cudaError_t offidentity_sumsq(const double *G, int64_t ldg, int64_t p, double *out, cudaStream_t s);
+// out[0] = ||G - I||_F^2 of the symmetric p x p matrix G (upper triangle
+// read), through kOffIdMaxBlocks partial sums in `part`
+constexpr int kOffIdMaxBlocks = 608;
+cudaError_t offidentity_sumsq(const double *G, int64_t ldg, int64_t p, double *part, double *out, cudaStream_t s);
 // the first-order factor of a near-identity G (see chol_small): R (p x p,
 // ld ldr, zeros below the diagonal) and the inverses of its diagonal panels
 // of width pb at RiD + J pb^2 (ld pb)

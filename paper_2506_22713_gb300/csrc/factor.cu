@@ -101,7 +101,7 @@ template <> struct Traits<float> { static constexpr int dtype = EOD_F32; static 
 template <typename T>
 struct CoreWork {
     double *G = nullptr, *R = nullptr, *Rp = nullptr, *RiD = nullptr, *RiT = nullptr,
-           *trace = nullptr;
+           *trace = nullptr, *part = nullptr;
     T *InvT = nullptr, *Tmp = nullptr;
     int *info = nullptr;
     int64_t pcap = 0, rows_cap = 0;
@@ -265,7 +265,7 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
         eod_status st = EOD_OK;
         bool near_id = false;
         if (pass > 0 && shift == 0.0) {
-            EOD_CU(offidentity_sumsq(w.G, p, p, w.trace, s));
+            EOD_CU(offidentity_sumsq(w.G, p, p, w.part, w.trace, s));
             EOD_CU(cudaMemcpyAsync(hm.val, w.trace, sizeof(double), cudaMemcpyDeviceToHost, s));
             EOD_CU(cudaStreamSynchronize(s));
             near_id = hm.val[0] <= near_id_tau2<T>();
@@ -643,6 +643,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(ar.get(&cw.RiD, (size_t)((r + kPB - 1) / kPB) * kPB * kPB));
     EOD_TRY(ar.get(&cw.RiT, (size_t)kPB * kPB));
     EOD_TRY(ar.get(&cw.trace, 1));
+    EOD_TRY(ar.get(&cw.part, (size_t)kOffIdMaxBlocks));
     EOD_TRY(ar.get(&cw.InvT, (size_t)std::max<int64_t>(r, kPB) * kPB));
     EOD_TRY(ar.get(&cw.Tmp, (size_t)std::max(m, n) * kPB));
     EOD_TRY(ar.get(&cw.info, (size_t)2 * nblk));

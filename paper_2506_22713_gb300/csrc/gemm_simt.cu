@@ -465,19 +465,18 @@ bool fp64_use_emulated(int64_t M, int64_t N, int64_t K) {
     return (double)M * (double)N * (double)K >= 33554432.0 && K >= 8 && (M >= 128 || N >= 128);
 }
 
-// FP32 products through the emulation: EOD_FP32_GEMM=simt keeps them all on
-// FFMA; otherwise those of at least 2^27 multiply-adds (the FFMA rate is 64
-// times the DFMA rate, so the emulation pays off later than for FP64).
+// FP32 products through the emulation only with EOD_FP32_GEMM=emulated: the
+// FFMA rate is 64 times the DFMA rate, and at the shapes of the method (one
+// side at most a few hundred, FP32 operands sliced on every call) the FFMA
+// kernel measured as fast or faster (8192 x 455 x 455: 259 us FFMA against
+// 255 us emulated plus 64 us of slicing; 8192 x 256 x 256: 75 against
+// 85 + 36 us), so it stays the default.
 bool fp32_use_emulated(int64_t M, int64_t N, int64_t K) {
-    static const int mode = [] {
+    static const bool on = [] {
         const char *v = std::getenv("EOD_FP32_GEMM");
-        if (v && std::strcmp(v, "simt") == 0) return 0;
-        if (v && std::strcmp(v, "emulated") == 0) return 2;
-        return 1;
+        return v && std::strcmp(v, "emulated") == 0;
     }();
-    if (mode == 0) return false;
-    if (mode == 2) return M >= 1 && N >= 1 && K >= 1;
-    return (double)M * (double)N * (double)K >= 134217728.0 && K >= 8 && (M >= 128 || N >= 128);
+    return on && M >= 1 && N >= 1 && K >= 1;
 }
 
 template <typename TA, typename TB, typename TC, typename Acc>

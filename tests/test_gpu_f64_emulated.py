@@ -261,3 +261,33 @@ def test_simt_small_products(eod, ta, tb, M, N, K, flags):
         assert ((C - ref).abs()[keep] <= tol[keep]).all()
     else:
         assert ((C - ref).abs() <= tol).all()
+
+
+def test_fp32_products_through_the_emulation_match_the_oracle():
+    """EOD_FP32_GEMM=emulated sends the FP32 paths' large products through the
+    same emulation (FP32 data exact in FP64, rounded once to FP32): a plain
+    FP32 and a mixed factorisation still match the FP64 oracle.  Run in a
+    child process because the switch is read once per process."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r'''
+import numpy as np, torch, oracle, workloads as W
+import paper_2506_22713_gb300 as eod
+w = W.image_like(m=1500, n=1200, r=60, tol=2e-3)
+A32 = w.A.astype(np.float32)
+ref = oracle.eod_abe(A32.astype(np.float64), w.tol, 1, k=64, seed=w.seed)
+A = torch.from_numpy(np.asfortranarray(A32)).cuda()
+for prec in ("plain", "mixed"):
+    f = eod.factor(A, w.tol, w.seed, block_k=64, tol_mode="rel", precision=prec)
+    assert f.rank == ref["r"], (prec, f.rank, ref["r"])
+    assert abs(f.rel_err - ref["rel_err"]) <= 1e-4, (prec, f.rel_err, ref["rel_err"])
+    I = torch.eye(f.rank, dtype=torch.float64, device="cuda")
+    assert torch.linalg.norm(f.V.double().t() @ f.V.double() - I).item() < 1e-4
+    f.close()
+print("ok")
+'''
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=root, timeout=600,
+                         env=dict(os.environ, EOD_FP32_GEMM="emulated", PYTHONPATH=root))
+    assert out.returncode == 0 and "ok" in out.stdout, out.stderr[-3000:]
