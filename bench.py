@@ -48,7 +48,7 @@ FP64_SM_PEAK_GFLOPS = FP64_PEAK_GFLOPS / 152
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 L2_BYTES = 129 * 1024 * 1024
 # kernel kinds of the library's profile counters, in PROF_* order
-KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm", "oz_slice"]
+KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm", "oz_slice", "gemm_simt_f32"]
 # BF16 slice-pair products per emulated FP64 multiply-add (8 slices, s + t <= 7)
 OZ_PAIRS = 36
 
@@ -212,6 +212,7 @@ KIND_SOURCES = {
     "tc_gemm": ["paper_2506_22713_gb300/csrc/tc_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"],
     "chol": ["paper_2506_22713_gb300/csrc/chol.cu"],
     "gemm_simt": ["paper_2506_22713_gb300/csrc/gemm_simt.cu"],
+    "gemm_simt_f32": ["paper_2506_22713_gb300/csrc/gemm_simt.cu", "paper_2506_22713_gb300/csrc/gram.cu"],
     "stream": ["paper_2506_22713_gb300/csrc/stream_kernels.cu"],
 }
 
@@ -243,6 +244,12 @@ def roofline_of(kind, rec, peaks):
         ach = fl / (ms / 1e3) / 1e9
         out.update(bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS, unit="GFLOP/s",
                    peak_source="FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz")
+    elif kind == "gemm_simt_f32":
+        ach = fl / (ms / 1e3) / 1e9
+        out.update(bound="alu", achieved=ach, peak=FP32_PEAK_GFLOPS, unit="GFLOP/s",
+                   peak_source="FP32 from unit counts: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz",
+                   note="the FP32 Gram forms each product exactly and sums with TwoSum (~9 FP32 operations "
+                        "per multiply-add); achieved counts 2 flops per multiply-add")
     else:
         ach = by / (ms / 1e3) / 1e9
         out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s",

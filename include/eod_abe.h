@@ -223,7 +223,8 @@ EOD_API void eod_abe_debug_fail_alloc_after(int32_t n);
  * test, 2 Omega generation, 3 streaming (norms, copies, splitting),
  * 4 tcgen05 tensor-core GEMM (mixed path), 5 FP64 GEMM emulated on tcgen05
  * (plain FP64 path), 6 slicing of FP64 operands into the BF16 digits of that
- * emulation; eod_abe_debug_profile(0) stops it and clears.
+ * emulation, 7 SIMT GEMM and Gram in FP32 arithmetic (FP32-data paths; kind 0
+ * is then the FP64 ones); eod_abe_debug_profile(0) stops it and clears.
  * eod_abe_debug_profile_read() waits for the recorded events of one kind and
  * returns the launch count, the summed device time (ms) and the summed
  * algorithmic flops and bytes of those launches; EOD_EINVAL for an unknown
@@ -299,8 +300,10 @@ EOD_API eod_status eod_abe_fro_norm_noalloc(const void *A, int64_t m, int64_t n,
  * factorisation stops at the first pivot that is not kept.  Writes R (upper,
  * zeros below, leading p x p) and, when Rinv is not null, R^{-1} (same ld);
  * info[0] = p (columns factored), info[1] = 0 all kept / 1 below eps /
- * 2 undecided / 3 not positive.  Returns after synchronising `stream`;
- * EOD_EINVAL for w outside [1, 128] or short leading dimensions. */
+ * 2 undecided / 3 not positive.  decide | 256 runs the schedule with two
+ * barriers per pivot instead of the lookahead one the library uses (same
+ * results up to rounding; for comparison).  Returns after synchronising
+ * `stream`; EOD_EINVAL for w outside [1, 128] or short leading dimensions. */
 EOD_API eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w, int32_t decide, double eps2,
                                       double delta_coef, double rho, double shift, double *R, double *Rinv,
                                       int64_t ldr, int32_t *info, void *stream);

@@ -101,8 +101,10 @@ __device__ __forceinline__ void ldl_pivot(const double *S, int ld, int w, int j,
 constexpr int kLeafThreads = 512;
 
 size_t leaf_smem_bytes(int w) {
+    // S, M, pivots, sqrt and 1/sqrt, three key arrays, the entry table, then
+    // (8-byte aligned) the lookahead's second M buffer
     return sizeof(double) * ((size_t)w * (w + 1) + 4 * (size_t)w) + sizeof(long long) * 3 * (size_t)w +
-           sizeof(uint16_t) * (size_t)((w - 1) * (w - 2) / 2 + 1);
+           sizeof(uint16_t) * (size_t)((w - 1) * (w - 2) / 2 + 1) + 8 + sizeof(double) * (size_t)w;
 }
 
 // One CTA: G + shift I = L D L^T (unit lower L, no square roots on the
@@ -129,6 +131,7 @@ size_t leaf_smem_bytes(int w) {
 // hide more of the update loop's latency (61 vs 70 us at w = 64).
 // The rank test reads the pivots d_j = T(j,j)^2 exactly as the Cholesky form
 // would; R differs from a square-root Cholesky only by rounding.
+template <bool LA>
 __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *__restrict__ G, int64_t ldg, int w,
                                                                   int decide, double eps2, double delta_coef,
                                                                   double rho, double shift, double *__restrict__ R,
@@ -176,8 +179,11 @@ __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *
     long long *khi = klo + w;
     long long *krg = khi + w;
     uint16_t *ent = (uint16_t *)(krg + w);             // (w-1)(w-2)/2 entries: row | k << 8
+    double *mcol2 = (double *)(((uintptr_t)(ent + (w - 1) * (w - 2) / 2 + 1) + 7) & ~(uintptr_t)7);   // LA: M of odd steps
     __shared__ int p_sh, code_sh, go_sh;
     __shared__ double rd_sh, mt_sh;
+    __shared__ int go2_sh[2];
+    __shared__ double rd2_sh[2], mt2_sh[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // S(i, c) = G(c, i) for i >= c: G's upper triangle read along its columns
@@ -223,12 +229,81 @@ __global__ void __launch_bounds__(kLeafThreads) chol_small_kernel(const double *
         code_sh = CHOL_ALL;
     }
     __syncthreads();
-    if (warp == 0) ldl_pivot(S, ld, w, 0, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &mt_sh, &p_sh, &code_sh, tid == 0);
-    __syncthreads();
-
     constexpr int NW = (NT / 32 - NT / 128) * 32;          // update threads: warps not on sub-partition 0
     const bool worker = (warp & 3) != 0;
     const int me = (warp - (warp >> 2) - 1) * 32 + lane;
+    if (LA) {
+        // Lookahead: one barrier per step.  In phase j the workers apply step
+        // j (multipliers M_j, row u_j) to the columns >= j + 2 and to the rows
+        // of Z, warp 4 stores M_j as Z's column j, and warp 0 meanwhile gives
+        // column j + 1 its step-j update, decides pivot j + 1 and stages u_{j+1}
+        // and M_{j+1} (the other buffer) for phase j + 1.  Column j + 1 holds
+        // the updates of steps < j from the workers of phase j - 1.
+        double *mb[2] = {mcol, mcol2};
+        if (warp == 0) {
+            ldl_pivot(S, ld, w, 0, klo, khi, krg, decide, dv, &go2_sh[0], &rd2_sh[0], &mt2_sh[0], &p_sh, &code_sh,
+                      lane == 0);
+            __syncwarp();
+            if (go2_sh[0]) {
+                const double r0 = rd2_sh[0];
+                for (int i = 1 + lane; i < w; i += 32) {
+                    const double ui = S[i];
+                    S[i * ld] = ui;
+                    mcol[i] = -(ui * r0);
+                }
+            }
+        }
+        __syncthreads();
+        for (int j = 0; j < w; ++j) {
+            const int b = j & 1;
+            if (!go2_sh[b] || j + 1 >= w) break;
+            const double *M = mb[b];
+            if (warp == 0) {
+                const double uj1 = S[j + (j + 1) * ld];             // u_j(j + 1)
+                for (int i = j + 1 + lane; i < w; i += 32) S[i + (j + 1) * ld] = fma(M[i], uj1, S[i + (j + 1) * ld]);
+                __syncwarp();
+                ldl_pivot(S, ld, w, j + 1, klo, khi, krg, decide, dv, &go2_sh[b ^ 1], &rd2_sh[b ^ 1], &mt2_sh[b ^ 1],
+                          &p_sh, &code_sh, lane == 0);
+                __syncwarp();
+                if (go2_sh[b ^ 1]) {
+                    const double r1 = rd2_sh[b ^ 1];
+                    double *M1 = mb[b ^ 1];
+                    for (int i = j + 2 + lane; i < w; i += 32) {
+                        const double ui = S[i + (j + 1) * ld];
+                        S[(j + 1) + i * ld] = ui;
+                        M1[i] = -(ui * r1);
+                    }
+                }
+            } else if (warp == 4) {
+                for (int i = j + 1 + lane; i < w; i += 32) S[i + j * ld] = M[i];
+            } else if (worker) {
+                const int cnt = ((w - 2) * (w - 1) - j * (j - 1)) / 2;
+                int e = me;
+                for (; e + NW < cnt; e += 2 * NW) {   // two entries in flight
+                    const int pa = ent[e], pb = ent[e + NW];
+                    const int ra = pa & 0xff, ka = pa >> 8, rb = pb & 0xff, kb = pb >> 8;
+                    const int ca = ka < j ? ka : ka + 2, cb = kb < j ? kb : kb + 2;
+                    const double ma = M[ra], mbv = M[rb];
+                    const double xa = S[j + ca * ld], xb = S[j + cb * ld];
+                    const double sa = S[ra + ca * ld], sb = S[rb + cb * ld];
+                    S[ra + ca * ld] = fma(ma, xa, sa);
+                    S[rb + cb * ld] = fma(mbv, xb, sb);
+                }
+                if (e < cnt) {
+                    const int pa = ent[e];
+                    const int ra = pa & 0xff, ka = pa >> 8;
+                    const int ca = ka < j ? ka : ka + 2;
+                    S[ra + ca * ld] = fma(M[ra], S[j + ca * ld], S[ra + ca * ld]);
+                }
+            }
+            __syncthreads();
+        }
+        go_sh = 0;   // the classic loop below is skipped
+    } else {
+        if (warp == 0)
+            ldl_pivot(S, ld, w, 0, klo, khi, krg, decide, dv, &go_sh, &rd_sh, &mt_sh, &p_sh, &code_sh, tid == 0);
+    }
+    __syncthreads();
     for (int j = 0; j < w; ++j) {
         if (!go_sh) break;
         const double rd = rd_sh, mt = mt_sh;
@@ -367,14 +442,19 @@ __global__ void trace_kernel(const double *G, int64_t ldg, int64_t p, double *ou
 
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2, double delta_coef,
                        double rho, double shift, double *R, int64_t ldr, double *Rinv, int64_t ldinv, int *info,
-                       cudaStream_t s, double ni_tau2) {
+                       cudaStream_t s, double ni_tau2, bool classic) {
     if (w < 1 || w > 128) return cudaErrorInvalidValue;
     if (decide || shift != 0.0) ni_tau2 = 0.0;
-    EOD_CUDA_TRY(set_smem_once(chol_small_kernel, (int)leaf_smem_bytes(128)));
+    EOD_CUDA_TRY(set_smem_once(chol_small_kernel<true>, (int)leaf_smem_bytes(128)));
+    EOD_CUDA_TRY(set_smem_once(chol_small_kernel<false>, (int)leaf_smem_bytes(128)));
     ProfScope prof(PROF_CHOL, (double)w * w * w * (Rinv ? 2.0 : 1.0) / 3.0, sizeof(double) * 3.0 * w * w, s);
     count_launch();
-    chol_small_kernel<<<1, kLeafThreads, leaf_smem_bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho, shift, R,
-                                                                  ldr, Rinv, ldinv, info, ni_tau2);
+    if (classic)
+        chol_small_kernel<false><<<1, kLeafThreads, leaf_smem_bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho,
+                                                                            shift, R, ldr, Rinv, ldinv, info, ni_tau2);
+    else
+        chol_small_kernel<true><<<1, kLeafThreads, leaf_smem_bytes(w), s>>>(G, ldg, w, decide, eps2, delta_coef, rho,
+                                                                           shift, R, ldr, Rinv, ldinv, info, ni_tau2);
     return cudaGetLastError();
 }
 
@@ -437,7 +517,9 @@ extern "C" eod_status eod_abe_debug_chol(const double *G, int64_t ldg, int32_t w
     using namespace eod;
     if (!G || !R || !info || w < 1 || w > 128 || ldg < w || ldr < w) return EOD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = chol_small(G, ldg, w, decide ? 1 : 0, eps2, delta_coef, rho, shift, R, ldr, Rinv, ldr, info, s);
+    const bool classic = (decide & 256) != 0;
+    cudaError_t e = chol_small(G, ldg, w, (decide & 255) ? 1 : 0, eps2, delta_coef, rho, shift, R, ldr, Rinv, ldr, info,
+                               s, 0.0, classic);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();

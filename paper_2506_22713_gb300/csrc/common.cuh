@@ -265,7 +265,8 @@ enum CholCode { CHOL_ALL = 0, CHOL_BELOW = 1, CHOL_UNCERTAIN = 2, CHOL_FAIL = 3 
 // O(||G - I||^2)), without the factorisation.
 cudaError_t chol_small(const double *G, int64_t ldg, int w, int decide, double eps2,
                        double delta_coef, double rho, double shift, double *R, int64_t ldr,
-                       double *Rinv, int64_t ldinv, int *info, cudaStream_t s, double ni_tau2 = 0.0);
+                       double *Rinv, int64_t ldinv, int *info, cudaStream_t s, double ni_tau2 = 0.0,
+                       bool classic = false);
 // out[0] = ||G - I||_F^2 of the symmetric p x p matrix G (upper triangle
 // read), through kOffIdMaxBlocks partial sums in `part`
 constexpr int kOffIdMaxBlocks = 608;

@@ -271,7 +271,8 @@ __global__ void gemv_t_reduce_kernel(int64_t M, int S, const Acc *__restrict__ p
 template <typename TA, typename TB, typename TC, typename Acc>
 cudaError_t launch_gemv(bool ta, int64_t M, int64_t K, double alpha, const TA *A, int64_t lda, const TB *x,
                         double beta, TC *y, Scratch *ws, cudaStream_t s) {
-    ProfScope prof(PROF_GEMM_SIMT, 2.0 * (double)M * K, (double)sizeof(TA) * M * K, s);
+    ProfScope prof(std::is_same<Acc, float>::value ? PROF_GEMM_SIMT32 : PROF_GEMM_SIMT, 2.0 * (double)M * K,
+                   (double)sizeof(TA) * M * K, s);
     if (!ta) {
         // K split so that about four CTAs per SM work (a row's FMAs form one
         // dependent chain per range), ranges of at least 16
@@ -422,7 +423,7 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
     const double flops = 2.0 * (double)M * (double)N * (double)K * frac;
     double bytes = (double)sizeof(TA) * M * K + (double)sizeof(TB) * K * N + (double)sizeof(TC) * M * N;
     if (beta != 0.0 || x.epilogue == EPI_ERR) bytes += (double)sizeof(TC) * M * N;
-    ProfScope prof(PROF_GEMM_SIMT, flops, bytes, s);
+    ProfScope prof(std::is_same<Acc, float>::value ? PROF_GEMM_SIMT32 : PROF_GEMM_SIMT, flops, bytes, s);
     if (x.epilogue == EPI_ERR) {
         if ((N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
         count_launch();

@@ -15,6 +15,7 @@
 #include "instrument.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace eod {
 namespace {
@@ -263,7 +264,7 @@ cudaError_t gram_tiled_f32(const float *W, int64_t rows, int64_t p, int64_t ldw,
     }
     const int64_t rows_per = ((rows + S - 1) / S + TBK - 1) / TBK * TBK;
     S = (rows + rows_per - 1) / rows_per;
-    ProfScope prof(PROF_GEMM_SIMT, (double)rows * p * (p + 1), 4.0 * rows * p, s);
+    ProfScope prof(PROF_GEMM_SIMT32, (double)rows * p * (p + 1), 4.0 * rows * p, s);
     dim3 grid((unsigned)gt, (unsigned)gt, (unsigned)S);
     if (S > 1) {
         count_launch(2);
@@ -299,7 +300,8 @@ cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, in
     size_t smem = sizeof(T) * (size_t)GR * (w + 1);
     if (smem < sizeof(double) * GT * 16) smem = sizeof(double) * GT * 16;   // room for the row-group sums
     EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T>, (int)(sizeof(double) * GR * 129)));
-    ProfScope prof(PROF_GEMM_SIMT, (double)m * w * (w + 1), (double)sizeof(T) * m * w, s);
+    ProfScope prof(std::is_same<T, float>::value ? PROF_GEMM_SIMT32 : PROF_GEMM_SIMT, (double)m * w * (w + 1),
+                   (double)sizeof(T) * m * w, s);
     count_launch(2);
     gram_partial_kernel<T><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
     EOD_CUDA_TRY(cudaGetLastError());

@@ -7,14 +7,15 @@ namespace eod {
 
 // kernel kinds, as reported by eod_abe_debug_profile_read()
 enum ProfKind {
-    PROF_GEMM_SIMT = 0,   // SIMT GEMM (plain path contractions), incl. its split-K reduction
+    PROF_GEMM_SIMT = 0,   // SIMT GEMM in FP64 arithmetic (plain path contractions), incl. its split-K reduction
     PROF_CHOL = 1,        // one-CTA Cholesky / rank test
     PROF_OMEGA = 2,       // Gaussian test blocks
     PROF_STREAM = 3,      // norms, copies, scaling, splitting
     PROF_TC_GEMM = 4,     // tcgen05 tensor-core contractions (mixed path)
     PROF_OZ_GEMM = 5,     // FP64 contractions emulated on tcgen05 (plain FP64 path)
     PROF_OZ_SLICE = 6,    // FP64 operands cut into BF16 digit slices for those contractions
-    PROF_KINDS = 7
+    PROF_GEMM_SIMT32 = 7, // SIMT GEMM and Gram in FP32 arithmetic (FP32-data paths)
+    PROF_KINDS = 8
 };
 
 void count_launch(int n = 1);

@@ -144,3 +144,24 @@ def test_leaf_reciprocal_against_cuda_division(eod):
     assert np.isinf(e[0]) and e[0] > 0 and np.isinf(e[1]) and np.isinf(e[2])
     assert e[3] == 0.0 and e[4] == 0.0
     assert eod.eod_abe_debug_recip(None, P(eo), 1, s) == eod.EOD_EINVAL
+
+
+@pytest.mark.parametrize("w,cond,decide", [(64, 1e4, 0), (128, 1e6, 0), (37, 1e3, 0), (64, 1e8, 1), (2, 10.0, 0),
+                                           (1, 1.0, 0), (100, 1e5, 1)])
+def test_lookahead_schedule_matches_the_two_barrier_schedule(eod, w, cond, decide):
+    """The library's leaf (one barrier per pivot, the next pivot decided
+    while the trailing update runs) against the two-barrier schedule (decide
+    | 256): same columns factored, same outcome, factors equal up to
+    rounding; in decide mode with eps between the pivots, the same stop."""
+    G = _spd(w, cond, 100 + w)
+    eps2 = float(np.sort(np.linalg.eigvalsh(G))[w // 2]) if decide else 0.0
+    coef = 64 * (64 + np.sqrt(1000.0)) * U64 if decide else 0.0
+    rho = 1e-10 if decide else 0.0
+    a = _run(eod, G, decide=decide, eps2=eps2, coef=coef, rho=rho)
+    b = _run(eod, G, decide=decide | 256, eps2=eps2, coef=coef, rho=rho)
+    assert a[0] == b[0] and a[1] == b[1]
+    p = a[0]
+    if p:
+        scale = np.abs(a[2]).max()
+        assert np.abs(a[2] - b[2]).max() <= 1e-12 * cond * scale
+        assert np.abs(a[3] @ a[2] - np.eye(p)).max() <= 1e-9 * cond
