@@ -334,6 +334,42 @@ struct SimtPlan {
     int64_t gm, gn, S;
 };
 
+// FP32 arithmetic has 64 times the issue rate, and there shared memory
+// bounds the tile instead: per step of K a warp issues TPT^2 FFMA (4 per
+// clock per SM) against about 2 TPT shared-memory wavefronts (1 per clock),
+// so the per-CTA cost is kch * max(TPT^2 / 4, 2 TPT) and the 128-tiles
+// (TPT = 8) are the only ones that keep the FFMA pipes busy.
+inline SimtPlan simt_plan_f32(int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
+    SimtPlan best{64, 0, 0, 1};
+    double best_cost = -1.0;
+    for (int ts = 128; ts >= 16; ts /= 2) {
+        const int64_t gm = (M + ts - 1) / ts, gn = (N + ts - 1) / ts;
+        if (gn > 65535) continue;
+        int64_t tiles = gm * gn;
+        if (x.upper_only) tiles = (tiles + gm) / 2 + 1;
+        const double tpt = ts / 16.0;
+        const double per_k = std::max(tpt * tpt / 4.0, 2.0 * tpt);
+        for (int64_t kc = BK;; kc *= 2) {
+            const int64_t kch = K > 0 ? std::min<int64_t>(kc, K) : 1;
+            const int64_t S = K > 0 ? (K + kch - 1) / kch : 1;
+            if (S <= x.max_split && S <= 65535) {
+                // a 128-tile CTA holds 64 accumulators per thread: one CTA per
+                // SM sub-partition set; smaller tiles overlap two
+                const int64_t per_sm = ts == 128 ? 1 : 2;
+                const int64_t waves = (tiles * S + per_sm * kNumSMs - 1) / (per_sm * kNumSMs);
+                double cost = (double)waves * per_sm * (double)kch * per_k * 8.0;
+                if (S > 1) cost += 3000.0 + 2.0 * (double)M * (double)N * (double)S * 4.0 / 2400.0;
+                if (best_cost < 0.0 || cost < best_cost) {
+                    best_cost = cost;
+                    best = {ts, gm, gn, S};
+                }
+            }
+            if (kc >= K) break;
+        }
+    }
+    return best;
+}
+
 inline SimtPlan simt_plan(int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
     SimtPlan best{64, 0, 0, 1};
     double best_cost = -1.0;
@@ -433,8 +469,12 @@ cudaError_t launch(int64_t M, int64_t N, int64_t K, double alpha, const TA *A, i
             (const TC *)x.ref, x.ldref, x.err_partials, nullptr);
         return cudaGetLastError();
     }
-    const SimtPlan pl = simt_plan(M, N, K, x);
+    const bool f32 = std::is_same<Acc, float>::value;
+    const SimtPlan pl = f32 ? simt_plan_f32(M, N, K, x) : simt_plan(M, N, K, x);
     if (pl.gm == 0) return cudaErrorInvalidValue;
+    if (f32 && pl.ts == 128)
+        return launch_store<TA, TB, TC, Acc, TRA, TRB, 128>(pl, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags,
+                                                             x, ws, s);
     if (pl.ts == 64)
         return launch_store<TA, TB, TC, Acc, TRA, TRB, 64>(pl, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, flags,
                                                             x, ws, s);
