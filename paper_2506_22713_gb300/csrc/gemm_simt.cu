@@ -334,12 +334,19 @@ struct SimtPlan {
     int64_t gm, gn, S;
 };
 
+inline SimtPlan simt_plan(int64_t M, int64_t N, int64_t K, const GemmExtra &x);
+
 // FP32 arithmetic has 64 times the issue rate, and there shared memory
 // bounds the tile instead: per step of K a warp issues TPT^2 FFMA (4 per
 // clock per SM) against about 2 TPT shared-memory wavefronts (1 per clock),
 // so the per-CTA cost is kch * max(TPT^2 / 4, 2 TPT) and the 128-tiles
-// (TPT = 8) are the only ones that keep the FFMA pipes busy.
+// (TPT = 8) are the only ones that keep the FFMA pipes busy -- once there
+// are enough of them: with fewer than 128 such tiles (or K < 128) the
+// latency of each CTA's K loop dominates and the FP64 plan's smaller tiles
+// measured faster (8192 x 64 x 64: 11 us on 32-tiles, 16 us on 128-tiles;
+// 8192 x 455 x 455: 126 us on 128-tiles, 259 us on 32-tiles).
 inline SimtPlan simt_plan_f32(int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
+    if (((M + 127) / 128) * ((N + 127) / 128) < 128 || K < 128) return simt_plan(M, N, K, x);
     SimtPlan best{64, 0, 0, 1};
     double best_cost = -1.0;
     for (int ts = 128; ts >= 16; ts /= 2) {
