@@ -344,9 +344,11 @@ inline SimtPlan simt_plan(int64_t M, int64_t N, int64_t K, const GemmExtra &x);
 // are enough of them: with fewer than 128 such tiles (or K < 128) the
 // latency of each CTA's K loop dominates and the FP64 plan's smaller tiles
 // measured faster (8192 x 64 x 64: 11 us on 32-tiles, 16 us on 128-tiles;
-// 8192 x 455 x 455: 126 us on 128-tiles, 259 us on 32-tiles).
+// 8192 x 455 x 455: 126 us on 128-tiles, 259 us on 32-tiles), and with
+// fewer than 4096 rows (the 2048^2 image workload's core products ran 2.6x
+// slower as a whole on 128-tiles).
 inline SimtPlan simt_plan_f32(int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
-    if (((M + 127) / 128) * ((N + 127) / 128) < 128 || K < 128) return simt_plan(M, N, K, x);
+    if (((M + 127) / 128) * ((N + 127) / 128) < 128 || K < 128 || M < 4096) return simt_plan(M, N, K, x);
     SimtPlan best{64, 0, 0, 1};
     double best_cost = -1.0;
     for (int ts = 128; ts >= 16; ts /= 2) {
