@@ -86,13 +86,15 @@ typedef enum {
     EOD_TOL_REL_FRO = 1    /* eps = tol * ||A||_F */
 } eod_tol_mode;
 
-/* Options.  eod_opts_default() fills: F64, PLAIN, TOL_ABS, block_k 0 (= 32),
+/* Options.  eod_opts_default() fills: F64, PLAIN, TOL_ABS, block_k 0 (the
+ * tuned k, eod_abe_tuning_load, else 32),
  * power_iters 0, compute_err 1, stream NULL, batch_index 0. */
 typedef struct {
     int32_t a_dtype;       /* eod_dtype of A (and of A_hat in eod_abe_reconstruct) */
     int32_t precision;     /* eod_precision */
     int32_t tol_mode;      /* eod_tol_mode */
-    int32_t block_k;       /* block size k of Alg. 1 (1..128); 0 selects 32 */
+    int32_t block_k;       /* block size k of Alg. 1 (1..128); 0 selects the tuned
+                              k for this form and size, else 32 */
     int32_t power_iters;   /* tau of Alg. 2 (0..16): subspace iterations after
                               BasisExt, steps 2-7 (Y~ = A^T Q, QR, Y = A Q~, QR),
                               on the rank BasisExt found; 0 = power-free.  The
@@ -175,8 +177,8 @@ EOD_API eod_status eod_abe_reconstruct(const eod_factors *f, void *A_hat, int64_
  * A[i] is a device pointer.  Item i draws Omega with batch_index = i, so its
  * result equals a single eod_abe_factor_ex call with that batch_index.  The
  * items run concurrently on a pool of worker threads, each with its own
- * non-blocking stream (8 by default; the environment variable
- * EOD_BATCH_STREAMS overrides), largest m*n*min(m,n) first; the workers wait
+ * non-blocking stream (EOD_BATCH_STREAMS if set, else the tuned
+ * "batch_workers", else 8), largest m*n*min(m,n) first; the workers wait
  * for the work already queued on opts->stream.  Every item gets its own
  * status in per_item[i] and, on EOD_OK, its own factors in out[i] (free each
  * with eod_abe_free).  Returns EOD_OK if every item succeeded, else the
@@ -347,6 +349,37 @@ EOD_API eod_status eod_abe_debug_f64_gemm(int32_t mode, int32_t ta, int32_t tb, 
  * when it ran out, EOD_EINVAL for budget_cycles outside [1, 4e9] (the
  * library's own per-wait budget is 4e9 cycles, about 2 s). */
 EOD_API eod_status eod_abe_debug_bounded_wait(int64_t budget_cycles, int32_t arrive, void *stream);
+
+/* Tuned parameters (no counterpart in the paper; the autotuner of this
+ * library, paper_2506_22713_gb300/autotune.py, writes them from timings on
+ * the GPU).  The table is a text file of lines
+ *     key a_lo a_hi b_lo b_hi c_lo c_hi value
+ * (inclusive integer ranges, '#' comments, first matching row wins) read
+ * once per process from $EOD_TUNING_FILE, else tuning.txt beside the
+ * library; a missing file means no tuned values and the fixed defaults.
+ * Keys the library consults: "block_k" (a = form: 0 plain FP64, 1 plain
+ * FP32, 2 mixed BF16, 3 mixed TF32; b = m; c = n) for opts->block_k == 0
+ * (default 32); "f32_tile" (a = M, b = N, c = K) for the FP32 SIMT product
+ * tile (16, 32, 64, 128); "batch_workers" (a = count, b = mean m, c = mean n)
+ * for eod_abe_factor_batched's worker streams (default 8; the environment
+ * variable EOD_BATCH_STREAMS overrides).
+ * eod_abe_tuning_load(path) replaces the table by the file at path (NULL:
+ * the default location); EOD_EINVAL for a malformed line (the table is then
+ * left unchanged); a missing file empties it.  eod_abe_tuning_lookup returns
+ * 1 and stores the value when a row matches, else 0. */
+EOD_API eod_status eod_abe_tuning_load(const char *path);
+EOD_API int32_t eod_abe_tuning_lookup(const char *key, int64_t a, int64_t b, int64_t c, int64_t *value);
+
+/* Timing hook of the autotuner (no counterpart in the paper): one FP32
+ * product C = alpha op(A) op(B) + beta C on the SIMT kernel (the one the FP32
+ * data paths use for their products), column-major device matrices, op(X)
+ * = X^T when the flag is nonzero, with the tile forced to ts (16, 32, 64 or
+ * 128) or chosen by the library (ts = 0, the table's "f32_tile" first).
+ * Returns after synchronising `stream`; EOD_EINVAL for another ts, bad sizes
+ * or leading dimensions. */
+EOD_API eod_status eod_abe_debug_f32_gemm(int32_t ts, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,
+                                          double alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                                          double beta, float *C, int64_t ldc, void *stream);
 
 /* Build identification (static string). */
 EOD_API const char *eod_abe_version(void);

@@ -34,7 +34,7 @@ EXPORTED = [
     "eod_abe_debug_fail_alloc_after", "eod_abe_version", "eod_abe_debug_profile",
     "eod_abe_debug_profile_read", "eod_abe_debug_launch_count", "eod_abe_fro_norm_noalloc",
     "eod_abe_debug_tc_gemm", "eod_abe_debug_f64_gemm", "eod_abe_debug_chol", "eod_abe_debug_bounded_wait",
-    "eod_abe_debug_recip",
+    "eod_abe_debug_recip", "eod_abe_tuning_load", "eod_abe_tuning_lookup", "eod_abe_debug_f32_gemm",
 ]
 
 
@@ -120,6 +120,12 @@ def _load() -> ctypes.CDLL:
     lib.eod_abe_debug_bounded_wait.restype = I32
     lib.eod_abe_debug_recip.argtypes = [P, P, I64, P]
     lib.eod_abe_debug_recip.restype = I32
+    lib.eod_abe_tuning_load.argtypes = [ctypes.c_char_p]
+    lib.eod_abe_tuning_load.restype = I32
+    lib.eod_abe_tuning_lookup.argtypes = [ctypes.c_char_p, I64, I64, I64, ctypes.POINTER(I64)]
+    lib.eod_abe_tuning_lookup.restype = I32
+    lib.eod_abe_debug_f32_gemm.argtypes = [I32, I32, I32, I64, I64, I64, F64, P, I64, P, I64, F64, P, I64, P]
+    lib.eod_abe_debug_f32_gemm.restype = I32
     lib.eod_abe_debug_f64_gemm.argtypes = [I32, I32, I32, I64, I64, I64, F64, P, I64, P, I64, F64, P, I64, P]
     lib.eod_abe_debug_f64_gemm.restype = I32
     lib.eod_abe_debug_chol.argtypes = [P, I64, I32, I32, F64, F64, F64, F64, P, P, I64, P, P]
@@ -152,6 +158,15 @@ eod_abe_fro_norm_noalloc = _lib.eod_abe_fro_norm_noalloc
 eod_abe_debug_tc_gemm = _lib.eod_abe_debug_tc_gemm
 eod_abe_debug_bounded_wait = _lib.eod_abe_debug_bounded_wait
 eod_abe_debug_recip = _lib.eod_abe_debug_recip
+eod_abe_tuning_load = _lib.eod_abe_tuning_load
+eod_abe_tuning_lookup = _lib.eod_abe_tuning_lookup
+eod_abe_debug_f32_gemm = _lib.eod_abe_debug_f32_gemm
+
+
+def tuning_lookup(key: str, a: int, b: int = 0, c: int = 0):
+    """The autotuner's value for key at (a, b, c), or None."""
+    v = ctypes.c_int64(0)
+    return v.value if _lib.eod_abe_tuning_lookup(key.encode(), int(a), int(b), int(c), ctypes.byref(v)) else None
 eod_abe_debug_f64_gemm = _lib.eod_abe_debug_f64_gemm
 eod_abe_debug_chol = _lib.eod_abe_debug_chol
 

@@ -166,7 +166,12 @@ struct GemmExtra {
     int64_t ldref = 0;
     double *err_partials = nullptr; // EPI_ERR: one double per CTA (gridDim.x*gridDim.y)
     int max_split = 64;
+    int force_ts = 0;          // SIMT tile forced by the autotuner's timing hook (0 = plan)
 };
+
+// A value of the autotuner's table (tuning.cu) for key at (a, b, c); false
+// when the table has none.
+bool tuned_value(const char *key, int64_t a, int64_t b, int64_t c, int64_t *out);
 
 template <typename TA, typename TB, typename TC, typename Acc>
 cudaError_t gemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,

@@ -815,6 +815,13 @@ eod_status factor_any(const void *A, int64_t m, int64_t n, int64_t lda, double t
     eod_opts_default(&o);
     if (opts) o = *opts;
     EOD_TRY(validate(A, m, n, lda, tol, o));
+    if (o.block_k == 0) {
+        // the autotuner's k for this form and size, else 32
+        const int64_t form = o.precision == EOD_MIXED_BF16 ? 2 : o.precision == EOD_MIXED_TF32 ? 3
+                             : o.a_dtype == EOD_F32 ? 1 : 0;
+        int64_t k = 0;
+        if (tuned_value("block_k", form, m, n, &k) && k >= 1 && k <= 128) o.block_k = (int32_t)k;
+    }
     cudaStream_t s = (cudaStream_t)o.stream;
     eod_factors *F = (eod_factors *)std::calloc(1, sizeof(eod_factors));
     if (!F) return EOD_ENOMEM;
@@ -997,8 +1004,21 @@ eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const 
         const double cb = (double)m[b] * n[b] * std::min(m[b], n[b]);
         return ca > cb;
     });
+    // worker streams: EOD_BATCH_STREAMS, else the autotuner's value for this
+    // batch (count, mean m, mean n), else 8
     int workers = 8;
-    if (const char *env = std::getenv("EOD_BATCH_STREAMS")) workers = std::max(1, std::atoi(env));
+    if (const char *env = std::getenv("EOD_BATCH_STREAMS")) {
+        workers = std::max(1, std::atoi(env));
+    } else {
+        double sm = 0.0, sn = 0.0;
+        for (int64_t i = 0; i < count; ++i) {
+            sm += (double)m[i];
+            sn += (double)n[i];
+        }
+        int64_t v = 0;
+        if (tuned_value("batch_workers", count, (int64_t)(sm / count), (int64_t)(sn / count), &v) && v >= 1 && v <= 64)
+            workers = (int)v;
+    }
     if (workers > count) workers = (int)count;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }

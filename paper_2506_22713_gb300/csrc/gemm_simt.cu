@@ -348,10 +348,16 @@ inline SimtPlan simt_plan(int64_t M, int64_t N, int64_t K, const GemmExtra &x);
 // fewer than 4096 rows (the 2048^2 image workload's core products ran 2.6x
 // slower as a whole on 128-tiles).
 inline SimtPlan simt_plan_f32(int64_t M, int64_t N, int64_t K, const GemmExtra &x) {
-    if (((M + 127) / 128) * ((N + 127) / 128) < 128 || K < 128 || M < 4096) return simt_plan(M, N, K, x);
+    // the tile: forced (timing hook), else the autotuner's table, else the rule
+    int only = x.force_ts;
+    int64_t tv = 0;
+    if (!only && tuned_value("f32_tile", M, N, K, &tv) && (tv == 16 || tv == 32 || tv == 64 || tv == 128))
+        only = (int)tv;
+    if (!only && (((M + 127) / 128) * ((N + 127) / 128) < 128 || K < 128 || M < 4096)) return simt_plan(M, N, K, x);
     SimtPlan best{64, 0, 0, 1};
     double best_cost = -1.0;
     for (int ts = 128; ts >= 16; ts /= 2) {
+        if (only && ts != only) continue;
         const int64_t gm = (M + ts - 1) / ts, gn = (N + ts - 1) / ts;
         if (gn > 65535) continue;
         int64_t tiles = gm * gn;
@@ -565,6 +571,42 @@ template cudaError_t gemm<float, float, double, double>(bool, bool, int64_t, int
     Scratch *, cudaStream_t);
 
 }  // namespace eod
+
+// ---------------------------------------------------------------------------
+// Timing hook of the autotuner: one FP32 product on the SIMT kernel with a
+// forced tile (ts = 16, 32, 64, 128) or the library's choice (ts = 0).
+// ---------------------------------------------------------------------------
+extern "C" eod_status eod_abe_debug_f32_gemm(int32_t ts, int32_t ta, int32_t tb, int64_t M, int64_t N, int64_t K,
+                                             double alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                                             double beta, float *C, int64_t ldc, void *stream) {
+    using namespace eod;
+    if (!(ts == 0 || ts == 16 || ts == 32 || ts == 64 || ts == 128)) return EOD_EINVAL;
+    if (M < 1 || N < 1 || K < 1 || !A || !B || !C || ldc < M) return EOD_EINVAL;
+    if (lda < (ta ? K : M) || ldb < (tb ? N : K)) return EOD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Arena ar(s);
+    Scratch ws;
+    eod_status st = ar.get((char **)&ws.base, (size_t)64 << 20);
+    if (st != EOD_OK) return st;
+    ws.size = (size_t)64 << 20;
+    st = ar.get(&ws.tile_count, (size_t)kTileCounters);
+    if (st != EOD_OK) return st;
+    ws.tile_count_n = kTileCounters;
+    if (cudaMemsetAsync(ws.tile_count, 0, sizeof(unsigned) * kTileCounters, s) != cudaSuccess) {
+        cudaGetLastError();
+        return EOD_ECUDA;
+    }
+    GemmExtra x;
+    x.force_ts = ts;
+    cudaError_t e = gemm<float, float, float, float>(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+                                                     x, &ws, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return EOD_ECUDA;
+    }
+    return EOD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Test hook: one FP64 GEMM through the SIMT kernel (mode 0) or the tensor-core

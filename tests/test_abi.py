@@ -103,3 +103,40 @@ def test_bounded_wait_hook_rejects_bad_budgets(eod):
     assert eod.eod_abe_debug_bounded_wait(0, 1, None) == eod.EOD_EINVAL
     assert eod.eod_abe_debug_bounded_wait(-5, 0, None) == eod.EOD_EINVAL
     assert eod.eod_abe_debug_bounded_wait(4000000001, 0, None) == eod.EOD_EINVAL
+
+
+def test_tuning_table_parse_lookup_and_reload(eod, tmp_path):
+    """The autotuner's table: ranges match inclusively, the first matching
+    row wins, a malformed file is refused without touching the loaded table,
+    a missing file empties it (host-side only)."""
+    good = tmp_path / "t.txt"
+    good.write_text("# comment\n"
+                    "block_k 2 2 4096 16384 4096 16384 96   # mixed, large\n"
+                    "block_k 0 3 1 100000 1 100000 48\n"
+                    "f32_tile 4096 1000000 256 512 128 100000 128\n")
+    try:
+        assert eod.eod_abe_tuning_load(str(good).encode()) == eod.EOD_OK
+        assert eod.tuning_lookup("block_k", 2, 8192, 8192) == 96
+        assert eod.tuning_lookup("block_k", 2, 16384, 4096) == 96
+        assert eod.tuning_lookup("block_k", 2, 2048, 8192) == 48
+        assert eod.tuning_lookup("block_k", 4, 10, 10) is None
+        assert eod.tuning_lookup("f32_tile", 8192, 455, 455) == 128
+        assert eod.tuning_lookup("f32_tile", 8192, 64, 455) is None
+        assert eod.tuning_lookup("batch_workers", 256, 1000, 1000) is None
+        bad = tmp_path / "bad.txt"
+        bad.write_text("block_k 2 1 1 2 1 2 7\n")          # lo > hi
+        assert eod.eod_abe_tuning_load(str(bad).encode()) == eod.EOD_EINVAL
+        assert eod.tuning_lookup("block_k", 2, 8192, 8192) == 96
+        bad.write_text("block_k 1 2 3\n")                   # too few fields
+        assert eod.eod_abe_tuning_load(str(bad).encode()) == eod.EOD_EINVAL
+        assert eod.eod_abe_tuning_load(str(tmp_path / "missing.txt").encode()) == eod.EOD_OK
+        assert eod.tuning_lookup("block_k", 2, 8192, 8192) is None
+    finally:
+        eod.eod_abe_tuning_load(None)
+
+
+def test_f32_gemm_hook_rejects_bad_arguments(eod):
+    P = ctypes.c_void_p(16)   # never dereferenced: rejected before any launch
+    assert eod.eod_abe_debug_f32_gemm(48, 0, 0, 8, 8, 8, 1.0, P, 8, P, 8, 0.0, P, 8, None) == eod.EOD_EINVAL
+    assert eod.eod_abe_debug_f32_gemm(0, 0, 0, 8, 8, 8, 1.0, P, 7, P, 8, 0.0, P, 8, None) == eod.EOD_EINVAL
+    assert eod.eod_abe_debug_f32_gemm(0, 0, 0, 0, 8, 8, 1.0, P, 8, P, 8, 0.0, P, 8, None) == eod.EOD_EINVAL
