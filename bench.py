@@ -39,8 +39,26 @@ sys.path.insert(0, ROOT)
 
 METRIC = "EOD-ABE GFLOP/s & % roofline, mixed vs plain FP64 at rel-err ≤1e-4"
 WORKLOAD = ("harmonic 8192x8192 FP32: rank-400 s_i=1/i (Haar U, V) + Gaussian noise 1e-6, tol 0.0128 relative, "
-            "k=64; mixed BF16 form (plain FP64 form on the same matrix beside it)")
-HEAD_K = 64
+            "tuned k; mixed BF16 form (plain FP64 form on the same matrix beside it)")
+HEAD_K = 64          # the fixed k reported beside the tuned one
+
+
+def tuned_k(form, m, n, default=32):
+    """k the library takes for block_k = 0: the first "block_k" row of the
+    autotuner's table (paper_2506_22713_gb300/tuning.txt) covering (form, m,
+    n), read as text so that the reference arm needs no GPU library."""
+    code = {"plain_f64": 0, "plain_f32": 1, "mixed": 2, "mixed_tf32": 3}[form]
+    path = os.path.join(ROOT, "paper_2506_22713_gb300", "tuning.txt")
+    try:
+        for line in open(path):
+            f = line.split("#")[0].split()
+            if len(f) == 8 and f[0] == "block_k":
+                v = [int(x) for x in f[1:]]
+                if v[0] <= code <= v[1] and v[2] <= m <= v[3] and v[4] <= n <= v[5]:
+                    return v[6]
+    except OSError:
+        pass
+    return default
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 FP64_SM_PEAK_GFLOPS = FP64_PEAK_GFLOPS / 152
@@ -144,10 +162,11 @@ def oracle_whole(A64, tol, k, seed, threads):
     return flops / el / 1e9, el, r, used
 
 
-def _oracle_sample_text(cores, r):
+def _oracle_sample_text(cores, r, k):
     return (f"whole method (Alg. 1 + Alg. 2 steps 8-11 + explicit RelErr) of the FP64 oracle (plain C, naive "
             f"loops, OpenMP over output columns) on the same 8192x8192 harmonic matrix widened to FP64, "
-            f"k={HEAD_K}, one run on {cores} host thread(s); rank {r}; GFLOP/s of the same cost model as value")
+            f"k={k} (the GPU headline's), one run on {cores} host thread(s); rank {r}; GFLOP/s of the same cost "
+            f"model as value")
 
 
 # ----------------------------------------------------------------- clocks --
@@ -314,9 +333,11 @@ class Stepper:
 
 
 def _factor_fn(eod, A, w, k, prec, **kw):
+    """One factorisation; k = 0 takes the autotuner's k.  Returns (rank,
+    RelErr, k used)."""
     def fn():
         f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec, **kw)
-        out = (f.rank, f.rel_err)
+        out = (f.rank, f.rel_err, f.block_k)
         f.close()
         return out
     return fn
@@ -348,23 +369,24 @@ def run_ours(args):
     # ---- headline: mixed BF16, instrumentation off ----
     clocks = ClockSampler(local)
     clocks.start()
-    t_mx, (r_mx, rel_mx), launches = st.run(_factor_fn(eod, A32, w, HEAD_K, "mixed"), args.steps, args.warmup)
+    t_mx, (r_mx, rel_mx, k_mx), launches = st.run(_factor_fn(eod, A32, w, 0, "mixed"), args.steps, args.warmup)
     clk = clocks.stop()
-    flops_mx = eod.model_flops(m, n, r_mx, HEAD_K, True)
+    flops_mx = eod.model_flops(m, n, r_mx, k_mx, True)
     value = ws * args.steps * flops_mx / (t_mx / 1e3) / 1e9
     ms_step = t_mx / args.steps
 
     # ---- plain FP64 on the same matrix (widened), same steps ----
-    t_64, (r_64, rel_64), _ = st.run(_factor_fn(eod, A64, w, HEAD_K, "plain"), args.steps, args.warmup)
+    t_64, (r_64, rel_64, k_64), _ = st.run(_factor_fn(eod, A64, w, 0, "plain"), args.steps, args.warmup)
     ms_64 = t_64 / args.steps
-    gf_64 = ws * args.steps * eod.model_flops(m, n, r_64, HEAD_K, True) / (t_64 / 1e3) / 1e9
-    forms = {"mixed_bf16": {"gflops": value, "ms": ms_step, "rank": r_mx, "rel_err": rel_mx},
-             "plain_f64": {"gflops": gf_64, "ms": ms_64, "rank": r_64, "rel_err": rel_64}}
+    gf_64 = ws * args.steps * eod.model_flops(m, n, r_64, k_64, True) / (t_64 / 1e3) / 1e9
+    forms = {"mixed_bf16": {"gflops": value, "ms": ms_step, "rank": r_mx, "rel_err": rel_mx, "k": k_mx},
+             "plain_f64": {"gflops": gf_64, "ms": ms_64, "rank": r_64, "rel_err": rel_64, "k": k_64}}
     ctx_steps = max(2, args.steps // 2)
-    for name, A, prec in (("plain_f32", A32, "plain"), ("mixed_tf32", A32, "mixed_tf32")):
-        t, (r, rel), _ = st.run(_factor_fn(eod, A, w, HEAD_K, prec), ctx_steps, 1)
-        forms[name] = {"gflops": ws * ctx_steps * eod.model_flops(m, n, r, HEAD_K, True) / (t / 1e3) / 1e9,
-                       "ms": t / ctx_steps, "rank": r, "rel_err": rel}
+    for name, A, prec, k in (("plain_f32", A32, "plain", 0), ("mixed_tf32", A32, "mixed_tf32", 0),
+                             ("mixed_bf16_fixed_k64", A32, "mixed", HEAD_K), ("plain_f64_fixed_k64", A64, "plain", HEAD_K)):
+        t, (r, rel, kk), _ = st.run(_factor_fn(eod, A, w, k, prec), ctx_steps, 1)
+        forms[name] = {"gflops": ws * ctx_steps * eod.model_flops(m, n, r, kk, True) / (t / 1e3) / 1e9,
+                       "ms": t / ctx_steps, "rank": r, "rel_err": rel, "k": kk}
     for v in forms.values():
         v["rank_equal_f64"] = v["rank"] == r_64
         v["d_rel_err_vs_f64"] = abs(v["rel_err"] - rel_64)
@@ -373,7 +395,7 @@ def run_ours(args):
                       "parity_ok": (r_mx == r_64) and abs(rel_mx - rel_64) <= 1e-4}
 
     # ---- roofline: a separate profiled pass of the headline form ----
-    kinds = st.profile(_factor_fn(eod, A32, w, HEAD_K, "mixed"), 2)
+    kinds = st.profile(_factor_fn(eod, A32, w, 0, "mixed"), 2)
     prof_total = sum(v["ms"] for v in kinds.values())
     dom = max(kinds, key=lambda k: kinds[k]["ms"])
     roofline = roofline_of(dom, kinds[dom], peaks)
@@ -390,7 +412,7 @@ def run_ours(args):
     Vh = torch.empty((cap, n), dtype=torch.float32).pin_memory().t()
 
     def e2e_step():
-        return eod.factor_host(Ah, w.tol, w.seed, block_k=HEAD_K, tol_mode="rel", precision="mixed",
+        return eod.factor_host(Ah, w.tol, w.seed, block_k=0, tol_mode="rel", precision="mixed",
                                U_out=Uh, D_out=Dh, V_out=Vh)
     for _ in range(args.warmup):
         e2e_step()
@@ -402,7 +424,7 @@ def run_ours(args):
         re2e, _ = e2e_step()
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks(time.perf_counter() - t0, dist, "cuda")
-    e2e_val = ws * args.steps * eod.model_flops(m, n, re2e, HEAD_K, True) / e2e_s / 1e9
+    e2e_val = ws * args.steps * eod.model_flops(m, n, re2e, k_mx, True) / e2e_s / 1e9
 
     out = {
         "metric": METRIC,
@@ -417,7 +439,9 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "bf16",
         "data": "synthetic (seeded harmonic low-rank + noise; no dataset)",
-        "config": {"workload": WORKLOAD, "m": m, "n": n, "rank": r_mx, "rel_err": rel_mx, "block_k": HEAD_K,
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "rank": r_mx, "rel_err": rel_mx, "block_k": k_mx,
+                   "tuning": "k, FP32 tiles and batch workers from the autotuner's table "
+                             "(paper_2506_22713_gb300/tuning.txt); forms *_fixed_k64 beside with k = 64",
                    "form": "mixed BF16: sketch/projection/error on tcgen05 (BF16 split, FP32 accumulation); "
                            "Gram/Cholesky/rank test/core in FP64",
                    "parallelism": f"replicas x{ws}", "l2": "flushed between timed steps (258 MB write)",
@@ -442,12 +466,12 @@ def run_ours(args):
         out["robustness_matrices_f64"] = robustness_matrices(eod)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         A64_np = np.asfortranarray(A32_np.astype(np.float64))
-        v, el, r_o, cores = oracle_whole(A64_np, w.tol, HEAD_K, w.seed, 0)
+        v, el, r_o, cores = oracle_whole(A64_np, w.tol, k_mx, w.seed, 0)
         out["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                               "sample": _oracle_sample_text(cores, r_o), "seconds": el,
+                               "sample": _oracle_sample_text(cores, r_o, k_mx), "seconds": el,
                                "rank": r_o, "rank_equal_gpu": r_o == r_mx}
         if args.cpu_one_core:
-            v1, el1, _, _ = oracle_whole(A64_np, w.tol, HEAD_K, w.seed, 1)
+            v1, el1, _, _ = oracle_whole(A64_np, w.tol, k_mx, w.seed, 1)
             out["cpu_baseline"]["one_core"] = {"value": v1, "seconds": el1, "cores": 1}
     if rank == 0:
         print(json.dumps(out))
@@ -473,12 +497,13 @@ def compare_workloads(eod, st, steps, warmup):
         A32 = torch.from_numpy(np.asfortranarray(w.A.astype(np.float32))).cuda()
         m, n = A64.shape
         res = {}
-        for form, A, prec in (("plain_f64", A64, "plain"), ("plain_f32", A32, "plain"), ("mixed_bf16", A32, "mixed"),
-                              ("mixed_tf32", A32, "mixed_tf32")):
-            t, (r, rel), _ = st.run(_factor_fn(eod, A, w, k, prec), steps, warmup)
+        for form, A, prec, kk in (("plain_f64", A64, "plain", 0), ("plain_f32", A32, "plain", 0),
+                                  ("mixed_bf16", A32, "mixed", 0), ("mixed_tf32", A32, "mixed_tf32", 0),
+                                  ("plain_f64_fixed_k", A64, "plain", k), ("mixed_bf16_fixed_k", A32, "mixed", k)):
+            t, (r, rel, ku), _ = st.run(_factor_fn(eod, A, w, kk, prec), steps, warmup)
             ms = t / steps
-            res[form] = {"gflops": eod.model_flops(m, n, r, k, True) / (ms / 1e3) / 1e9, "ms": ms, "rank": r,
-                         "rel_err": rel}
+            res[form] = {"gflops": eod.model_flops(m, n, r, ku, True) / (ms / 1e3) / 1e9, "ms": ms, "rank": r,
+                         "rel_err": rel, "k": ku}
         base = res["plain_f64"]
         for v in res.values():
             v["rank_equal_f64"] = v["rank"] == base["rank"]
@@ -503,9 +528,9 @@ def subspace_iterations(eod, st, steps):
     m, n = w.A.shape
     out = {}
     for tau in (0, 1, 2):
-        t, (r, rel), _ = st.run(_factor_fn(eod, A, w, 64, "plain", power_iters=tau), steps, 2)
+        t, (r, rel, ku), _ = st.run(_factor_fn(eod, A, w, 0, "plain", power_iters=tau), steps, 2)
         ms = t / steps
-        fl = eod.model_flops(m, n, r, 64, True) + 2.0 * tau * (2.0 * m * n * r + 2.0 * m * r * r + 2.0 * n * r * r)
+        fl = eod.model_flops(m, n, r, ku, True) + 2.0 * tau * (2.0 * m * n * r + 2.0 * m * r * r + 2.0 * n * r * r)
         out[f"tau{tau}"] = {"ms_per_step": ms, "gflops": fl / (ms / 1e3) / 1e9, "rank": r, "rel_err": rel}
     return out
 
@@ -620,10 +645,25 @@ def compare_batched(eod, steps, warmup):
                 r, st = eod.factor_batched(mats, tol, w.seed, block_k=32, tol_mode="rel", precision=prec)
             torch.cuda.synchronize()
             dt = (time.perf_counter() - t0) / steps
+            # the fixed default of 8 worker streams beside the tuned count
+            os.environ["EOD_BATCH_STREAMS"] = "8"
+            try:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r8, _ = eod.factor_batched(mats, tol, w.seed, block_k=32, tol_mode="rel", precision=prec)
+                torch.cuda.synchronize()
+                dt8 = time.perf_counter() - t0
+                del r8
+            finally:
+                os.environ.pop("EOD_BATCH_STREAMS", None)
             ranks[form] = [x.rank for x in r]
             rels[form] = [x.rel_err for x in r]
             flops = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, 32, True) for a, x in zip(w.A, r))
             res[form] = {"fact_per_s": len(mats) / dt, "ms_per_batch": dt * 1e3, "gflops": flops / dt / 1e9,
+                         "workers": eod.tuning_lookup("batch_workers", len(mats),
+                                                      int(np.mean([a.shape[0] for a in w.A])),
+                                                      int(np.mean([a.shape[1] for a in w.A]))) or 8,
+                         "fact_per_s_fixed_8_workers": len(mats) / dt8,
                          "statuses_ok": all(x == 0 for x in st),
                          "rank_mean": float(np.mean(ranks[form])), "rank_max": int(np.max(ranks[form]))}
             del r
@@ -649,11 +689,12 @@ def run_reference(args):
     w = W.harmonic()
     A64 = np.asfortranarray(w.A.astype(np.float64))
     m, n = A64.shape
+    k = tuned_k("mixed", m, n)
     for _ in range(args.warmup):
-        oracle_whole(A64, w.tol, HEAD_K, w.seed, 0)
+        oracle_whole(A64, w.tol, k, w.seed, 0)
     secs, flops, r, cores = 0.0, 0.0, 0, 1
     for _ in range(args.steps):
-        v, el, r, cores = oracle_whole(A64, w.tol, HEAD_K, w.seed, 0)
+        v, el, r, cores = oracle_whole(A64, w.tol, k, w.seed, 0)
         secs += el
         flops += v * el * 1e9
     value = flops / secs / 1e9
@@ -671,10 +712,10 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded harmonic low-rank + noise; no dataset)",
-        "config": {"workload": WORKLOAD, "m": m, "n": n, "rank": r, "block_k": HEAD_K,
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "rank": r, "block_k": k,
                    "parallelism": f"host, {cores} threads"},
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                         "sample": _oracle_sample_text(cores, r)},
+                         "sample": _oracle_sample_text(cores, r, k)},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))

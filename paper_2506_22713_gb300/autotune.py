@@ -237,7 +237,7 @@ def main(argv=None):
         r, n = tune_batch_workers(eod, torch, candidates=(8, 16) if args.quick else (4, 8, 12, 16, 24, 32))
         rows += r
         notes += n
-    meta = {"when": datetime.datetime.utcnow().strftime("%Y-%m-%dT%H:%M:%SZ"),
+    meta = {"when": datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%dT%H:%M:%SZ"),
             "gpu": torch.cuda.get_device_name(0), "torch": torch.__version__,
             "seconds": f"{time.time() - t0:.0f}"}
     write_table(args.out, rows, notes, meta)

@@ -229,3 +229,22 @@ def test_pixel_batch_256_every_item_vs_oracle(eod, form):
     drel = max(abs(res[i].rel_err - refs[i]["rel_err"]) for i in range(256))
     assert drel <= RELERR_TOL[form], drel
     print(f"\n[pixel batch {form}] 256/256 ranks equal, max |dRelErr| = {drel:.3g}, recomputed {recomputed}")
+
+
+# ------------------------------------------------------ the autotuner's k --
+@pytest.mark.parametrize("form", ["mixed", "plain_f64"])
+def test_tuned_block_k_harmonic_8192_vs_oracle(eod, form):
+    """block_k = 0 takes the autotuner's k for the form and size (the table
+    shipped beside the library); the factorisation at that k still matches
+    the oracle run with the same k."""
+    w = W.harmonic()
+    code = {"mixed": 2, "plain_f64": 0}[form]
+    k = eod.tuning_lookup("block_k", code, 8192, 8192) or 32
+    A64 = w.A.astype(np.float64)
+    ref = _oracle(A64, w.tol, k, w.seed)
+    Ad64 = _to_dev(A64, np.float64)
+    A = Ad64 if form == "plain_f64" else _to_dev(w.A, np.float32)
+    f = eod.factor(A, w.tol, w.seed, block_k=0, tol_mode="rel", precision="plain" if form == "plain_f64" else form)
+    assert f.block_k == k
+    compare(f, ref, Ad64, form, f"harmonic8192 {form} tuned k={k}", signal=40)
+    f.close()
