@@ -62,28 +62,47 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
 #pragma unroll
         for (int j = 0; j < TPT; ++j) acc[i][j] = Acc(0);
 
-    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    // The next K tile's operands are loaded into registers while the
+    // current one is multiplied out of shared memory, so the global loads'
+    // latency overlaps the FMAs.
+    constexpr int QA = (BM * BK) / NT, QB = (BN * BK) / NT;
+    Acc ra[QA], rb[QB];
+    auto load_tile = [&](int64_t k0) {
 #pragma unroll
-        for (int q = 0; q < (BM * BK) / NT; ++q) {
+        for (int q = 0; q < QA; ++q) {
             const int e = tid + q * NT;
             int i, kk;
             if (!TRA) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
             const int64_t gi = m0 + i, gk = k0 + kk;
-            Acc v = Acc(0);
-            if (gi < M && gk < ke) v = (Acc)(TRA ? A[gk + gi * lda] : A[gi + gk * lda]);
-            As[kk][i] = v;
+            ra[q] = (gi < M && gk < ke) ? (Acc)(TRA ? A[gk + gi * lda] : A[gi + gk * lda]) : Acc(0);
         }
 #pragma unroll
-        for (int q = 0; q < (BN * BK) / NT; ++q) {
+        for (int q = 0; q < QB; ++q) {
             const int e = tid + q * NT;
             int j, kk;
             if (!TRB) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
             const int64_t gj = n0 + j, gk = k0 + kk;
-            Acc v = Acc(0);
-            if (gj < N && gk < ke) v = (Acc)(TRB ? B[gj + gk * ldb] : B[gk + gj * ldb]);
-            Bs[kk][j] = v;
+            rb[q] = (gj < N && gk < ke) ? (Acc)(TRB ? B[gj + gk * ldb] : B[gk + gj * ldb]) : Acc(0);
+        }
+    };
+    if (kb < ke) load_tile(kb);
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+        for (int q = 0; q < QA; ++q) {
+            const int e = tid + q * NT;
+            int i, kk;
+            if (!TRA) { i = e % BM; kk = e / BM; } else { kk = e % BK; i = e / BK; }
+            As[kk][i] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+            const int e = tid + q * NT;
+            int j, kk;
+            if (!TRB) { kk = e % BK; j = e / BK; } else { j = e % BN; kk = e / BN; }
+            Bs[kk][j] = rb[q];
         }
         __syncthreads();
+        if (k0 + BK < ke) load_tile(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             Acc a[TPT], b[TPT];

@@ -45,7 +45,10 @@ template <> struct GramAcc<float> {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-template <typename T>
+// MAXB: 4 x 4 blocks per thread, 1 while the upper triangle has at most GT
+// blocks (w <= 88), else 3 (w <= 128): the accumulators of the unused blocks
+// would otherwise hold registers and cap the CTAs per SM.
+template <typename T, int MAXB>
 __global__ void __launch_bounds__(GT) gram_partial_kernel(const T *__restrict__ Y, int64_t m, int w, int64_t ldy,
                                                           int64_t rows_per_cta, double *__restrict__ part) {
     extern __shared__ __align__(16) unsigned char gsm[];
@@ -57,7 +60,6 @@ __global__ void __launch_bounds__(GT) gram_partial_kernel(const T *__restrict__ 
     // rsplit-th row of the chunk; their sums are combined in shared memory
     const int rsplit = nblocks * 2 <= GT ? GT / nblocks : 1;
     const int grp = threadIdx.x / nblocks;     // valid when rsplit > 1
-    constexpr int MAXB = 3;                    // blocks per thread (w <= 128 -> 528 blocks)
     int bi[MAXB], bj[MAXB], nmine = 0;
     {
         int b0 = rsplit > 1 ? threadIdx.x % nblocks : threadIdx.x;
@@ -299,11 +301,15 @@ cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, in
     if (!part) return cudaErrorMemoryAllocation;
     size_t smem = sizeof(T) * (size_t)GR * (w + 1);
     if (smem < sizeof(double) * GT * 16) smem = sizeof(double) * GT * 16;   // room for the row-group sums
-    EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T>, (int)(sizeof(double) * GR * 129)));
+    const int nb4 = (w + 3) / 4;
+    const bool one = nb4 * (nb4 + 1) / 2 <= GT;
+    EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T, 1>, (int)(sizeof(double) * GR * 129)));
+    EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T, 3>, (int)(sizeof(double) * GR * 129)));
     ProfScope prof(std::is_same<T, float>::value ? PROF_GEMM_SIMT32 : PROF_GEMM_SIMT, (double)m * w * (w + 1),
                    (double)sizeof(T) * m * w, s);
     count_launch(2);
-    gram_partial_kernel<T><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
+    if (one) gram_partial_kernel<T, 1><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
+    else gram_partial_kernel<T, 3><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
     EOD_CUDA_TRY(cudaGetLastError());
     gram_reduce_kernel<<<(w * w + 31) / 32, 256, 0, s>>>(part, (int)ctas, w, G, ldg);
     EOD_CUDA_TRY(cudaGetLastError());
