@@ -59,6 +59,8 @@ def tuned_k(form, m, n, default=32):
     except OSError:
         pass
     return default
+
+
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2070 MHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 FP64_SM_PEAK_GFLOPS = FP64_PEAK_GFLOPS / 152

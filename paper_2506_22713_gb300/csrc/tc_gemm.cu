@@ -221,55 +221,81 @@ __global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kern
             __syncwarp();
         }
         if (leader) umma_commit(tmem_full);   // completes once every MMA issued above has finished
+    } else if (warp >= 2 && EPI == EPI_ERR) {
+        // ---------------- error epilogue ----------------
+        // Each thread owns one row of the tile.  The reference entries of a
+        // chunk of 32 columns are loaded before the accumulators are ready (the
+        // first chunk while the MMAs still run) and one chunk ahead of the
+        // arithmetic afterwards, so their latency overlaps the TMEM reads
+        // and the sums instead of following them.
+        constexpr int CW = 32;
+        const int q = warp & 3;
+        const int64_t row = m0 + 32 * q + lane;
+        const bool rin = row < p.M;
+        float rn[CW];
+        auto load_ref = [&](int c) {
+#pragma unroll
+            for (int j = 0; j < CW; ++j) {
+                const int64_t col = n0 + c + j;
+                rn[j] = (rin && col < p.N) ? __ldcs(p.R + row + col * p.ldr) : 0.0f;
+            }
+        };
+        load_ref(0);
+        const bool got = __all_sync(0xffffffffu, mbar_wait(tmem_full, 0) ? 1 : 0) != 0;
+        if (!got) atomicExch(p.err_flag, 1);
+        tc_fence_after();
+        double local = 0.0;
+        if (got && iters > 0) {
+#pragma unroll 1
+            for (int c = 0; c < BN_; c += CW) {
+                float rc[CW];
+#pragma unroll
+                for (int j = 0; j < CW; ++j) rc[j] = rn[j];
+                if (c + CW < BN_) load_ref(c + CW);
+                float v[CW];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c + 16), v + 16);
+                // residual in FP32 (the difference of two FP32 values), squares
+                // summed in FP32 over the 32 columns, FP64 across chunks
+                float part = 0.f;
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    const float d = (n0 + c + j < p.N) ? rc[j] - v[j] : 0.0f;
+                    part = fmaf(d, d, part);
+                }
+                if (rin) local += (double)part;
+            }
+        }
+        local = warp_sum(local);
+        __shared__ double red[4];
+        if (lane == 0) red[q] = local;
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
+        if (warp == 2 && lane == 0) p.errp[blockIdx.x + (int64_t)blockIdx.y * gridDim.x] = red[0] + red[1] + red[2] + red[3];
     } else if (warp >= 2) {
-        // ---------------- epilogue ----------------
+        // ---------------- store epilogue ----------------
         const int q = warp & 3;   // TMEM lane quarter this warp may access
         const bool got = __all_sync(0xffffffffu, mbar_wait(tmem_full, 0) ? 1 : 0) != 0;
         if (!got) atomicExch(p.err_flag, 1);
         tc_fence_after();
         const int64_t row = m0 + 32 * q + lane;
-        double local = 0.0;
         if (got && iters > 0) {
 #pragma unroll 1
             for (int c = 0; c < BN_; c += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c, v);
                 if (row < p.M) {
-                    if (EPI == EPI_STORE) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int64_t col = n0 + c + j;
-                            if (col < p.N) p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = v[j];
-                        }
-                    } else {
-                        // residual in FP32 (the difference of two FP32 values), squares
-                        // summed in FP32 over the 16 columns, FP64 across chunks
-                        float part = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int64_t col = n0 + c + j;
-                            if (col < p.N) {
-                                const float d = p.R[row + col * p.ldr] - v[j];
-                                part = fmaf(d, d, part);
-                            }
-                        }
-                        local += (double)part;
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t col = n0 + c + j;
+                        if (col < p.N) p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = v[j];
                     }
                 }
             }
-        } else if (EPI == EPI_STORE && iters == 0 && row < p.M) {
+        } else if (iters == 0 && row < p.M) {
             for (int c = 0; c < BN_; ++c) {
                 const int64_t col = n0 + c;
                 if (col < p.N) p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = 0.0f;
             }
-        }
-        if (EPI == EPI_ERR) {
-            local = warp_sum(local);
-            __shared__ double red[4];
-            if (lane == 0) red[q] = local;
-            asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
-            if (warp == 2 && lane == 0)
-                p.errp[blockIdx.x + (int64_t)blockIdx.y * gridDim.x] = red[0] + red[1] + red[2] + red[3];
         }
     }
     tc_fence_before();
