@@ -46,8 +46,9 @@ template <> struct GramAcc<float> {
 };
 
 // MAXB: 4 x 4 blocks per thread, 1 while the upper triangle has at most GT
-// blocks (w <= 88), else 3 (w <= 128): the accumulators of the unused blocks
-// would otherwise hold registers and cap the CTAs per SM.
+// blocks (w <= 88), 2 up to 2 GT (w <= 124), else 3 (w <= 128): the
+// accumulators of unused blocks would otherwise hold registers and cap the
+// CTAs per SM.
 template <typename T, int MAXB>
 __global__ void __launch_bounds__(GT) gram_partial_kernel(const T *__restrict__ Y, int64_t m, int w, int64_t ldy,
                                                           int64_t rows_per_cta, double *__restrict__ part) {
@@ -302,13 +303,16 @@ cudaError_t gram_skinny(const T *Y, int64_t m, int w, int64_t ldy, double *G, in
     size_t smem = sizeof(T) * (size_t)GR * (w + 1);
     if (smem < sizeof(double) * GT * 16) smem = sizeof(double) * GT * 16;   // room for the row-group sums
     const int nb4 = (w + 3) / 4;
-    const bool one = nb4 * (nb4 + 1) / 2 <= GT;
+    const int nblk = nb4 * (nb4 + 1) / 2;
+    const int maxb = nblk <= GT ? 1 : (nblk <= 2 * GT ? 2 : 3);
     EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T, 1>, (int)(sizeof(double) * GR * 129)));
+    EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T, 2>, (int)(sizeof(double) * GR * 129)));
     EOD_CUDA_TRY(set_smem_once(gram_partial_kernel<T, 3>, (int)(sizeof(double) * GR * 129)));
     ProfScope prof(std::is_same<T, float>::value ? PROF_GEMM_SIMT32 : PROF_GEMM_SIMT, (double)m * w * (w + 1),
                    (double)sizeof(T) * m * w, s);
     count_launch(2);
-    if (one) gram_partial_kernel<T, 1><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
+    if (maxb == 1) gram_partial_kernel<T, 1><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
+    else if (maxb == 2) gram_partial_kernel<T, 2><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
     else gram_partial_kernel<T, 3><<<(unsigned)ctas, GT, smem, s>>>(Y, m > 0 ? m : 0, w, ldy, rows_per, part);
     EOD_CUDA_TRY(cudaGetLastError());
     gram_reduce_kernel<<<(w * w + 31) / 32, 256, 0, s>>>(part, (int)ctas, w, G, ldg);
