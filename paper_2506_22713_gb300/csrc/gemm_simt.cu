@@ -40,12 +40,21 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
                  double *__restrict__ errp, unsigned *__restrict__ tile_count)
 {
     constexpr int BM = TS, BN = TS, TPT = TS / 16;   // outputs per thread along each axis
-    __shared__ Acc As[BK][BM + 1];
-    __shared__ Acc Bs[BK][BN + 1];
+    // FP32 tiles of 64 and 128: each thread owns runs of four consecutive
+    // rows (and columns), read from shared memory as float4 (one 128-bit
+    // load per four FMAs-rows instead of four 32-bit ones); the rows are
+    // padded by 4 to keep those loads 16-byte aligned.  Otherwise a thread's
+    // outputs are 16 apart.
+    constexpr bool VEC = std::is_same<Acc, float>::value && TS >= 64;
+    constexpr int PAD = VEC ? 4 : 1;
+    __shared__ __align__(16) Acc As[BK][BM + PAD];
+    __shared__ __align__(16) Acc Bs[BK][BN + PAD];
     __shared__ double red[32];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    // tile-local row of the thread's i-th output (column: same with ty)
+    auto lo = [&](int t, int i) -> int { return VEC ? ((i >> 2) * 64 + t * 4 + (i & 3)) : (t + 16 * i); };
 
     if ((flags & F_UPPER_ONLY) && m0 > n0 + BN - 1) {
         if (EPI == EPI_ERR && tid == 0) errp[blockIdx.x + (int64_t)blockIdx.y * gridDim.x] = 0.0;
@@ -107,9 +116,20 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
         for (int kk = 0; kk < BK; ++kk) {
             Acc a[TPT], b[TPT];
 #pragma unroll
-            for (int i = 0; i < TPT; ++i) a[i] = As[kk][tx + 16 * i];
+            if constexpr (VEC) {
 #pragma unroll
-            for (int j = 0; j < TPT; ++j) b[j] = Bs[kk][ty + 16 * j];
+                for (int h = 0; h < TPT / 4; ++h) {
+                    const float4 av = *reinterpret_cast<const float4 *>(&As[kk][h * 64 + tx * 4]);
+                    const float4 bv = *reinterpret_cast<const float4 *>(&Bs[kk][h * 64 + ty * 4]);
+                    a[4 * h] = av.x; a[4 * h + 1] = av.y; a[4 * h + 2] = av.z; a[4 * h + 3] = av.w;
+                    b[4 * h] = bv.x; b[4 * h + 1] = bv.y; b[4 * h + 2] = bv.z; b[4 * h + 3] = bv.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < TPT; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+                for (int j = 0; j < TPT; ++j) b[j] = Bs[kk][ty + 16 * j];
+            }
 #pragma unroll
             for (int i = 0; i < TPT; ++i)
 #pragma unroll
@@ -122,11 +142,11 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
         Acc *dst = part + (int64_t)blockIdx.z * M * N;
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
-            const int64_t col = n0 + ty + 16 * j;
+            const int64_t col = n0 + lo(ty, j);
             if (col >= N) continue;
 #pragma unroll
             for (int i = 0; i < TPT; ++i) {
-                const int64_t row = m0 + tx + 16 * i;
+                const int64_t row = m0 + lo(tx, i);
                 if (row < M) dst[row + col * M] = acc[i][j];
             }
         }
@@ -157,21 +177,21 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
             const Acc *src = part + (int64_t)z * M * N;
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
-                const int64_t col = n0 + ty + 16 * j;
+                const int64_t col = n0 + lo(ty, j);
 #pragma unroll
                 for (int i = 0; i < TPT; ++i) {
-                    const int64_t row = m0 + tx + 16 * i;
+                    const int64_t row = m0 + lo(tx, i);
                     if (row < M && col < N) sum[i][j] += __ldcg(src + row + col * M);
                 }
             }
         }
 #pragma unroll
         for (int j = 0; j < TPT; ++j) {
-            const int64_t col = n0 + ty + 16 * j;
+            const int64_t col = n0 + lo(ty, j);
             if (col >= N) continue;
 #pragma unroll
             for (int i = 0; i < TPT; ++i) {
-                const int64_t row = m0 + tx + 16 * i;
+                const int64_t row = m0 + lo(tx, i);
                 if (row >= M) continue;
                 Acc v = alpha * sum[i][j];
                 if (beta != Acc(0)) v = fma(beta, (Acc)C[row + col * ldc], v);
@@ -183,11 +203,11 @@ gemm_simt_kernel(int64_t M, int64_t N, int64_t K, Acc alpha, const TA *__restric
     double local = 0.0;
 #pragma unroll
     for (int j = 0; j < TPT; ++j) {
-        const int64_t col = n0 + ty + 16 * j;
+        const int64_t col = n0 + lo(ty, j);
         if (col >= N) continue;
 #pragma unroll
         for (int i = 0; i < TPT; ++i) {
-            const int64_t row = m0 + tx + 16 * i;
+            const int64_t row = m0 + lo(tx, i);
             if (row >= M) continue;
             Acc v = alpha * acc[i][j];
             if (EPI == EPI_STORE) {
