@@ -185,8 +185,11 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            # the first sample comes a few hundred ms after the start: let it
+            # begin before the (short) timed region
+            time.sleep(0.5)
         except Exception:
             self.proc = None
 
