@@ -228,6 +228,9 @@ template <typename T>
 cudaError_t fro_norm(const T *A, int64_t m, int64_t n, int64_t lda, double *out,
                      int *flag, Scratch *ws, cudaStream_t s);
 // out = sqrt(sum(partials[0..count))) / denom (denom read from device pointer or 1)
+// out[0] = sqrt(sum of the count partials); flag[0] |= any of the flags
+cudaError_t finalize_norm(const double *partials, const int *flags, int64_t count, double *out, int *flag,
+                          cudaStream_t s);
 cudaError_t finalize_sqrt_sum(const double *partials, int64_t count, const double *denom,
                               double *out, cudaStream_t s);
 // Omega columns col0.. into out (n x ncols, ld n) in type T (values are BF16-exact)

@@ -74,10 +74,10 @@ constexpr int kMaxPowerIters = 16;
 
 // Second CholQR pass on a near-identity Gram I + E: the first-order factor
 // I + Phi(E) is exact to O(||E||^2) and replaces the factorisation (see
-// chol_small) when that is below the data's rounding: ||E||_F <= 1e-8 for
-// FP64 data (O(E^2) <= 1e-16), ||E||_F <= 3.2e-5 for FP32 data (O(E^2) <=
-// 1e-9, under the FP32 unit roundoff 6e-8).
-template <typename T> constexpr double near_id_tau2() { return std::is_same<T, double>::value ? 1e-16 : 1e-9; }
+// chol_small) when that is at or below the data's rounding: ||E||_F <= 1e-8
+// for FP64 data (O(E^2) <= 1e-16), ||E||_F <= 2e-4 for FP32 data (O(E^2) <=
+// 4e-8, the FP32 unit roundoff being 6e-8).
+template <typename T> constexpr double near_id_tau2() { return std::is_same<T, double>::value ? 1e-16 : 4e-8; }
 
 // smallest eps / ||A||_F the FP32-data paths accept (see factor_impl)
 constexpr double kMixedFloor = 1e-5;
@@ -415,10 +415,15 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     double *d_norm = dsc, *d_t = dsc + 1, *d_err = dsc + 2;
 
     // ---- S0: ||A||_F and finiteness ----
+    // (the BF16 mixed form takes both from its split pass over A: one read of
+    // A for the two)
+    MixedOps<T> mx;
+    const bool norm_in_split = mixed && o.precision == EOD_MIXED_BF16;
     {
         Phase ph_norm("eod.norm");
         EOD_CU(cudaMemsetAsync(iflag, 0, sizeof(int) * 4, s));
-        EOD_CU(fro_norm<T>(A, m, n, lda, d_norm, iflag, &ws, s));
+        if (norm_in_split) EOD_TRY(mx.prepare(A, m, n, lda, k, ar, &ws, s, false, d_norm, iflag));
+        else EOD_CU(fro_norm<T>(A, m, n, lda, d_norm, iflag, &ws, s));
         EOD_CU(cudaMemcpyAsync(hm.val, d_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
         EOD_CU(cudaMemcpyAsync(hm.flag, iflag, sizeof(int), cudaMemcpyDeviceToHost, s));
         EOD_CU(cudaStreamSynchronize(s));
@@ -437,8 +442,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     F->eps = eps;
     F->block_k = k;
 
-    MixedOps<T> mx;
-    if (mixed) EOD_TRY(mx.prepare(A, m, n, lda, k, ar, &ws, s, o.precision == EOD_MIXED_TF32));
+    if (mixed && !norm_in_split) EOD_TRY(mx.prepare(A, m, n, lda, k, ar, &ws, s, o.precision == EOD_MIXED_TF32));
 
     OzCache oz;
     oz.on = std::is_same<T, double>::value && fp64_use_emulated(m, k, n);

@@ -48,7 +48,7 @@ static int stream_blocks(int64_t total) {
 }
 
 eod_status MixedOps<float>::prepare(const float *A_, int64_t m_, int64_t n_, int64_t lda_, int64_t k_, Arena &ar_,
-                                    Scratch *ws_, cudaStream_t s, bool tf32_) {
+                                    Scratch *ws_, cudaStream_t s, bool tf32_, double *d_norm, int *d_flag) {
     A = A_;
     m = m_;
     n = n_;
@@ -78,7 +78,15 @@ eod_status MixedOps<float>::prepare(const float *A_, int64_t m_, int64_t n_, int
     MX_ST(ar->get(&Ahi, (size_t)ldm8 * n));
     MX_ST(ar->get(&Alo, (size_t)ldm8 * n));
     MX_ST(ar->get(&A3, (size_t)ldm8 * n));
-    MX_TRY(split_norm(A, m, n, lda, Ahi, Alo, ldm8, nullptr, nullptr, stream_blocks(m * n), s, A3));
+    const int blocks = stream_blocks(m * n);
+    double *part = nullptr;
+    int *pflag = nullptr;
+    if (d_norm) {
+        MX_ST(ar->get(&part, (size_t)blocks));
+        MX_ST(ar->get(&pflag, (size_t)blocks));
+    }
+    MX_TRY(split_norm(A, m, n, lda, Ahi, Alo, ldm8, part, pflag, blocks, s, A3));
+    if (d_norm) MX_TRY(finalize_norm(part, pflag, blocks, d_norm, d_flag, s));
     MX_ST(ar->get(&Om, (size_t)ldn8 * win_cap));
     return EOD_OK;
 }

@@ -240,6 +240,13 @@ cudaError_t fro_norm(const T *A, int64_t m, int64_t n, int64_t lda, double *out,
     return cudaSuccess;
 }
 
+cudaError_t finalize_norm(const double *partials, const int *flags, int64_t count, double *out, int *flag,
+                          cudaStream_t s) {
+    count_launch();
+    finalize_norm_kernel<<<1, 1024, 0, s>>>(partials, flags, count, out, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t finalize_sqrt_sum(const double *partials, int64_t count, const double *denom, double *out,
                               cudaStream_t s) {
     count_launch();

@@ -65,7 +65,8 @@ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // types never reach the tensor cores (FP64 input is narrowed to FP32 first).
 template <typename T>
 struct MixedOps {
-    eod_status prepare(const T *, int64_t, int64_t, int64_t, int64_t, Arena &, Scratch *, cudaStream_t, bool) {
+    eod_status prepare(const T *, int64_t, int64_t, int64_t, int64_t, Arena &, Scratch *, cudaStream_t, bool,
+                       double * = nullptr, int * = nullptr) {
         return EOD_EUNSUPPORTED;
     }
     eod_status sketch(int64_t, int64_t, uint64_t, uint64_t, T *, int64_t, cudaStream_t) { return EOD_EUNSUPPORTED; }
@@ -94,8 +95,10 @@ struct MixedOps<float> {
     int64_t win_cap = 0, win_c0 = -1, win_w = 0, next_w = 0;
     int *err_flag = nullptr;
 
+    // splits A; with d_norm (BF16 form only) the same pass also gives
+    // ||A||_F into d_norm and ORs the non-finite flag into d_flag
     eod_status prepare(const float *A, int64_t m, int64_t n, int64_t lda, int64_t k, Arena &ar, Scratch *ws,
-                       cudaStream_t s, bool tf32);
+                       cudaStream_t s, bool tf32, double *d_norm = nullptr, int *d_flag = nullptr);
     eod_status sketch(int64_t col0, int64_t f, uint64_t seed, uint64_t batch, float *Y, int64_t ldy, cudaStream_t s);
     eod_status project(const float *Q, int64_t r, float *Ct, cudaStream_t s);
     // buffers from the arena on `s`; the kernels run on `run` (which may be
