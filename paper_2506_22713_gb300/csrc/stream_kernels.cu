@@ -6,6 +6,8 @@
 #include "instrument.cuh"
 
 #include <cuda.h>
+#include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 namespace eod {
@@ -54,7 +56,8 @@ __device__ __forceinline__ double omega_value_f64(uint32_t x0, uint32_t x1) {
 // ulps of g; if no BF16 rounding midpoint lies within twice that distance of
 // the FP32 result, both roundings agree and the FP32 value is returned,
 // otherwise the FP64 formula decides.
-__device__ __forceinline__ double omega_value_fast(uint64_t seed, uint32_t row, uint32_t col, uint32_t batch) {
+template <typename T>
+__device__ __forceinline__ T omega_value_fast(uint64_t seed, uint32_t row, uint32_t col, uint32_t batch) {
     uint32_t c[4] = {row, col, batch, 0u};
     philox_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     const uint32_t x0 = c[0], x1 = c[1];
@@ -70,23 +73,24 @@ __device__ __forceinline__ double omega_value_fast(uint64_t seed, uint32_t row, 
     const float g = sqrtf(L) * cs;
     const int low = (int)(__float_as_uint(g) & 0xFFFFu);
     const float guard = 26.f / fabsf(cs) + 12.f;
-    if (fabsf((float)(low - 0x8000)) > guard && isfinite(g))
-        return (double)__bfloat162float(__float2bfloat16_rn(g));
-    return omega_value_f64(x0, x1);
+    if (fabsf((float)(low - 0x8000)) > guard && isfinite(g)) {
+        // the BF16 value itself, converted without an FP64 instruction
+        const __nv_bfloat16 b = __float2bfloat16_rn(g);
+        if constexpr (std::is_same<T, __nv_bfloat16>::value) return b;
+        else return (T)__bfloat162float(b);
+    }
+    const double v = omega_value_f64(x0, x1);   // exactly a BF16 value
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) return __float2bfloat16_rn((float)v);
+    else return (T)v;
 }
 
-template <typename T> __device__ __forceinline__ T from_f64(double x) { return (T)x; }
-template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
-
+// Columns from blockIdx.y, rows from blockIdx.x: no index division per entry.
 template <typename T>
 __global__ void omega_kernel(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, uint32_t batch,
                              T *out, int64_t ldo) {
-    const int64_t total = n * ncols;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % n, c = e / n;
-        out[i + c * ldo] = from_f64<T>(omega_value_fast(seed, (uint32_t)i, (uint32_t)(col0 + c), batch));
-    }
+    for (int64_t c = blockIdx.y; c < ncols; c += gridDim.y)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            out[i + c * ldo] = omega_value_fast<T>(seed, (uint32_t)i, (uint32_t)(col0 + c), batch);
 }
 
 // ------------------------------------------------------------- norms ----
@@ -218,7 +222,9 @@ cudaError_t omega_fill(int64_t n, int64_t col0, int64_t ncols, uint64_t seed, ui
     if (n <= 0 || ncols <= 0) return cudaSuccess;
     ProfScope prof(PROF_OMEGA, 0.0, (double)sizeof(T) * n * ncols, s);
     count_launch();
-    omega_kernel<T><<<grid_for(n * ncols), 256, 0, s>>>(n, col0, ncols, seed, (uint32_t)batch, out, ldo);
+    const int gx = (int)std::min<int64_t>((n + 255) / 256, 64);
+    const int gy = (int)std::min<int64_t>(ncols, std::max<int64_t>(1, 4LL * kNumSMs * 4 / gx));
+    omega_kernel<T><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(n, col0, ncols, seed, (uint32_t)batch, out, ldo);
     return cudaGetLastError();
 }
 
