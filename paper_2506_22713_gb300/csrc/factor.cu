@@ -475,11 +475,16 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
         if (e != cudaSuccess) return e;
         return oz_slice(Qd + c0 * m, m, cnt, 1, m, (uint16_t *)oz.Qr + c0, nullptr, 1, oz.cap8, m * oz.cap8, s);
     };
-    // slices of a small B operand (rows x K, X(r, k) at X[r*sr + k*sk]) into oz.Bt
-    auto oz_small = [&](const T *X, int64_t rows, int64_t K, int64_t sr, int64_t sk, OzOperand &out) -> cudaError_t {
+    // slices of a small B operand (rows x K, X(r, k) at X[r*sr + k*sk]) into
+    // bt / ebt (oz.Bt on the main stream) on stream st
+    auto oz_small_to = [&](const T *X, int64_t rows, int64_t K, int64_t sr, int64_t sk, void *bt, int *ebt,
+                           cudaStream_t st, OzOperand &out) -> cudaError_t {
         const int64_t ldk = round_up8(K);
-        out = {oz.Bt, oz.eBt, 0, ldk, rows * ldk};
-        return oz_slice((const double *)X, rows, K, sr, sk, oz.Bt, oz.eBt, 0, ldk, rows * ldk, s);
+        out = {bt, ebt, 0, ldk, rows * ldk};
+        return oz_slice((const double *)X, rows, K, sr, sk, bt, ebt, 0, ldk, rows * ldk, st);
+    };
+    auto oz_small = [&](const T *X, int64_t rows, int64_t K, int64_t sr, int64_t sk, OzOperand &out) -> cudaError_t {
+        return oz_small_to(X, rows, K, sr, sk, oz.Bt, oz.eBt, s, out);
     };
 
     // ---- Alg. 1 ----
@@ -494,50 +499,148 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     bool stop = (norm_a == 0.0);
     if (stop) tdiag.push_back(0.0);
 
+    // One projection pass Yc <- Yc - Q(:, q0:q1) (Q(:, q0:q1)^T Yc) on stream
+    // st with its own workspace and slice buffer (step 4 of Alg. 1).
+    auto deflate = [&](T *Yc, int64_t wdt, int64_t q0, int64_t q1, T *Sb, Scratch *w, void *bt, int *ebt,
+                       cudaStream_t st) -> cudaError_t {
+        const int64_t nq = q1 - q0;
+        if (nq <= 0) return cudaSuccess;
+        const T *Qq = Qb + q0 * m;
+        cudaError_t e;
+        if (oz.on && fp64_use_emulated(nq, wdt, m)) {
+            OzOperand bo;
+            e = oz_small_to(Yc, wdt, m, m, 1, bt, ebt, st, bo);
+            if (e != cudaSuccess) return e;
+            const OzOperand qc{(const uint16_t *)oz.Qc + q0 * oz.m8, oz.eQc + q0, 0, oz.m8, cap * oz.m8};
+            e = oz_gemm_ops(qc, bo, nq, wdt, m, 1.0, 0.0, (double *)Sb, cap, ex, w->err_flag, st);
+        } else {
+            e = gemm<T, T, T, T>(true, false, nq, wdt, m, 1.0, Qq, m, Yc, m, 0.0, Sb, cap, ex, w, st);
+        }
+        if (e != cudaSuccess) return e;
+        if (oz.on && fp64_use_emulated(m, wdt, nq) && q0 % 8 == 0) {
+            OzOperand bo;
+            e = oz_small_to(Sb, wdt, nq, cap, 1, bt, ebt, st, bo);
+            if (e != cudaSuccess) return e;
+            const OzOperand qr{(const uint16_t *)oz.Qr + q0, nullptr, 1, oz.cap8, m * oz.cap8};
+            return oz_gemm_ops(qr, bo, m, wdt, nq, -1.0, 1.0, (double *)Yc, m, ex, w->err_flag, st);
+        }
+        return gemm<T, T, T, T>(false, false, m, wdt, nq, -1.0, Qq, m, Sb, cap, 1.0, Yc, m, ex, w, st);
+    };
+    // Y_j = A Omega_j for the block of global Omega columns col0 .. col0+f-1
+    auto sketch = [&](int64_t col0, int64_t f, T *Yd, T *Omd, Scratch *w, void *bt, int *ebt,
+                      cudaStream_t st) -> eod_status {
+        if (mixed) {
+            Scratch *keep_ws = mx.ws;
+            mx.ws = w;
+            const eod_status r = mx.sketch(col0, f, seed, o.batch_index, Yd, m, st);
+            mx.ws = keep_ws;
+            return r;
+        }
+        EOD_CU(omega_fill<T>(n, col0, f, seed, o.batch_index, Omd, n, st));
+        if (oz.on) {
+            OzOperand bo;
+            EOD_CU(oz_small_to(Omd, f, n, n, 1, bt, ebt, st, bo));
+            EOD_CU(oz_gemm_ops(oz.arow(), bo, m, f, n, 1.0, 0.0, (double *)Yd, m, ex, w->err_flag, st));
+        } else {
+            EOD_CU((gemm<T, T, T, T>(false, false, m, f, n, 1.0, A, lda, Omd, n, 0.0, Yd, m, ex, w, st)));
+        }
+        return EOD_OK;
+    };
+
+    // Lookahead across blocks: while block j's Gram and rank-test leaf run
+    // (one CTA), the next block is sketched and given its first projection
+    // pass against the basis that existed before block j, on a side stream
+    // with its own buffers; block j+1 then only projects out block j's own
+    // columns before its second pass (the same BCGS2 result in exact
+    // arithmetic: the two groups of columns are orthogonal).
+    // (only where the sketch has work enough to hide: for small problems the
+    // extra buffers and events cost more than the leaf they overlap;
+    // EOD_LOOKAHEAD=0 / 1 turns it off / on regardless of size)
+    cudaStream_t s2 = cap > k ? side_stream() : nullptr;
+    bool lookahead = s2 != nullptr && s2 != s && (double)m * (double)n >= 4.0e6;
+    if (const char *env = std::getenv("EOD_LOOKAHEAD")) lookahead = s2 != nullptr && s2 != s && env[0] == '1';
+    T *Y2 = nullptr, *S2 = nullptr, *Om2 = nullptr;
+    void *Bt2 = nullptr;
+    int *eBt2 = nullptr;
+    Scratch ws2;
+    JoinOnExit join_la;
+    if (lookahead) {
+        EOD_TRY(ar.get(&Y2, (size_t)m * k));
+        EOD_TRY(ar.get(&S2, (size_t)cap * k));
+        EOD_TRY(ar.get(&Om2, (size_t)n * k));
+        EOD_TRY(ar.get((char **)&ws2.base, ws_bytes));
+        ws2.size = ws_bytes;
+        ws2.err_flag = ws.err_flag;
+        ws2.tile_count_n = kTileCounters;
+        EOD_TRY(ar.get(&ws2.tile_count, (size_t)kTileCounters));
+        EOD_CU(cudaMemsetAsync(ws2.tile_count, 0, sizeof(unsigned) * kTileCounters, s));
+        if (oz.on) {
+            EOD_TRY(ar.get((uint16_t **)&Bt2, (size_t)oz.bt_elems));
+            EOD_TRY(ar.get(&eBt2, (size_t)std::max(m, n)));
+        }
+        join_la.main = s;
+        join_la.side = s2;
+    }
+    bool ahead = false;          // Y2 holds the block at ahead_col0, projected once against Q(:, 0:ahead_q)
+    int64_t ahead_col0 = -1, ahead_q = 0;
+
     while (!stop && kept < cap) {
         const int64_t f = std::min(k, cap - kept);
         ++blocks;
         // steps 3-4: Omega_j and Y = A Omega_j
         Phase ph_block("eod.basis_ext_block");
-        if (mixed) {
-            EOD_TRY(mx.sketch(kept, f, seed, o.batch_index, Y, m, s));
+        const bool from_ahead = ahead && ahead_col0 == kept;
+        if (ahead) EOD_CU(stream_after(s, s2));
+        if (from_ahead) {
+            std::swap(Y, Y2);
         } else {
-            EOD_CU(omega_fill<T>(n, kept, f, seed, o.batch_index, Om, n, s));
-            if (oz.on) {
-                OzOperand bo;
-                EOD_CU(oz_small(Om, f, n, n, 1, bo));
-                EOD_CU(oz_gemm_ops(oz.arow(), bo, m, f, n, 1.0, 0.0, (double *)Y, m, ex, ws.err_flag, s));
-            } else {
-                EOD_CU((gemm<T, T, T, T>(false, false, m, f, n, 1.0, A, lda, Om, n, 0.0, Y, m, ex, &ws, s)));
-            }
+            EOD_TRY(sketch(kept, f, Y, Om, &ws, oz.on ? oz.Bt : nullptr, oz.on ? oz.eBt : nullptr, s));
         }
+        ahead = false;
+        const int64_t kept_block = kept;   // the basis this block starts from
         int64_t cur = 0;
         while (!stop && cur < f) {
             T *Yc = Y + cur * m;
             const int64_t wdt = f - cur;
             // step 4: Y <- (I - Q Q^T) Y, twice
-            for (int pass = 0; pass < 2 && kept > 0; ++pass) {
-                if (oz.on && fp64_use_emulated(kept, wdt, m)) {
-                    OzOperand bo;
-                    EOD_CU(oz_small(Yc, wdt, m, m, 1, bo));
-                    const OzOperand qc{oz.Qc, oz.eQc, 0, oz.m8, cap * oz.m8};
-                    EOD_CU(oz_gemm_ops(qc, bo, kept, wdt, m, 1.0, 0.0, (double *)S, cap, ex, ws.err_flag, s));
-                } else {
-                    EOD_CU((gemm<T, T, T, T>(true, false, kept, wdt, m, 1.0, Qb, m, Yc, m, 0.0, S, cap, ex, &ws, s)));
-                }
-                if (oz.on && fp64_use_emulated(m, wdt, kept)) {
-                    OzOperand bo;
-                    EOD_CU(oz_small(S, wdt, kept, cap, 1, bo));
-                    const OzOperand qr{oz.Qr, nullptr, 1, oz.cap8, m * oz.cap8};
-                    EOD_CU(oz_gemm_ops(qr, bo, m, wdt, kept, -1.0, 1.0, (double *)Yc, m, ex, ws.err_flag, s));
-                } else {
-                    EOD_CU((gemm<T, T, T, T>(false, false, m, wdt, kept, -1.0, Qb, m, S, cap, 1.0, Yc, m, ex, &ws, s)));
+            if (cur == 0 && from_ahead) {
+                // the first pass's rest: the columns added since the lookahead
+                // (from a multiple of 8 for the sliced Q; the overlap is only
+                // projected twice), then the second pass
+                EOD_CU(deflate(Yc, wdt, ahead_q & ~(int64_t)7, kept, S, &ws, oz.on ? oz.Bt : nullptr,
+                               oz.on ? oz.eBt : nullptr, s));
+                EOD_CU(deflate(Yc, wdt, 0, kept, S, &ws, oz.on ? oz.Bt : nullptr, oz.on ? oz.eBt : nullptr, s));
+            } else {
+                for (int pass = 0; pass < 2 && kept > 0; ++pass)
+                    EOD_CU(deflate(Yc, wdt, 0, kept, S, &ws, oz.on ? oz.Bt : nullptr, oz.on ? oz.eBt : nullptr, s));
+            }
+            // the lookahead: Y2 free (its last use, the swap above, is on s)
+            // and Q(:, 0:kept_block) final before this point of s
+            const bool launch_ahead = lookahead && cur == 0 && kept_block + f < cap;
+            cudaEvent_t ev_ready = nullptr;
+            if (launch_ahead) {
+                EOD_CU(cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming));
+                cudaError_t e = cudaEventRecord(ev_ready, s);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(ev_ready);
+                    EOD_CU(e);
                 }
             }
             // step 5 (pass 1) + steps 6-11: Gram, Cholesky with the rank test
             EOD_CU(gram_skinny<T>(Yc, m, (int)wdt, m, G, k, &ws, s));
             EOD_CU(chol_small(G, k, (int)wdt, 1, eps2, delta_coef, Traits<T>::rho, 0.0, R1, k, R1i, k, info, s));
             EOD_CU(cudaMemcpyAsync(hm.info, info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+            if (launch_ahead) {
+                const int64_t c1 = kept_block + f, f1 = std::min(k, cap - c1);
+                cudaError_t e = cudaStreamWaitEvent(s2, ev_ready, 0);
+                cudaEventDestroy(ev_ready);
+                EOD_CU(e);
+                EOD_TRY(sketch(c1, f1, Y2, Om2, &ws2, Bt2, eBt2, s2));
+                EOD_CU(deflate(Y2, f1, 0, kept_block, S2, &ws2, Bt2, eBt2, s2));
+                ahead = true;
+                ahead_col0 = c1;
+                ahead_q = kept_block;
+            }
             EOD_CU(cudaStreamSynchronize(s));
             const int p = hm.info[0], code = hm.info[1];
             if (p > 0) {
@@ -607,6 +710,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
             }
         }
     }
+    if (ahead) EOD_CU(stream_after(s, s2));   // an unused lookahead: its buffers are shared after this
     const int64_t r = kept;
     F->rank = r;
     F->blocks = blocks;

@@ -65,6 +65,7 @@ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 // types never reach the tensor cores (FP64 input is narrowed to FP32 first).
 template <typename T>
 struct MixedOps {
+    Scratch *ws = nullptr;
     eod_status prepare(const T *, int64_t, int64_t, int64_t, int64_t, Arena &, Scratch *, cudaStream_t, bool,
                        double * = nullptr, int * = nullptr) {
         return EOD_EUNSUPPORTED;
