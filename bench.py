@@ -68,7 +68,7 @@ FP64_SM_PEAK_GFLOPS = FP64_PEAK_GFLOPS / 152
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.070
 L2_BYTES = 129 * 1024 * 1024
 # kernel kinds of the library's profile counters, in PROF_* order
-KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm", "oz_slice", "gemm_simt_f32"]
+KINDS = ["gemm_simt", "chol", "omega", "stream", "tc_gemm", "oz_gemm", "oz_slice", "gemm_simt_f32", "batch"]
 # BF16 slice-pair products per emulated FP64 multiply-add (8 slices, s + t <= 7)
 OZ_PAIRS = 36
 

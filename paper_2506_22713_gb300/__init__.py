@@ -171,7 +171,7 @@ eod_abe_debug_f64_gemm = _lib.eod_abe_debug_f64_gemm
 eod_abe_debug_chol = _lib.eod_abe_debug_chol
 
 (PROF_GEMM_SIMT, PROF_CHOL, PROF_OMEGA, PROF_STREAM, PROF_TC_GEMM, PROF_OZ_GEMM, PROF_OZ_SLICE,
- PROF_GEMM_SIMT32) = range(8)
+ PROF_GEMM_SIMT32, PROF_BATCH) = range(9)
 
 
 def profile_read(kind: int) -> dict:

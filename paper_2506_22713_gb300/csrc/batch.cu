@@ -1,0 +1,876 @@
+// The batched form in one persistent launch: many matrices of uneven sizes
+// and ranks (the per-image use of Sec. 4.1) factored by a kernel whose CTAs
+// take matrices from an atomic work queue, largest first, and run the whole
+// method on each one without returning to the host: ||A||_F (the RelErr
+// denominator, and eps in relative mode), Alg. 1 with its block loop and its
+// stop decision on the device (Omega_j, Y = A Omega_j, Y <- (I - Q Q^T) Y
+// twice, CholQR2 with the rank test folded into the first Cholesky, the
+// explicit residual for undecided pivots), Alg. 2 steps 8-11 (C^T = A^T Q,
+// C^T = V R, R^T = Qh D, U = Q Qh) and ||A - Q C||_F.
+//
+// One CTA (512 threads, one per SM) owns an item from start to end: a CTA
+// never waits for another, so there is no inter-CTA wait of any kind.  The
+// arithmetic is that of the FP32 forms of the single-matrix path: FP32
+// products with FP32 accumulation, Grams formed from exact FP32 products
+// summed by TwoSum into FP64 values, FP64 Cholesky (the same leaf
+// factorisation, chol_leaf.cuh) and FP64 products of triangular factors.
+//
+// Capacity: an item keeps at most kPRcap = 128 basis columns (the core's
+// Cholesky is one leaf of width r).  An item whose rank would exceed it, or
+// whose core Gram is too ill-conditioned for unshifted CholQR, stops with
+// kPFallback and the host factors it with the single-matrix path.
+#include "common.cuh"
+#include "chol_leaf.cuh"
+#include "omega.cuh"
+#include "instrument.cuh"
+#include "batch.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+namespace eod {
+namespace {
+
+constexpr int PT = kLeafThreads;   // threads per CTA (the leaf's CTA size)
+static_assert(PT == 512, "the tile shapes below assume 512 threads");
+
+// ------------------------------------------------------------ FP32 GEMM ----
+// C = alpha op(A) op(B) + beta C on one CTA, FP32 accumulation.
+//   op(A) M x K: TA = false: A(i, k) at A[i + k lda]; TA = true: A[k + i lda]
+//   op(B) K x N: TB = false: B(k, j) at B[k + j ldb]; TB = true: B[j + k ldb]
+// Tiles of BM x BN (BN = 64: 128 x 64; BN = 32: 256 x 32), K steps of 16
+// through a three-stage ring of shared buffers filled by 4-byte cp.async
+// copies (two steps in flight while one is multiplied; one barrier per
+// step); each thread owns a 4 x 4 block of the tile.  ERR: no store; the thread adds
+// (ref(i, j) - alpha acc(i, j))^2 to *ss instead (the reconstruction error,
+// each square exact, summed by TwoSum).  COMP: the 16-term partial sum of
+// each K step is added to a TwoSum pair (hi, lo) instead of running on in
+// one FP32 accumulator, so a long dot product (K = m or n) carries the
+// rounding of 16-term sums rather than of K-term ones: those errors, in the
+// sketch and in the projections against Q, are what the singular-value
+// decay amplifies into the basis (about u sqrt(K) s_1 / s_r).
+constexpr int GK = 16;
+
+// Exact FP32 products summed by TwoSum: s + c carries the sum of the exact
+// products to about 2^-46 relative, at FP32 ALU rates.
+struct TwoSumAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float e = fmaf(a, b, -p);
+        const float t = s + p;
+        const float z = t - s;
+        const float err = (s - (t - z)) + (p - z);
+        s = t;
+        c += err + e;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+
+constexpr int GS = 3;   // pipeline stages
+
+template <int BN>
+__host__ __device__ constexpr int gemm_smem_floats() {
+    return GS * GK * ((PT / (BN / 4)) * 4 + 4) + GS * GK * (BN + 4);
+}
+
+// one 4-byte asynchronous copy global -> shared, zero-filled when !valid
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int BN, bool TA, bool TB, bool ERR, bool COMP>
+__device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const float *__restrict__ A, int64_t lda,
+                                      const float *__restrict__ B, int64_t ldb, float beta, float *C, int64_t ldc,
+                                      const float *__restrict__ ref, int64_t ldref, TwoSumAcc *ss, float *sm) {
+    constexpr int TX = BN / 4, TY = PT / TX, BM = TY * 4;
+    constexpr int LAS = BM + 4, LBS = BN + 4;
+    constexpr int AL = BM * GK / PT, BL = BN * GK / PT;
+    float *As = sm;                     // [GS][GK][LAS]
+    float *Bs = sm + GS * GK * LAS;     // [GS][GK][LBS]
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int nk = (K + GK - 1) / GK;
+    for (int m0 = 0; m0 < M; m0 += BM) {
+        for (int n0 = 0; n0 < N; n0 += BN) {
+            float acc[4][4], hi[4][4], lo[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
+            // stage t of the K loop into buffer t % GS: each thread copies
+            // AL elements of the A tile and BL of the B tile, element (i, k)
+            // of op(A) to As[k][i] and (k, j) of op(B) to Bs[k][j] (the
+            // transposes happen in the addressing)
+            // per-thread sources: element q of this thread's share of the A
+            // tile sits at pa + q sa_q + t sa_k (B likewise)
+            const int ia = TA ? tid / GK : tid % BM, ka = TA ? tid % GK : tid / BM;
+            const int64_t sa_q = TA ? (int64_t)(PT / GK) * lda : (int64_t)(PT / BM) * lda;
+            const int64_t sa_k = TA ? GK : (int64_t)GK * lda;
+            const float *pa = TA ? A + ka + (int64_t)(m0 + ia) * lda : A + (m0 + ia) + (int64_t)ka * lda;
+            const int jb = TB ? tid % BN : tid / GK, kb = TB ? tid / BN : tid % GK;
+            const int64_t sb_q = TB ? (int64_t)(PT / BN) * ldb : (int64_t)(PT / GK) * ldb;
+            const int64_t sb_k = TB ? (int64_t)GK * ldb : GK;
+            const float *pb = TB ? B + (n0 + jb) + (int64_t)kb * ldb : B + kb + (int64_t)(n0 + jb) * ldb;
+            auto issue = [&](int t) {
+                const int k0 = t * GK, buf = t % GS;
+                float *as = As + buf * GK * LAS, *bs = Bs + buf * GK * LBS;
+                const float *a_t = pa + (int64_t)t * sa_k, *b_t = pb + (int64_t)t * sb_k;
+#pragma unroll
+                for (int q = 0; q < AL; ++q) {
+                    const int i = TA ? ia + q * (PT / GK) : ia, kk = TA ? ka : ka + q * (PT / BM);
+                    const bool v = m0 + i < M && k0 + kk < K;
+                    cp_async4(as + kk * LAS + i, v ? a_t + q * sa_q : A, v);
+                }
+#pragma unroll
+                for (int q = 0; q < BL; ++q) {
+                    const int j = TB ? jb : jb + q * (PT / GK), kk = TB ? kb + q * (PT / BN) : kb;
+                    const bool v = n0 + j < N && k0 + kk < K;
+                    cp_async4(bs + kk * LBS + j, v ? b_t + q * sb_q : B, v);
+                }
+            };
+#pragma unroll
+            for (int t = 0; t < GS - 1; ++t) {
+                if (t < nk) issue(t);
+                cp_async_commit();
+            }
+            for (int t = 0; t < nk; ++t) {
+                cp_async_wait<GS - 2>();      // stage t has landed (this thread's copies)
+                __syncthreads();              // ... everyone's; buffer (t - 1) % GS is free
+                if (t + GS - 1 < nk) issue(t + GS - 1);
+                cp_async_commit();
+                const int buf = t % GS;
+                const float *as = As + buf * GK * LAS + ty * 4, *bs = Bs + buf * GK * LBS + tx * 4;
+#pragma unroll
+                for (int kk = 0; kk < GK; ++kk) {
+                    const float4 a = *(const float4 *)(as + kk * LAS);
+                    const float4 b = *(const float4 *)(bs + kk * LBS);
+                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+                }
+                if (COMP) {
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) {
+                            const float a = hi[x][y], b = acc[x][y];
+                            const float t2 = a + b, z = t2 - a;
+                            lo[x][y] += (a - (t2 - z)) + (b - z);
+                            hi[x][y] = t2;
+                            acc[x][y] = 0.f;
+                        }
+                }
+            }
+            cp_async_wait<0>();
+            __syncthreads();                  // the buffers are reused by the next tile
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const int gi = m0 + ty * 4 + x;
+                if (gi >= M) continue;
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int gj = n0 + tx * 4 + y;
+                    if (gj >= N) continue;
+                    const float v = alpha * (COMP ? hi[x][y] + lo[x][y] : acc[x][y]);
+                    if (ERR) {
+                        const float d = ref[gi + (int64_t)gj * ldref] - v;
+                        ss->add(d, d);
+                    } else {
+                        float *c = C + gi + (int64_t)gj * ldc;
+                        *c = (beta == 0.f) ? v : fmaf(beta, *c, v);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// op(A) op(B) with the narrow tile when N <= 32; COMP for the long dot
+// products (K = m or n)
+template <bool TA, bool TB, bool COMP = false>
+__device__ void cta_mm(int M, int N, int K, float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
+                       float beta, float *C, int64_t ldc, float *sm) {
+    if (N <= 32)
+        cta_gemm<32, TA, TB, false, COMP>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr, sm);
+    else
+        cta_gemm<64, TA, TB, false, COMP>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr, sm);
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ FP64 Gram ----
+// G = Y^T Y (w x w, w <= 128, upper triangle with the diagonal blocks whole,
+// ld ldg) for FP32 Y (rows x w, ld ldy): every product formed exactly as
+// p + e (e = fma(a, b, -p)), the p's summed with TwoSum, the e's and the
+// TwoSum errors in FP32, converted to FP64 per thread; thread groups taking
+// every groups-th row are combined in a fixed order.  Rows are staged in
+// chunks of 32 (row-major, odd stride) in shared memory.
+constexpr int GRC = 32;   // rows per staged chunk
+
+__host__ __device__ constexpr size_t gram_smem_bytes() {
+    return sizeof(float) * GRC * (kPRcap + 1) + sizeof(double) * PT * 16;
+}
+
+__device__ __forceinline__ void block_of(int b, int &bi, int &bj) {
+    int j = (int)((sqrtf(8.f * b + 1.f) - 1.f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= b) ++j;
+    while (j * (j + 1) / 2 > b) --j;
+    bi = b - j * (j + 1) / 2;
+    bj = j;
+}
+
+__device__ __noinline__ void cta_gram(const float *__restrict__ Y, int64_t rows, int w, int64_t ldy, double *G,
+                                      int ldg, unsigned char *smraw) {
+    float *sY = (float *)smraw;                                   // GRC x (w + 1)
+    double *red = (double *)(smraw + sizeof(float) * GRC * (kPRcap + 1));
+    const int ld = w + 1;
+    const int nb4 = (w + 3) / 4, nblocks = nb4 * (nb4 + 1) / 2;   // <= 528
+    const int tid = threadIdx.x;
+    // sweeps of at most PT blocks, one block per thread (two sweeps only
+    // above w = 124); a sweep of at most PT / 2 blocks splits the rows
+    // among groups of threads instead
+    for (int sb = 0; sb < nblocks; sb += PT) {
+        const int nbs = nblocks - sb < PT ? nblocks - sb : PT;
+        const int groups = nbs <= PT / 2 ? PT / nbs : 1;
+        const int grp = tid / nbs;
+        const bool active = grp < groups;
+        int bi = 0, bj = 0;
+        if (active) block_of(sb + tid % nbs, bi, bj);
+        const int i0 = 4 * bi, j0 = 4 * bj;
+        TwoSumAcc acc[4][4];
+        for (int64_t c0 = 0; c0 < rows; c0 += GRC) {
+            const int cnt = (int)((rows - c0) < GRC ? (rows - c0) : GRC);
+            __syncthreads();
+            for (int e = tid; e < GRC * w; e += PT) {
+                const int r = e % GRC, c = e / GRC;
+                sY[r * ld + c] = (r < cnt) ? Y[(c0 + r) + (int64_t)c * ldy] : 0.f;
+            }
+            __syncthreads();
+            if (active) {
+                for (int r = grp; r < cnt; r += groups) {
+                    const float *row = sY + r * ld;
+                    float a[4], b[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        a[t] = (i0 + t < w) ? row[i0 + t] : 0.f;
+                        b[t] = (j0 + t < w) ? row[j0 + t] : 0.f;
+                    }
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 4; ++y) acc[x][y].add(a[x], b[y]);
+                }
+            }
+        }
+        if (groups > 1) {
+            // the row groups combined in a fixed order
+            if (active) {
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) red[((size_t)grp * nbs + tid % nbs) * 16 + x * 4 + y] = acc[x][y].value();
+            }
+            __syncthreads();
+            for (int e = tid; e < nbs * 16; e += PT) {
+                const int blk = e / 16, x = (e % 16) / 4, y = e % 4;
+                double sum = 0.0;
+                for (int g = 0; g < groups; ++g) sum += red[((size_t)g * nbs + blk) * 16 + x * 4 + y];
+                int ib, jb;
+                block_of(sb + blk, ib, jb);
+                if (4 * ib + x < w && 4 * jb + y < w) G[(4 * ib + x) + (int64_t)(4 * jb + y) * ldg] = sum;
+            }
+        } else if (tid < nbs) {
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y)
+                    if (i0 + x < w && j0 + y < w) G[(i0 + x) + (int64_t)(j0 + y) * ldg] = acc[x][y].value();
+        }
+    }
+    __syncthreads();
+}
+
+// --------------------------------------------------------- small helpers ----
+// sum of squares of an FP32 matrix (TwoSum accumulation per thread, FP64
+// block sum) and whether it holds a non-finite value
+__device__ double cta_sumsq(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, int *bad,
+                            double *red) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    TwoSumAcc acc;
+    int nf = 0;
+    for (int64_t j = warp; j < n; j += PT / 32) {
+        const float *col = A + j * lda;
+        int64_t i = lane;
+        for (; i + 96 < m; i += 128) {
+            const float v0 = col[i], v1 = col[i + 32], v2 = col[i + 64], v3 = col[i + 96];
+            nf |= !isfinite(v0) | !isfinite(v1) | !isfinite(v2) | !isfinite(v3);
+            acc.add(v0, v0);
+            acc.add(v1, v1);
+            acc.add(v2, v2);
+            acc.add(v3, v3);
+        }
+        for (; i < m; i += 32) {
+            const float v = col[i];
+            nf |= !isfinite(v);
+            acc.add(v, v);
+        }
+    }
+    *bad = __syncthreads_or(nf);
+    return block_sum(acc.value(), red);
+}
+
+// FP64 sum of squares of a vector of FP32 values
+__device__ double cta_norm2(const float *z, int64_t m, double *red) {
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += PT) acc = fma((double)z[i], (double)z[i], acc);
+    return block_sum(acc, red);
+}
+
+// Dst (p x p, FP32) = Src or Src^T (FP64), zeros kept
+__device__ void cta_to_f32(const double *Src, int lds, int p, float *Dst, int ldd, bool transpose) {
+    for (int e = threadIdx.x; e < p * p; e += PT) {
+        const int i = e % p, j = e / p;
+        Dst[i + j * ldd] = (float)(transpose ? Src[j + i * lds] : Src[i + j * lds]);
+    }
+    __syncthreads();
+}
+
+// C = A B for upper triangular p x p FP64 factors (C upper, zeros below)
+__device__ void cta_triu_mul(const double *A, int lda, const double *B, int ldb, double *C, int ldc, int p) {
+    for (int e = threadIdx.x; e < p * p; e += PT) {
+        const int i = e % p, j = e / p;
+        double s = 0.0;
+        for (int l = i; l <= j; ++l) s = fma(A[i + l * lda], B[l + j * ldb], s);
+        C[i + j * ldc] = s;
+    }
+    __syncthreads();
+}
+
+// Omega_j (n x f, ld n) in FP32: the same draws as the streaming fill
+__device__ void cta_omega(int64_t n, int64_t col0, int f, uint64_t seed, uint32_t batch, float *Om) {
+    const int64_t tot = n * f;
+    for (int64_t e = threadIdx.x; e < tot; e += PT) {
+        const int64_t c = e / n, i = e - c * n;
+        Om[e] = omega_value_fast<float>(seed, (uint32_t)i, (uint32_t)(col0 + c), batch);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------- the kernel ----
+struct PItem {
+    const float *A;
+    int64_t m, n, lda;
+    float *Q, *C, *U, *V;     // m x cap, n x cap, m x cap, n x cap (ld m, n, m, n)
+    double *D;                // r x r, ld r
+    int64_t cap;              // min(m, n, kPRcap)
+    uint32_t batch;           // Omega's third counter word (the item's index)
+};
+
+struct PRes {
+    int32_t status, rank, blocks, restarts, ntdiag, pad;
+    double norm_a, eps, rel_err;
+};
+
+struct PParams {
+    const PItem *items;
+    const int32_t *order;     // queue order: largest first
+    PRes *res;
+    double *tdiag;            // count x kPTdCap
+    unsigned char *scratch;   // one region per CTA
+    int64_t stride, mmax, nmax;
+    unsigned *next;           // the work queue's counter
+    int count, k, tol_mode, compute_err;
+    double tol;
+    uint64_t seed;
+};
+
+// per-CTA scratch: FP64 k x k / r x r factors first, then the FP32 panels
+struct PLayout {
+    int64_t g, r1, r1i, r2, r2i, rc;            // doubles
+    int64_t y, t1, om, sp, w, rf, rtf, w2, qh;  // floats, after the doubles
+    int64_t dbytes, bytes;
+};
+
+__host__ __device__ inline PLayout playout(int64_t mmax, int64_t nmax) {
+    auto up = [](int64_t x) { return (x + 63) / 64 * 64; };
+    PLayout L;
+    const int64_t rr = (int64_t)kPRcap * kPRcap;
+    L.g = 0;
+    L.r1 = L.g + rr;
+    L.r1i = L.r1 + rr;
+    L.r2 = L.r1i + rr;
+    L.r2i = L.r2 + rr;
+    L.rc = L.r2i + rr;
+    L.dbytes = (L.rc + rr) * (int64_t)sizeof(double);
+    L.y = 0;
+    L.t1 = L.y + up(mmax * kPKmax);
+    L.om = L.t1 + up(mmax * kPKmax);
+    L.sp = L.om + up(nmax * kPKmax);
+    L.w = L.sp + up((int64_t)kPRcap * kPKmax);
+    L.rf = L.w + up(nmax * kPRcap);
+    L.rtf = L.rf + rr;
+    L.w2 = L.rtf + rr;
+    L.qh = L.w2 + rr;
+    L.bytes = L.dbytes + (L.qh + rr) * (int64_t)sizeof(float);
+    L.bytes = (L.bytes + 255) / 256 * 256;
+    return L;
+}
+
+__device__ __noinline__ void leaf(const double *G, int w, int decide, double eps2, double delta_coef, double rho,
+                                     double *R, double *Ri, int *info, double ni_tau2, unsigned char *sm) {
+    chol_leaf_cta<true>(G, kPRcap, w, decide, eps2, delta_coef, rho, 0.0, R, kPRcap, Ri, kPRcap, info, ni_tau2,
+                        (double *)sm);
+    __syncthreads();
+}
+// One matrix, start to end, on this CTA.
+__device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *info, double *red) {
+    const PItem it = P.items[idx];
+    PRes *res = P.res + idx;
+    double *tdg = P.tdiag + (int64_t)idx * kPTdCap;
+    const int tid = threadIdx.x;
+    const int64_t m = it.m, n = it.n, lda = it.lda;
+    const PLayout L = playout(P.mmax, P.nmax);
+    unsigned char *base = P.scratch + (int64_t)blockIdx.x * P.stride;
+    double *G = (double *)base + L.g, *R1 = (double *)base + L.r1, *R1i = (double *)base + L.r1i;
+    double *R2 = (double *)base + L.r2, *R2i = (double *)base + L.r2i, *Rc = (double *)base + L.rc;
+    float *fb = (float *)(base + L.dbytes);
+    float *Y = fb + L.y, *T1 = fb + L.t1, *Om = fb + L.om, *S = fb + L.sp, *W = fb + L.w;
+    float *Rf = fb + L.rf, *Rtf = fb + L.rtf, *W2 = fb + L.w2, *Qh = fb + L.qh;
+    float *smf = (float *)sm;
+    constexpr double kNearId = 4e-8;   // ||G - I||_F^2 below which R = I + Phi(G - I) (FP32 panels)
+
+    int kept = 0, blocks = 0, restarts = 0, ntd = 0;
+    double eps = 0.0, norm = 0.0;
+    auto finish = [&](int status, double rel) {
+        if (tid == 0) {
+            res->status = status;
+            res->rank = kept;
+            res->blocks = blocks;
+            res->restarts = restarts;
+            res->ntdiag = ntd;
+            res->norm_a = norm;
+            res->eps = eps;
+            res->rel_err = rel;
+        }
+    };
+
+    // ||A||_F and finiteness
+    int bad = 0;
+    norm = sqrt(cta_sumsq(it.A, m, n, lda, &bad, red));
+    if (bad) { finish(EOD_ENONFINITE, -1.0); return; }
+    eps = P.tol_mode == EOD_TOL_REL_FRO ? P.tol * norm : P.tol;
+    if (norm == 0.0) {
+        if (tid == 0) tdg[0] = 0.0;
+        ntd = 1;
+        finish(EOD_OK, P.compute_err ? 0.0 : -1.0);
+        return;
+    }
+
+    // ---- Alg. 1 ----
+    const int64_t cap = m < n ? m : n;
+    const double eps2 = eps * eps;
+    const double delta_coef = 64.0 * ((double)P.k + sqrt((double)m)) * kU64;
+    const double rho = 1e-6;
+    bool stop = false;
+    while (!stop && kept < cap) {
+        const int f = (int)((int64_t)P.k < cap - kept ? (int64_t)P.k : cap - kept);
+        ++blocks;
+        cta_omega(n, kept, f, P.seed, it.batch, Om);                                       // step 3
+        cta_mm<false, false, true>((int)m, f, (int)n, 1.f, it.A, lda, Om, n, 0.f, Y, m, smf);    // Y = A Omega_j
+        int cur = 0;
+        while (!stop && cur < f) {
+            float *Yc = Y + (int64_t)cur * m;
+            const int wdt = f - cur;
+            for (int pass = 0; pass < 2 && kept > 0; ++pass) {                             // step 4, twice
+                cta_mm<true, false, true>(kept, wdt, (int)m, 1.f, it.Q, m, Yc, m, 0.f, S, kPRcap, smf);
+                cta_mm<false, false>((int)m, wdt, kept, -1.f, it.Q, m, S, kPRcap, 1.f, Yc, m, smf);
+            }
+            cta_gram(Yc, m, wdt, m, G, kPRcap, sm);                                          // step 5, pass 1
+            leaf(G, wdt, 1, eps2, delta_coef, rho, R1, R1i, info, 0.0, sm);                    // steps 6-11
+            const int p = info[0], code = info[1];
+            __syncthreads();
+            if (p > 0) {
+                if (kept + p > it.cap) { finish(kPFallback, -1.0); return; }
+                cta_to_f32(R1i, kPRcap, p, Rf, kPRcap, false);
+                cta_mm<false, false>((int)m, p, p, 1.f, Yc, m, Rf, kPRcap, 0.f, T1, m, smf);
+                cta_gram(T1, m, p, m, G, kPRcap, sm);                                        // pass 2
+                leaf(G, p, 0, 0.0, 0.0, 0.0, R2, R2i, info, kNearId, sm);
+                const int p2 = info[0], c2 = info[1];
+                __syncthreads();
+                if (p2 != p || c2 != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+                cta_to_f32(R2i, kPRcap, p, Rf, kPRcap, false);
+                cta_mm<false, false>((int)m, p, p, 1.f, T1, m, Rf, kPRcap, 0.f, it.Q + (int64_t)kept * m, m, smf);
+                for (int l = tid; l < p; l += PT) tdg[ntd + l] = fabs(R1[l + l * kPRcap] * R2[l + l * kPRcap]);
+                ntd += p;
+                kept += p;
+            }
+            if (code == CHOL_ALL) {
+                cur = f;
+            } else {
+                // column p: its explicit residual after two more projections
+                float *z = Yc + (int64_t)p * m;
+                for (int pass = 0; pass < 2 && kept > 0; ++pass) {
+                    cta_mm<true, false, true>(kept, 1, (int)m, 1.f, it.Q, m, z, m, 0.f, S, kPRcap, smf);
+                    cta_mm<false, false>((int)m, 1, kept, -1.f, it.Q, m, S, kPRcap, 1.f, z, m, smf);
+                }
+                const double t = sqrt(cta_norm2(z, m, red));
+                if (tid == 0) tdg[ntd] = t;
+                ++ntd;
+                if (code == CHOL_BELOW) {
+                    stop = true;
+                } else {
+                    ++restarts;
+                    if (!(t > eps)) {
+                        stop = true;
+                    } else {
+                        if (kept + 1 > it.cap) { finish(kPFallback, -1.0); return; }
+                        const double inv = 1.0 / t;
+                        float *q = it.Q + (int64_t)kept * m;
+                        for (int64_t i = tid; i < m; i += PT) q[i] = (float)((double)z[i] * inv);
+                        __syncthreads();
+                        kept += 1;
+                        cur += p + 1;
+                    }
+                }
+            }
+        }
+    }
+    const int r = kept;
+    if (r == 0) { finish(EOD_OK, P.compute_err ? 1.0 : -1.0); return; }
+
+    // ---- Alg. 2 step 8: C (n x r) = A^T Q ----
+    cta_mm<true, false, true>((int)n, r, (int)m, 1.f, it.A, lda, it.Q, m, 0.f, it.C, n, smf);
+    double rel = -1.0;
+    if (P.compute_err) {                                                   // ||A - Q C^T||_F / ||A||_F
+        TwoSumAcc ssq;
+        cta_gemm<64, false, true, true, false>((int)m, (int)n, r, 1.f, it.Q, m, it.C, n, 0.f, nullptr, 0, it.A, lda, &ssq,
+                                        smf);
+        rel = sqrt(block_sum(ssq.value(), red)) / norm;
+    }
+
+    // ---- steps 9-10: C^T = V R, then R^T = Qh D (CholQR2 each) ----
+    cta_gram(it.C, n, r, n, G, kPRcap, sm);
+    leaf(G, r, 0, 0.0, 0.0, 0.0, R1, R1i, info, 0.0, sm);
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    cta_to_f32(R1i, kPRcap, r, Rf, kPRcap, false);
+    cta_mm<false, false>((int)n, r, r, 1.f, it.C, n, Rf, kPRcap, 0.f, W, n, smf);
+    cta_gram(W, n, r, n, G, kPRcap, sm);
+    leaf(G, r, 0, 0.0, 0.0, 0.0, R2, R2i, info, kNearId, sm);
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    cta_to_f32(R2i, kPRcap, r, Rf, kPRcap, false);
+    cta_mm<false, false>((int)n, r, r, 1.f, W, n, Rf, kPRcap, 0.f, it.V, n, smf);
+    cta_triu_mul(R2, kPRcap, R1, kPRcap, Rc, kPRcap, r);                  // R = R2 R1
+
+    cta_to_f32(Rc, kPRcap, r, Rtf, kPRcap, true);                         // R^T
+    cta_gram(Rtf, r, r, kPRcap, G, kPRcap, sm);
+    leaf(G, r, 0, 0.0, 0.0, 0.0, R1, R1i, info, 0.0, sm);
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    cta_to_f32(R1i, kPRcap, r, Rf, kPRcap, false);
+    cta_mm<false, false>(r, r, r, 1.f, Rtf, kPRcap, Rf, kPRcap, 0.f, W2, kPRcap, smf);
+    cta_gram(W2, r, r, kPRcap, G, kPRcap, sm);
+    leaf(G, r, 0, 0.0, 0.0, 0.0, R2, R2i, info, kNearId, sm);
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    cta_to_f32(R2i, kPRcap, r, Rf, kPRcap, false);
+    cta_mm<false, false>(r, r, r, 1.f, W2, kPRcap, Rf, kPRcap, 0.f, Qh, kPRcap, smf);
+    cta_triu_mul(R2, kPRcap, R1, kPRcap, it.D, r, r);                    // D = R2 R1 of this pair
+
+    // ---- step 11: U = Q Qh ----
+    cta_mm<false, false>((int)m, r, r, 1.f, it.Q, m, Qh, kPRcap, 0.f, it.U, m, smf);
+    finish(EOD_OK, rel);
+}
+
+__global__ void __launch_bounds__(PT, 1) batch_kernel(PParams P) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    __shared__ int item_sh;
+    __shared__ int info_sh[2];
+    __shared__ double red_sh[32];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) item_sh = (int)atomicAdd(P.next, 1u);
+        __syncthreads();
+        const int j = item_sh;
+        if (j >= P.count) return;
+        batch_item(P, P.order[j], psm, info_sh, red_sh);
+    }
+}
+
+size_t batch_smem_bytes() {
+    size_t b = leaf_smem_bytes(kPRcap);
+    b = std::max(b, gram_smem_bytes());
+    b = std::max(b, sizeof(float) * (size_t)gemm_smem_floats<32>());
+    b = std::max(b, sizeof(float) * (size_t)gemm_smem_floats<64>());
+    return (b + 15) / 16 * 16;
+}
+
+// ------------------------------------------------------- pooled factors ----
+// The factors of one persistent batch share one allocation; each factor set
+// holds a reference, the last release frees it.
+struct Pool {
+    void *base = nullptr;
+    int refs = 0;
+};
+std::mutex g_pool_mu;
+std::unordered_map<const void *, Pool *> g_pool_of;   // keyed by each factor set's Q
+
+}  // namespace
+
+bool release_pooled_factors(eod_factors *f) {
+    if (!f || !f->Q) return false;
+    Pool *pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        auto itp = g_pool_of.find(f->Q);
+        if (itp == g_pool_of.end()) return false;
+        pool = itp->second;
+        g_pool_of.erase(itp);
+        if (--pool->refs > 0) pool = nullptr;
+    }
+    if (pool) {
+        cudaFree(pool->base);
+        delete pool;
+    }
+    f->U = f->V = f->Q = f->C = nullptr;
+    f->D = nullptr;
+    return true;
+}
+
+eod_status factor_batched_persistent(const void *const *A, const int64_t *m, const int64_t *n, const int64_t *lda,
+                                     int64_t count, double tol, uint64_t seed, const eod_opts &o, eod_factors **out,
+                                     eod_status *per_item, std::vector<int64_t> &fallback) {
+    fallback.clear();
+    const int k = o.block_k > 0 ? o.block_k : 32;
+    const bool form_ok = o.a_dtype == EOD_F32 && o.power_iters == 0 && k <= kPKmax && tol > 0.0 &&
+                         std::isfinite(tol) && (o.tol_mode == EOD_TOL_ABS || o.tol_mode == EOD_TOL_REL_FRO) &&
+                         (o.precision == EOD_PLAIN || o.precision == EOD_MIXED_BF16 ||
+                          o.precision == EOD_MIXED_TF32) && count <= 0x7FFFFFFF;
+    std::vector<int64_t> items;
+    for (int64_t i = 0; i < count; ++i) {
+        const bool ok = form_ok && A[i] && m[i] >= 1 && n[i] >= 1 && lda[i] >= m[i] && m[i] <= kPMaxDim &&
+                        n[i] <= kPMaxDim;
+        (ok ? items : fallback).push_back(i);
+    }
+    if (items.empty()) return EOD_OK;
+    auto all_back = [&]() {
+        fallback.clear();
+        for (int64_t i = 0; i < count; ++i) fallback.push_back(i);
+    };
+    // largest first (the same cost order as the single-matrix workers)
+    std::stable_sort(items.begin(), items.end(), [&](int64_t a, int64_t b) {
+        return (double)m[a] * n[a] * std::min(m[a], n[a]) > (double)m[b] * n[b] * std::min(m[b], n[b]);
+    });
+    const int64_t ne = (int64_t)items.size();
+    int64_t mmax = 1, nmax = 1;
+    for (int64_t i : items) {
+        mmax = std::max(mmax, m[i]);
+        nmax = std::max(nmax, n[i]);
+    }
+    // the factors: one allocation, 256-byte aligned sections per item
+    auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
+    std::vector<int64_t> off(ne);
+    int64_t pool_bytes = 0;
+    for (int64_t e = 0; e < ne; ++e) {
+        const int64_t i = items[e], c = std::min<int64_t>(std::min(m[i], n[i]), kPRcap);
+        off[e] = pool_bytes;
+        pool_bytes += 2 * up(4 * m[i] * c) + 2 * up(4 * n[i] * c) + up(8 * c * c);
+    }
+    void *pool = nullptr;
+    if (cudaMalloc(&pool, (size_t)pool_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        all_back();
+        return EOD_OK;
+    }
+    std::vector<PItem> hitems(ne);
+    std::vector<int32_t> horder(ne);
+    for (int64_t e = 0; e < ne; ++e) {
+        const int64_t i = items[e], c = std::min<int64_t>(std::min(m[i], n[i]), kPRcap);
+        unsigned char *b = (unsigned char *)pool + off[e];
+        PItem &it = hitems[e];
+        it.A = (const float *)A[i];
+        it.m = m[i];
+        it.n = n[i];
+        it.lda = lda[i];
+        it.Q = (float *)b;
+        it.U = (float *)(b + up(4 * m[i] * c));
+        it.C = (float *)(b + 2 * up(4 * m[i] * c));
+        it.V = (float *)(b + 2 * up(4 * m[i] * c) + up(4 * n[i] * c));
+        it.D = (double *)(b + 2 * up(4 * m[i] * c) + 2 * up(4 * n[i] * c));
+        it.cap = c;
+        it.batch = (uint32_t)i;
+        horder[e] = (int32_t)e;
+    }
+
+    cudaStream_t caller = (cudaStream_t)o.stream;
+    int dev = 0, sms = kNumSMs;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(pool);
+        all_back();
+        return EOD_OK;
+    }
+    const int grid = (int)std::min<int64_t>(ne, sms);
+    const PLayout L = playout(mmax, nmax);
+    std::vector<PRes> hres(ne);
+    std::vector<double> htd((size_t)ne * kPTdCap);
+    cudaStream_t ps = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ready = nullptr;
+    bool launched = false;
+    {
+        Arena ar(caller);
+        PItem *ditems;
+        int32_t *dorder;
+        PRes *dres;
+        double *dtd;
+        unsigned char *scratch;
+        unsigned *next;
+        eod_status st = ar.get(&ditems, (size_t)ne);
+        if (st == EOD_OK) st = ar.get(&dorder, (size_t)ne);
+        if (st == EOD_OK) st = ar.get(&dres, (size_t)ne);
+        if (st == EOD_OK) st = ar.get(&dtd, (size_t)ne * kPTdCap);
+        if (st == EOD_OK) st = ar.get(&scratch, (size_t)(L.bytes * grid));
+        if (st == EOD_OK) st = ar.get(&next, (size_t)1);
+        cudaError_t e = st == EOD_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ditems, hitems.data(), sizeof(PItem) * ne, cudaMemcpyHostToDevice, caller);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dorder, horder.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, caller);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ready, caller);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ps, ready, 0);
+        const size_t smem = batch_smem_bytes();
+        if (e == cudaSuccess) e = set_smem_once(batch_kernel, (int)smem);
+        PParams P;
+        P.items = ditems;
+        P.order = dorder;
+        P.res = dres;
+        P.tdiag = dtd;
+        P.scratch = scratch;
+        P.stride = L.bytes;
+        P.mmax = mmax;
+        P.nmax = nmax;
+        P.next = next;
+        P.count = (int)ne;
+        P.k = k;
+        P.tol_mode = o.tol_mode;
+        P.compute_err = o.compute_err;
+        P.tol = tol;
+        P.seed = seed;
+        // the queue reset and the persistent kernel, captured as one graph
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaMemsetAsync(next, 0, sizeof(unsigned), ps);
+            if (e1 == cudaSuccess) {
+                batch_kernel<<<grid, PT, smem, ps>>>(P);
+                e1 = cudaGetLastError();
+            }
+            e = cudaStreamEndCapture(ps, &graph);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) {
+            double flops = 0.0, bytes = 0.0;
+            for (int64_t i : items) {
+                const double c = (double)std::min<int64_t>(std::min(m[i], n[i]), kPRcap);
+                flops += 2.0 * m[i] * n[i] * (3.0 * c + k);
+                bytes += 4.0 * m[i] * n[i] * 4.0;
+            }
+            count_launch(1);
+            ProfScope prof(PROF_BATCH, flops, bytes, ps);
+            e = cudaGraphLaunch(exec, ps);
+            launched = e == cudaSuccess;
+        }
+        if (launched) e = cudaStreamSynchronize(ps);
+        if (e == cudaSuccess) e = cudaMemcpy(hres.data(), dres, sizeof(PRes) * ne, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(htd.data(), dtd, sizeof(double) * ne * kPTdCap, cudaMemcpyDeviceToHost);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ready) cudaEventDestroy(ready);
+        if (ps) {
+            cudaStreamSynchronize(ps);
+            cudaStreamDestroy(ps);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize(caller);
+            cudaFree(pool);
+            if (launched) return EOD_ECUDA;   // the launch itself failed: no item is retried
+            all_back();
+            return EOD_OK;
+        }
+    }
+
+    // factor sets of the items that finished here
+    Pool *pl = new Pool;
+    pl->base = pool;
+    for (int64_t e = 0; e < ne; ++e) {
+        const int64_t i = items[e];
+        const PRes &rs = hres[e];
+        if (rs.status == kPFallback) {
+            fallback.push_back(i);
+            continue;
+        }
+        if (rs.status != EOD_OK) {
+            per_item[i] = (eod_status)rs.status;
+            continue;
+        }
+        eod_factors *F = (eod_factors *)std::calloc(1, sizeof(eod_factors));
+        const int nt = std::max(1, rs.ntdiag);
+        double *td = F ? (double *)std::malloc(sizeof(double) * nt) : nullptr;
+        if (!F || !td) {
+            std::free(F);
+            std::free(td);
+            per_item[i] = EOD_ENOMEM;
+            continue;
+        }
+        F->m = m[i];
+        F->n = n[i];
+        F->rank = rs.rank;
+        F->f_dtype = EOD_F32;
+        F->precision = EOD_PLAIN;
+        F->norm_a = rs.norm_a;
+        F->eps = rs.eps;
+        F->rel_err = rs.rel_err;
+        F->blocks = rs.blocks;
+        F->restarts = rs.restarts;
+        F->block_k = k;
+        F->ntdiag = rs.ntdiag;
+        std::memcpy(td, htd.data() + (size_t)e * kPTdCap, sizeof(double) * std::max(0, rs.ntdiag));
+        F->tdiag = td;
+        double margin = INFINITY;
+        for (int j = 0; j < rs.ntdiag; ++j)
+            if (td[j] > 0.0 && rs.eps > 0.0) margin = std::min(margin, std::fabs(std::log10(td[j] / rs.eps)));
+        F->t_margin = margin;
+        if (rs.rank > 0) {
+            const PItem &it = hitems[e];
+            F->Q = it.Q;
+            F->U = it.U;
+            F->C = it.C;
+            F->V = it.V;
+            F->D = it.D;
+            std::lock_guard<std::mutex> lk(g_pool_mu);
+            g_pool_of[it.Q] = pl;
+            ++pl->refs;
+        }
+        out[i] = F;
+        per_item[i] = EOD_OK;
+    }
+    if (pl->refs == 0) {
+        cudaFree(pool);
+        delete pl;
+    }
+    std::sort(fallback.begin(), fallback.end());
+    return EOD_OK;
+}
+
+}  // namespace eod

@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include "tc_gemm.cuh"
 #include "instrument.cuh"
+#include "batch.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -906,6 +907,11 @@ static eod_status validate(const void *A, int64_t m, int64_t n, int64_t lda, dou
 
 static void free_factors_device(eod_factors *f) {
     if (!f) return;
+    if (release_pooled_factors(f)) {   // factors of a persistent batch
+        std::free(f->tdiag);
+        f->tdiag = nullptr;
+        return;
+    }
     void *ptrs[] = {f->U, f->V, f->Q, f->C, (void *)f->D};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1104,9 +1110,28 @@ eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const 
         out[i] = nullptr;
         per_item[i] = EOD_EINVAL;
     }
+    // FP32 items first go through the persistent launch (batch.cu); what it
+    // hands back (rank above its capacity, shifted CholQR needed, other
+    // forms) runs below, one single-matrix factorisation per item on a pool
+    // of worker streams.  EOD_BATCH_PERSISTENT=0 skips the persistent launch.
+    std::vector<int64_t> todo;
+    const char *pers_env = std::getenv("EOD_BATCH_PERSISTENT");
+    if (o.a_dtype == EOD_F32 && !(pers_env && pers_env[0] == '0')) {
+        const eod_status pst = factor_batched_persistent(A, m, n, lda, count, tol, seed, o, out, per_item, todo);
+        if (pst != EOD_OK) {
+            for (int64_t i = 0; i < count; ++i) per_item[i] = pst;
+            return pst;
+        }
+    } else {
+        for (int64_t i = 0; i < count; ++i) todo.push_back(i);
+    }
+    if (todo.empty()) {
+        for (int64_t i = 0; i < count; ++i)
+            if (per_item[i] != EOD_OK) return per_item[i];
+        return EOD_OK;
+    }
     // longest first: the rank is unknown, so m * n * min(m, n) stands in for the cost
-    std::vector<int64_t> order((size_t)count);
-    for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::vector<int64_t> order(todo);
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
         const double ca = (double)m[a] * n[a] * std::min(m[a], n[a]);
         const double cb = (double)m[b] * n[b] * std::min(m[b], n[b]);
@@ -1127,7 +1152,7 @@ eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const 
         if (tuned_value("batch_workers", count, (int64_t)(sm / count), (int64_t)(sn / count), &v) && v >= 1 && v <= 64)
             workers = (int)v;
     }
-    if (workers > count) workers = (int)count;
+    if (workers > (int64_t)order.size()) workers = (int)order.size();
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
     // work already queued on the caller's stream (for example the matrices
@@ -1149,7 +1174,7 @@ eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const 
         cudaStreamWaitEvent(st, ready, 0);
         for (;;) {
             const int64_t j = next.fetch_add(1);
-            if (j >= count) break;
+            if (j >= (int64_t)order.size()) break;
             const int64_t i = order[(size_t)j];
             eod_opts oi = o;
             oi.batch_index = (uint64_t)i;

@@ -15,7 +15,8 @@ enum ProfKind {
     PROF_OZ_GEMM = 5,     // FP64 contractions emulated on tcgen05 (plain FP64 path)
     PROF_OZ_SLICE = 6,    // FP64 operands cut into BF16 digit slices for those contractions
     PROF_GEMM_SIMT32 = 7, // SIMT GEMM and Gram in FP32 arithmetic (FP32-data paths)
-    PROF_KINDS = 8
+    PROF_BATCH = 8,       // the persistent batched factorisation (one launch per batch)
+    PROF_KINDS = 9
 };
 
 void count_launch(int n = 1);

@@ -122,7 +122,11 @@ def test_pixel_batch_256_mixed_full(eod):
         assert abs(res[i].rel_err - _basis_relerr(res[i], w.A[i].astype(np.float64))) <= 1e-4
 
 
-def test_batched_equals_single_calls_mixed(eod):
+def test_batched_equals_single_calls_mixed(eod, monkeypatch):
+    # the worker-stream form (the persistent launch, which these small items
+    # would take, computes in FP32 and is compared with the oracle in
+    # test_gpu_batch_persistent.py)
+    monkeypatch.setenv("EOD_BATCH_PERSISTENT", "0")
     mats = [W.image_like(m=200 + 37 * i, n=150 + 23 * i, r=20 + 3 * i, seed=40 + i, dtype="f32", tol=0.02).A
             for i in range(10)]
     tens = [torch.from_numpy(a).cuda() for a in mats]
