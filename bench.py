@@ -233,6 +233,7 @@ def _traffic_for(kind_name, source_files):
 
 
 KIND_SOURCES = {
+    "batch": ["paper_2506_22713_gb300/csrc/batch.cu", "paper_2506_22713_gb300/csrc/chol_leaf.cuh"],
     "oz_gemm": ["paper_2506_22713_gb300/csrc/oz_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"],
     "tc_gemm": ["paper_2506_22713_gb300/csrc/tc_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"],
     "chol": ["paper_2506_22713_gb300/csrc/chol.cu"],
@@ -625,60 +626,85 @@ def robustness_matrices(eod):
 
 
 def compare_batched(eod, steps, warmup):
-    """Factorisations per second of the 256-matrix pixel batch, mixed against
-    plain FP64, as stated (clipped to [0, 255], tol 1e-3 relative) and
-    unclipped (same tolerance)."""
+    """Factorisations per second of the 256-matrix pixel batch, as stated
+    (clipped to [0, 255], tol 1e-3 relative) and unclipped (same tolerance):
+    plain FP64 (worker streams), the FP32 batch through the library's default
+    route (the persistent launch, items above its rank capacity handed to the
+    worker streams in the mixed BF16 form) and the same FP32 batch on the
+    worker streams alone (EOD_BATCH_PERSISTENT=0)."""
     import numpy as np
     import torch
     import workloads as W
+
+    def timed(mats, prec, tol, seed, env):
+        saved = {k: os.environ.get(k) for k in env}
+        os.environ.update(env)
+        try:
+            for _ in range(warmup):
+                r, st = eod.factor_batched(mats, tol, seed, block_k=32, tol_mode="rel", precision=prec)
+                del r
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                r, st = eod.factor_batched(mats, tol, seed, block_k=32, tol_mode="rel", precision=prec)
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) / steps, r, st
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
 
     out = []
     for name, clip, tol in (("pixel batch 256 (m,n~U[256,2048], r~U[8,128]), clipped [0,255], tol 1e-3 rel", True, 1e-3),
                             ("pixel batch 256, unclipped (no noise tail from clipping), tol 1e-3 rel", False, 1e-3)):
         w = W.pixel_batch(clip=clip, tol=tol)
-        sets = {"plain_f64": ([torch.from_numpy(np.asfortranarray(a.astype(np.float64))).cuda() for a in w.A], "plain"),
-                "mixed_bf16": ([torch.from_numpy(a).cuda() for a in w.A], "mixed")}
-        res = {}
-        ranks = {}
-        rels = {}
-        for form, (mats, prec) in sets.items():
-            for _ in range(warmup):
-                r, st = eod.factor_batched(mats, tol, w.seed, block_k=32, tol_mode="rel", precision=prec)
-                del r
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(steps):
-                r, st = eod.factor_batched(mats, tol, w.seed, block_k=32, tol_mode="rel", precision=prec)
-            torch.cuda.synchronize()
-            dt = (time.perf_counter() - t0) / steps
-            # the fixed default of 8 worker streams beside the tuned count
-            os.environ["EOD_BATCH_STREAMS"] = "8"
-            try:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                r8, _ = eod.factor_batched(mats, tol, w.seed, block_k=32, tol_mode="rel", precision=prec)
-                torch.cuda.synchronize()
-                dt8 = time.perf_counter() - t0
-                del r8
-            finally:
-                os.environ.pop("EOD_BATCH_STREAMS", None)
+        m32 = [torch.from_numpy(a).cuda() for a in w.A]
+        m64 = [torch.from_numpy(np.asfortranarray(a.astype(np.float64))).cuda() for a in w.A]
+        legs = {"plain_f64": (m64, "plain", {}),
+                "mixed_bf16": (m32, "mixed", {}),
+                "mixed_bf16_worker_streams": (m32, "mixed", {"EOD_BATCH_PERSISTENT": "0"})}
+        res, ranks, rels = {}, {}, {}
+        for form, (mats, prec, env) in legs.items():
+            dt, r, st = timed(mats, prec, tol, w.seed, env)
             ranks[form] = [x.rank for x in r]
             rels[form] = [x.rel_err for x in r]
             flops = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, 32, True) for a, x in zip(w.A, r))
             res[form] = {"fact_per_s": len(mats) / dt, "ms_per_batch": dt * 1e3, "gflops": flops / dt / 1e9,
-                         "workers": eod.tuning_lookup("batch_workers", len(mats),
-                                                      int(np.mean([a.shape[0] for a in w.A])),
-                                                      int(np.mean([a.shape[1] for a in w.A]))) or 8,
-                         "fact_per_s_fixed_8_workers": len(mats) / dt8,
                          "statuses_ok": all(x == 0 for x in st),
                          "rank_mean": float(np.mean(ranks[form])), "rank_max": int(np.max(ranks[form]))}
+            if form == "mixed_bf16":
+                # items the persistent launch finished (its factor sets say EOD_PLAIN)
+                res[form]["items_in_persistent_launch"] = sum(1 for x in r if x.precision == 0)
+            if form != "mixed_bf16":
+                res[form]["worker_streams"] = eod.tuning_lookup(
+                    "batch_workers", len(mats), int(np.mean([a.shape[0] for a in w.A])),
+                    int(np.mean([a.shape[1] for a in w.A]))) or 8
             del r
+        # the persistent kernel alone: its device time (CUDA events around
+        # the graph launch) against the cost model's flops of the items it
+        # finished, on the FP32 CUDA-core peak (its products are FP32 SIMT)
+        eod.eod_abe_debug_profile(1)
+        r, st = eod.factor_batched(m32, tol, w.seed, block_k=32, tol_mode="rel", precision="mixed")
+        pk = eod.profile_read(eod.PROF_BATCH)
+        eod.eod_abe_debug_profile(0)
+        fl = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, 32, True) for a, x in zip(w.A, r) if x.precision == 0)
+        if pk["launches"] and pk["ms"] > 0:
+            ach = fl / (pk["ms"] / 1e3) / 1e9
+            res["mixed_bf16"]["persistent_kernel"] = {
+                "ms": pk["ms"], "model_gflop": fl / 1e9, "achieved_gflops": ach, "bound": "alu",
+                "peak_gflops": FP32_PEAK_GFLOPS, "frac": ach / FP32_PEAK_GFLOPS,
+                "peak_source": "FP32 from unit counts: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
+        del r
         eq = sum(a == b for a, b in zip(ranks["mixed_bf16"], ranks["plain_f64"]))
         drel = max(abs(a - b) for a, b in zip(rels["mixed_bf16"], rels["plain_f64"]))
         out.append({"workload": name, "forms": res, "mixed_rank_equal_f64": f"{eq}/{len(ranks['plain_f64'])}",
                     "mixed_max_d_rel_err_vs_f64": drel,
-                    "mixed_speedup_vs_f64": res["mixed_bf16"]["fact_per_s"] / res["plain_f64"]["fact_per_s"]})
-        del sets
+                    "mixed_speedup_vs_f64": res["mixed_bf16"]["fact_per_s"] / res["plain_f64"]["fact_per_s"],
+                    "persistent_speedup_vs_worker_streams":
+                        res["mixed_bf16"]["fact_per_s"] / res["mixed_bf16_worker_streams"]["fact_per_s"]})
+        del m32, m64
         torch.cuda.empty_cache()
     return out
 

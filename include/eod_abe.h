@@ -233,6 +233,18 @@ EOD_API void eod_abe_debug_fail_alloc_after(int32_t n);
  * kind or NULL outputs.  eod_abe_debug_launch_count() is the number of
  * kernels the library has launched since it was loaded. */
 EOD_API void eod_abe_debug_profile(int32_t enable);
+
+/* Measurement hook of the persistent batched launch (eod_abe_factor_batched
+ * on FP32 items): with enable != 0 every later launch sums, per phase of an
+ * item, the SM clock ticks its CTAs spent there, in 11 counters: (unused:
+ * the norm is summed inside the first sketch), Omega, sketch A Omega_j
+ * (with the norm), projection against Q (step 4), Gram and
+ * rank-test leaf (steps 5-11), the panel's CholQR2 products, explicit
+ * residuals, C^T = A^T Q, reconstruction error, core QRs (steps 9-10),
+ * U = Q Qh.  out (n >= 11 doubles, may be NULL) receives the last launch's
+ * counters; EOD_EINVAL for n < 11 with non-NULL out.  Timing only: the
+ * results do not change. */
+EOD_API eod_status eod_abe_debug_batch_phases(int32_t enable, double *out, int64_t n);
 EOD_API eod_status eod_abe_debug_profile_read(int32_t kind, int64_t *launches, double *total_ms,
                                               double *total_flops, double *total_bytes);
 EOD_API int64_t eod_abe_debug_launch_count(void);

@@ -35,6 +35,7 @@ EXPORTED = [
     "eod_abe_debug_profile_read", "eod_abe_debug_launch_count", "eod_abe_fro_norm_noalloc",
     "eod_abe_debug_tc_gemm", "eod_abe_debug_f64_gemm", "eod_abe_debug_chol", "eod_abe_debug_bounded_wait",
     "eod_abe_debug_recip", "eod_abe_tuning_load", "eod_abe_tuning_lookup", "eod_abe_debug_f32_gemm",
+    "eod_abe_debug_batch_phases",
 ]
 
 
@@ -126,6 +127,8 @@ def _load() -> ctypes.CDLL:
     lib.eod_abe_tuning_lookup.restype = I32
     lib.eod_abe_debug_f32_gemm.argtypes = [I32, I32, I32, I64, I64, I64, F64, P, I64, P, I64, F64, P, I64, P]
     lib.eod_abe_debug_f32_gemm.restype = I32
+    lib.eod_abe_debug_batch_phases.argtypes = [I32, P, I64]
+    lib.eod_abe_debug_batch_phases.restype = I32
     lib.eod_abe_debug_f64_gemm.argtypes = [I32, I32, I32, I64, I64, I64, F64, P, I64, P, I64, F64, P, I64, P]
     lib.eod_abe_debug_f64_gemm.restype = I32
     lib.eod_abe_debug_chol.argtypes = [P, I64, I32, I32, F64, F64, F64, F64, P, P, I64, P, P]
@@ -161,6 +164,20 @@ eod_abe_debug_recip = _lib.eod_abe_debug_recip
 eod_abe_tuning_load = _lib.eod_abe_tuning_load
 eod_abe_tuning_lookup = _lib.eod_abe_tuning_lookup
 eod_abe_debug_f32_gemm = _lib.eod_abe_debug_f32_gemm
+eod_abe_debug_batch_phases = _lib.eod_abe_debug_batch_phases
+
+BATCH_PHASES = ("norm", "omega", "sketch", "deflate", "gram_leaf", "panel", "residual", "project", "err", "core",
+                "u")
+
+
+def batch_phases(enable: bool = True) -> dict:
+    """Turns the persistent launch's per-phase clock accounting on or off and
+    returns the last launch's counters (SM clock ticks summed over items)."""
+    out = (ctypes.c_double * len(BATCH_PHASES))()
+    st = _lib.eod_abe_debug_batch_phases(1 if enable else 0, out, len(BATCH_PHASES))
+    if st != EOD_OK:
+        raise EodError(st, "eod_abe_debug_batch_phases")
+    return dict(zip(BATCH_PHASES, list(out)))
 
 
 def tuning_lookup(key: str, a: int, b: int = 0, c: int = 0):

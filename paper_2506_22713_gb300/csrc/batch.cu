@@ -2,7 +2,8 @@
 // and ranks (the per-image use of Sec. 4.1) factored by a kernel whose CTAs
 // take matrices from an atomic work queue, largest first, and run the whole
 // method on each one without returning to the host: ||A||_F (the RelErr
-// denominator, and eps in relative mode), Alg. 1 with its block loop and its
+// denominator, and eps in relative mode; summed from the tiles of the first
+// sketch, which read every element once), Alg. 1 with its block loop and its
 // stop decision on the device (Omega_j, Y = A Omega_j, Y <- (I - Q Q^T) Y
 // twice, CholQR2 with the rank test folded into the first Cholesky, the
 // explicit residual for undecided pivots), Alg. 2 steps 8-11 (C^T = A^T Q,
@@ -47,10 +48,11 @@ static_assert(PT == 512, "the tile shapes below assume 512 threads");
 // copies (two steps in flight while one is multiplied; one barrier per
 // step); each thread owns a 4 x 4 block of the tile.  ERR: no store; the thread adds
 // (ref(i, j) - alpha acc(i, j))^2 to *ss instead (the reconstruction error,
-// each square exact, summed by TwoSum).  COMP: the 16-term partial sum of
-// each K step is added to a TwoSum pair (hi, lo) instead of running on in
-// one FP32 accumulator, so a long dot product (K = m or n) carries the
-// rounding of 16-term sums rather than of K-term ones: those errors, in the
+// each square exact, summed by TwoSum; the ref tile is copied to shared
+// memory, coalesced, while the K loop runs).  COMP: every four K steps the
+// 64-term partial sum is added to a TwoSum pair (hi, lo) instead of running
+// on in one FP32 accumulator, so a long dot product (K = m or n) carries the
+// rounding of 64-term sums rather than of K-term ones: those errors, in the
 // sketch and in the projections against Q, are what the singular-value
 // decay amplifies into the basis (about u sqrt(K) s_1 / s_r).
 constexpr int GK = 16;
@@ -74,9 +76,12 @@ struct TwoSumAcc {
 
 constexpr int GS = 3;   // pipeline stages
 
+constexpr int GFOLD = 4;   // K steps per compensated fold (64-term partial sums)
+
 template <int BN>
 __host__ __device__ constexpr int gemm_smem_floats() {
-    return GS * GK * ((PT / (BN / 4)) * 4 + 4) + GS * GK * (BN + 4);
+    // the stage ring, then (ERR) the reference tile, BN columns of BM + 4
+    return GS * GK * ((PT / (BN / 4)) * 4 + 4) + GS * GK * (BN + 4) + BN * ((PT / (BN / 4)) * 4 + 4);
 }
 
 // one 4-byte asynchronous copy global -> shared, zero-filled when !valid
@@ -92,14 +97,18 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <int BN, bool TA, bool TB, bool ERR, bool COMP>
 __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const float *__restrict__ A, int64_t lda,
                                       const float *__restrict__ B, int64_t ldb, float beta, float *C, int64_t ldc,
-                                      const float *__restrict__ ref, int64_t ldref, TwoSumAcc *ss, float *sm) {
+                                      const float *__restrict__ ref, int64_t ldref, TwoSumAcc *ss, float *sm,
+                                      TwoSumAcc *nrm, int *nonfinite) {
     constexpr int TX = BN / 4, TY = PT / TX, BM = TY * 4;
     constexpr int LAS = BM + 4, LBS = BN + 4;
     constexpr int AL = BM * GK / PT, BL = BN * GK / PT;
     float *As = sm;                     // [GS][GK][LAS]
     float *Bs = sm + GS * GK * LAS;     // [GS][GK][LBS]
+    float *Rs = Bs + GS * GK * LBS;     // ERR: [BN][LAS], the tile of ref
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int nk = (K + GK - 1) / GK;
+    TwoSumAcc nacc;                    // the norm's share of this thread, in registers
+    int nbad = 0;
     for (int m0 = 0; m0 < M; m0 += BM) {
         for (int n0 = 0; n0 < N; n0 += BN) {
             float acc[4][4], hi[4][4], lo[4][4];
@@ -138,6 +147,15 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
                     cp_async4(bs + kk * LBS + j, v ? b_t + q * sb_q : B, v);
                 }
             };
+            if (ERR) {
+                // the reference tile, column by column (coalesced), in the
+                // first stage's group: it lands while the K loop runs
+                for (int e = tid; e < BM * BN; e += PT) {
+                    const int i = e % BM, j = e / BM;
+                    const bool v = m0 + i < M && n0 + j < N;
+                    cp_async4(Rs + j * LAS + i, v ? ref + (m0 + i) + (int64_t)(n0 + j) * ldref : ref, v);
+                }
+            }
 #pragma unroll
             for (int t = 0; t < GS - 1; ++t) {
                 if (t < nk) issue(t);
@@ -146,6 +164,19 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
             for (int t = 0; t < nk; ++t) {
                 cp_async_wait<GS - 2>();      // stage t has landed (this thread's copies)
                 __syncthreads();              // ... everyone's; buffer (t - 1) % GS is free
+                if (nrm) {
+                    // the squares of the A elements this thread copied (zero
+                    // outside A): with a single column tile every element of A
+                    // passes through exactly once
+                    const float *as = As + (t % GS) * GK * LAS;
+#pragma unroll
+                    for (int q = 0; q < AL; ++q) {
+                        const int i = TA ? ia + q * (PT / GK) : ia, kk = TA ? ka : ka + q * (PT / BM);
+                        const float v = as[kk * LAS + i];
+                        nbad |= !isfinite(v);
+                        nacc.add(v, v);
+                    }
+                }
                 if (t + GS - 1 < nk) issue(t + GS - 1);
                 cp_async_commit();
                 const int buf = t % GS;
@@ -160,7 +191,7 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
 #pragma unroll
                         for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
                 }
-                if (COMP) {
+                if (COMP && ((t + 1) % GFOLD == 0 || t + 1 == nk)) {
 #pragma unroll
                     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -185,7 +216,7 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
                     if (gj >= N) continue;
                     const float v = alpha * (COMP ? hi[x][y] + lo[x][y] : acc[x][y]);
                     if (ERR) {
-                        const float d = ref[gi + (int64_t)gj * ldref] - v;
+                        const float d = Rs[(tx * 4 + y) * LAS + ty * 4 + x] - v;
                         ss->add(d, d);
                     } else {
                         float *c = C + gi + (int64_t)gj * ldc;
@@ -193,19 +224,63 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
                     }
                 }
             }
+            if (ERR) __syncthreads();         // the next tile's reference copies overwrite Rs
         }
+    }
+    if (nrm) {
+        // fold this call's share into the caller's accumulator
+        const double v = nacc.value();
+        const float h = (float)v;
+        nrm->add(h, 1.f);
+        nrm->add((float)(v - (double)h), 1.f);
+        *nonfinite |= nbad;
     }
 }
 
-// op(A) op(B) with the narrow tile when N <= 32; COMP for the long dot
-// products (K = m or n)
+// op(A) op(B); COMP for the long dot products (K = m or n)
+// With nrm (N <= 64: one column tile) the squares of every element of
+// op(A) are also summed into *nrm and its finiteness ORed into *nonfinite.
 template <bool TA, bool TB, bool COMP = false>
 __device__ void cta_mm(int M, int N, int K, float alpha, const float *A, int64_t lda, const float *B, int64_t ldb,
-                       float beta, float *C, int64_t ldc, float *sm) {
-    if (N <= 32)
-        cta_gemm<32, TA, TB, false, COMP>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr, sm);
-    else
-        cta_gemm<64, TA, TB, false, COMP>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr, sm);
+                       float beta, float *C, int64_t ldc, float *sm, TwoSumAcc *nrm = nullptr,
+                       int *nonfinite = nullptr) {
+    // whole 64-column tiles, then a remainder of at most 32 columns on the
+    // narrow tile (N = 83 computes 96 columns, not 128)
+    const int n64 = (N % 64 != 0 && N % 64 <= 32) ? N / 64 * 64 : N;
+    if (n64 > 0)
+        cta_gemm<64, TA, TB, false, COMP>(M, n64, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr, sm,
+                                          nrm, nonfinite);
+    if (n64 < N) {
+        const float *Bn = TB ? B + n64 : B + (int64_t)n64 * ldb;
+        cta_gemm<32, TA, TB, false, COMP>(M, N - n64, K, alpha, A, lda, Bn, ldb, beta, C + (int64_t)n64 * ldc, ldc,
+                                          nullptr, 0, nullptr, sm, nrm, nonfinite);
+    }
+    __syncthreads();
+}
+
+// S(0:M) = A^T z (A: K x M, ld lda): a warp per output, exact products
+// summed by TwoSum per lane, then an FP64 warp sum
+__device__ void cta_tmv(int M, int K, const float *__restrict__ A, int64_t lda, const float *__restrict__ z,
+                        float *S) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = warp; j < M; j += PT / 32) {
+        TwoSumAcc a;
+        const float *col = A + (int64_t)j * lda;
+        for (int i = lane; i < K; i += 32) a.add(col[i], z[i]);
+        const double v = warp_sum(a.value());
+        if (lane == 0) S[j] = (float)v;
+    }
+    __syncthreads();
+}
+
+// z(0:m) -= A S (A: m x K, ld lda): a thread per row
+__device__ void cta_mv_sub(int64_t m, int K, const float *__restrict__ A, int64_t lda, const float *__restrict__ S,
+                           float *z) {
+    for (int64_t i = threadIdx.x; i < m; i += PT) {
+        float acc = 0.f;
+        for (int l = 0; l < K; ++l) acc = fmaf(A[i + (int64_t)l * lda], S[l], acc);
+        z[i] -= acc;
+    }
     __syncthreads();
 }
 
@@ -302,34 +377,6 @@ __device__ __noinline__ void cta_gram(const float *__restrict__ Y, int64_t rows,
 }
 
 // --------------------------------------------------------- small helpers ----
-// sum of squares of an FP32 matrix (TwoSum accumulation per thread, FP64
-// block sum) and whether it holds a non-finite value
-__device__ double cta_sumsq(const float *__restrict__ A, int64_t m, int64_t n, int64_t lda, int *bad,
-                            double *red) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    TwoSumAcc acc;
-    int nf = 0;
-    for (int64_t j = warp; j < n; j += PT / 32) {
-        const float *col = A + j * lda;
-        int64_t i = lane;
-        for (; i + 96 < m; i += 128) {
-            const float v0 = col[i], v1 = col[i + 32], v2 = col[i + 64], v3 = col[i + 96];
-            nf |= !isfinite(v0) | !isfinite(v1) | !isfinite(v2) | !isfinite(v3);
-            acc.add(v0, v0);
-            acc.add(v1, v1);
-            acc.add(v2, v2);
-            acc.add(v3, v3);
-        }
-        for (; i < m; i += 32) {
-            const float v = col[i];
-            nf |= !isfinite(v);
-            acc.add(v, v);
-        }
-    }
-    *bad = __syncthreads_or(nf);
-    return block_sum(acc.value(), red);
-}
-
 // FP64 sum of squares of a vector of FP32 values
 __device__ double cta_norm2(const float *z, int64_t m, double *red) {
     double acc = 0.0;
@@ -390,6 +437,7 @@ struct PParams {
     unsigned char *scratch;   // one region per CTA
     int64_t stride, mmax, nmax;
     unsigned *next;           // the work queue's counter
+    unsigned long long *phase;   // null, or kPPhases cycle counters summed over items (measurement)
     int count, k, tol_mode, compute_err;
     double tol;
     uint64_t seed;
@@ -433,6 +481,25 @@ __device__ __noinline__ void leaf(const double *G, int w, int decide, double eps
                         (double *)sm);
     __syncthreads();
 }
+// Per-phase cycle accounting of the measurement hook: thread 0 adds the
+// SM clock ticks since the previous mark to the phase's counter.
+enum PPhase { PH_NORM, PH_OMEGA, PH_SKETCH, PH_DEFLATE, PH_GRAM_LEAF, PH_PANEL, PH_RESIDUAL, PH_PROJECT, PH_ERR,
+              PH_CORE, PH_U };
+struct PhaseClock {
+    unsigned long long *ctr;
+    long long t;
+    __device__ __forceinline__ void start(unsigned long long *c) {
+        ctr = c;
+        t = c ? (long long)clock64() : 0;
+    }
+    __device__ __forceinline__ void mark(int ph) {
+        if (!ctr) return;
+        const long long now = (long long)clock64();
+        if (threadIdx.x == 0) atomicAdd(ctr + ph, (unsigned long long)(now - t));
+        t = now;
+    }
+};
+
 // One matrix, start to end, on this CTA.
 __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *info, double *red) {
     const PItem it = P.items[idx];
@@ -465,21 +532,12 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
         }
     };
 
-    // ||A||_F and finiteness
-    int bad = 0;
-    norm = sqrt(cta_sumsq(it.A, m, n, lda, &bad, red));
-    if (bad) { finish(EOD_ENONFINITE, -1.0); return; }
-    eps = P.tol_mode == EOD_TOL_REL_FRO ? P.tol * norm : P.tol;
-    if (norm == 0.0) {
-        if (tid == 0) tdg[0] = 0.0;
-        ntd = 1;
-        finish(EOD_OK, P.compute_err ? 0.0 : -1.0);
-        return;
-    }
+    PhaseClock pc;
+    pc.start(P.phase);
 
     // ---- Alg. 1 ----
     const int64_t cap = m < n ? m : n;
-    const double eps2 = eps * eps;
+    double eps2 = 0.0;
     const double delta_coef = 64.0 * ((double)P.k + sqrt((double)m)) * kU64;
     const double rho = 1e-6;
     bool stop = false;
@@ -487,7 +545,30 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
         const int f = (int)((int64_t)P.k < cap - kept ? (int64_t)P.k : cap - kept);
         ++blocks;
         cta_omega(n, kept, f, P.seed, it.batch, Om);                                       // step 3
-        cta_mm<false, false, true>((int)m, f, (int)n, 1.f, it.A, lda, Om, n, 0.f, Y, m, smf);    // Y = A Omega_j
+        pc.mark(PH_OMEGA);
+        if (blocks == 1) {
+            // the first sketch reads every element of A once: ||A||_F and the
+            // finiteness check come from its shared-memory tiles
+            TwoSumAcc nrm;
+            int nf = 0;
+            cta_mm<false, false, true>((int)m, f, (int)n, 1.f, it.A, lda, Om, n, 0.f, Y, m, smf, &nrm, &nf);
+            const int bad = __syncthreads_or(nf);
+            norm = sqrt(block_sum(nrm.value(), red));
+            pc.mark(PH_SKETCH);
+            if (bad) { finish(EOD_ENONFINITE, -1.0); return; }
+            eps = P.tol_mode == EOD_TOL_REL_FRO ? P.tol * norm : P.tol;
+            eps2 = eps * eps;
+            if (norm == 0.0) {
+                if (tid == 0) tdg[0] = 0.0;
+                ntd = 1;
+                blocks = 0;
+                finish(EOD_OK, P.compute_err ? 0.0 : -1.0);
+                return;
+            }
+        } else {
+            cta_mm<false, false, true>((int)m, f, (int)n, 1.f, it.A, lda, Om, n, 0.f, Y, m, smf);   // Y = A Omega_j
+            pc.mark(PH_SKETCH);
+        }
         int cur = 0;
         while (!stop && cur < f) {
             float *Yc = Y + (int64_t)cur * m;
@@ -496,8 +577,10 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
                 cta_mm<true, false, true>(kept, wdt, (int)m, 1.f, it.Q, m, Yc, m, 0.f, S, kPRcap, smf);
                 cta_mm<false, false>((int)m, wdt, kept, -1.f, it.Q, m, S, kPRcap, 1.f, Yc, m, smf);
             }
+            pc.mark(PH_DEFLATE);
             cta_gram(Yc, m, wdt, m, G, kPRcap, sm);                                          // step 5, pass 1
             leaf(G, wdt, 1, eps2, delta_coef, rho, R1, R1i, info, 0.0, sm);                    // steps 6-11
+            pc.mark(PH_GRAM_LEAF);
             const int p = info[0], code = info[1];
             __syncthreads();
             if (p > 0) {
@@ -514,6 +597,7 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
                 for (int l = tid; l < p; l += PT) tdg[ntd + l] = fabs(R1[l + l * kPRcap] * R2[l + l * kPRcap]);
                 ntd += p;
                 kept += p;
+                pc.mark(PH_PANEL);
             }
             if (code == CHOL_ALL) {
                 cur = f;
@@ -521,10 +605,11 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
                 // column p: its explicit residual after two more projections
                 float *z = Yc + (int64_t)p * m;
                 for (int pass = 0; pass < 2 && kept > 0; ++pass) {
-                    cta_mm<true, false, true>(kept, 1, (int)m, 1.f, it.Q, m, z, m, 0.f, S, kPRcap, smf);
-                    cta_mm<false, false>((int)m, 1, kept, -1.f, it.Q, m, S, kPRcap, 1.f, z, m, smf);
+                    cta_tmv(kept, (int)m, it.Q, m, z, S);
+                    cta_mv_sub(m, kept, it.Q, m, S, z);
                 }
                 const double t = sqrt(cta_norm2(z, m, red));
+                pc.mark(PH_RESIDUAL);
                 if (tid == 0) tdg[ntd] = t;
                 ++ntd;
                 if (code == CHOL_BELOW) {
@@ -551,13 +636,15 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
 
     // ---- Alg. 2 step 8: C (n x r) = A^T Q ----
     cta_mm<true, false, true>((int)n, r, (int)m, 1.f, it.A, lda, it.Q, m, 0.f, it.C, n, smf);
+    pc.mark(PH_PROJECT);
     double rel = -1.0;
     if (P.compute_err) {                                                   // ||A - Q C^T||_F / ||A||_F
         TwoSumAcc ssq;
-        cta_gemm<64, false, true, true, false>((int)m, (int)n, r, 1.f, it.Q, m, it.C, n, 0.f, nullptr, 0, it.A, lda, &ssq,
-                                        smf);
+        cta_gemm<64, false, true, true, false>((int)m, (int)n, r, 1.f, it.Q, m, it.C, n, 0.f, nullptr, 0, it.A, lda,
+                                               &ssq, smf, nullptr, nullptr);
         rel = sqrt(block_sum(ssq.value(), red)) / norm;
     }
+    pc.mark(PH_ERR);
 
     // ---- steps 9-10: C^T = V R, then R^T = Qh D (CholQR2 each) ----
     cta_gram(it.C, n, r, n, G, kPRcap, sm);
@@ -584,9 +671,11 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
     cta_to_f32(R2i, kPRcap, r, Rf, kPRcap, false);
     cta_mm<false, false>(r, r, r, 1.f, W2, kPRcap, Rf, kPRcap, 0.f, Qh, kPRcap, smf);
     cta_triu_mul(R2, kPRcap, R1, kPRcap, it.D, r, r);                    // D = R2 R1 of this pair
+    pc.mark(PH_CORE);
 
     // ---- step 11: U = Q Qh ----
     cta_mm<false, false>((int)m, r, r, 1.f, it.Q, m, Qh, kPRcap, 0.f, it.U, m, smf);
+    pc.mark(PH_U);
     finish(EOD_OK, rel);
 }
 
@@ -622,6 +711,10 @@ struct Pool {
 };
 std::mutex g_pool_mu;
 std::unordered_map<const void *, Pool *> g_pool_of;   // keyed by each factor set's Q
+
+std::atomic<int> g_phase_on{0};
+std::mutex g_phase_mu;
+unsigned long long g_phase_last[kPPhases] = {};
 
 }  // namespace
 
@@ -684,8 +777,9 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         off[e] = pool_bytes;
         pool_bytes += 2 * up(4 * m[i] * c) + 2 * up(4 * n[i] * c) + up(8 * c * c);
     }
-    void *pool = nullptr;
-    if (cudaMalloc(&pool, (size_t)pool_bytes) != cudaSuccess) {
+    cudaStream_t caller = (cudaStream_t)o.stream;
+    void *pool = nullptr;   // stream-ordered, from the library's pool (eod_abe_free's cudaFree releases it)
+    if (lib_malloc_async(&pool, (size_t)pool_bytes, caller) != cudaSuccess) {
         cudaGetLastError();
         all_back();
         return EOD_OK;
@@ -710,11 +804,10 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         horder[e] = (int32_t)e;
     }
 
-    cudaStream_t caller = (cudaStream_t)o.stream;
     int dev = 0, sms = kNumSMs;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(pool);
+        cudaFreeAsync(pool, caller);
         all_back();
         return EOD_OK;
     }
@@ -735,7 +828,10 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         double *dtd;
         unsigned char *scratch;
         unsigned *next;
+        unsigned long long *dphase = nullptr;
+        const bool phases = g_phase_on.load() != 0;
         eod_status st = ar.get(&ditems, (size_t)ne);
+        if (st == EOD_OK && phases) st = ar.get(&dphase, (size_t)kPPhases);
         if (st == EOD_OK) st = ar.get(&dorder, (size_t)ne);
         if (st == EOD_OK) st = ar.get(&dres, (size_t)ne);
         if (st == EOD_OK) st = ar.get(&dtd, (size_t)ne * kPTdCap);
@@ -743,6 +839,7 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         if (st == EOD_OK) st = ar.get(&next, (size_t)1);
         cudaError_t e = st == EOD_OK ? cudaSuccess : cudaErrorMemoryAllocation;
         if (e == cudaSuccess) e = cudaMemcpyAsync(ditems, hitems.data(), sizeof(PItem) * ne, cudaMemcpyHostToDevice, caller);
+        if (e == cudaSuccess && dphase) e = cudaMemsetAsync(dphase, 0, sizeof(unsigned long long) * kPPhases, caller);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dorder, horder.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, caller);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
@@ -760,6 +857,7 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         P.mmax = mmax;
         P.nmax = nmax;
         P.next = next;
+        P.phase = dphase;
         P.count = (int)ne;
         P.k = k;
         P.tol_mode = o.tol_mode;
@@ -793,6 +891,10 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         if (launched) e = cudaStreamSynchronize(ps);
         if (e == cudaSuccess) e = cudaMemcpy(hres.data(), dres, sizeof(PRes) * ne, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) e = cudaMemcpy(htd.data(), dtd, sizeof(double) * ne * kPTdCap, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && dphase) {
+            std::lock_guard<std::mutex> lk(g_phase_mu);
+            e = cudaMemcpy(g_phase_last, dphase, sizeof(g_phase_last), cudaMemcpyDeviceToHost);
+        }
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (ready) cudaEventDestroy(ready);
@@ -802,8 +904,8 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         }
         if (e != cudaSuccess) {
             cudaGetLastError();
+            cudaFreeAsync(pool, caller);
             cudaStreamSynchronize(caller);
-            cudaFree(pool);
             if (launched) return EOD_ECUDA;   // the launch itself failed: no item is retried
             all_back();
             return EOD_OK;
@@ -866,7 +968,7 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         per_item[i] = EOD_OK;
     }
     if (pl->refs == 0) {
-        cudaFree(pool);
+        cudaFreeAsync(pool, caller);
         delete pl;
     }
     std::sort(fallback.begin(), fallback.end());
@@ -874,3 +976,20 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
 }
 
 }  // namespace eod
+
+// Measurement hook of the persistent batched launch: with enable != 0 every
+// later launch sums, per phase of an item, the SM clock ticks its CTAs spent
+// there (kPPhases counters: unused (the norm is summed in the first
+// sketch), Omega, sketch, projection against Q, Gram
+// and rank-test leaf, the panel's CholQR2 products, explicit residuals,
+// projection C = A^T Q, reconstruction error, core QRs, U = Q Qh); out
+// receives the last launch's counters (n >= kPPhases).  Timing only.
+extern "C" eod_status eod_abe_debug_batch_phases(int32_t enable, double *out, int64_t n) {
+    using namespace eod;
+    g_phase_on.store(enable ? 1 : 0);
+    if (!out) return EOD_OK;
+    if (n < kPPhases) return EOD_EINVAL;
+    std::lock_guard<std::mutex> lk(g_phase_mu);
+    for (int i = 0; i < kPPhases; ++i) out[i] = (double)g_phase_last[i];
+    return EOD_OK;
+}

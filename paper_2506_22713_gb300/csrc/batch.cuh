@@ -13,6 +13,7 @@ constexpr int kPKmax = 64;        // largest block size k of the persistent form
 constexpr int kPTdCap = kPRcap + 2;
 constexpr int kPFallback = -1;    // item status: left to the single-matrix path
 constexpr int64_t kPMaxDim = 16384;   // largest m or n of an item of the persistent form
+constexpr int kPPhases = 11;          // phases of the measurement hook
 
 // Factors items of FP32 data in one persistent launch on `s`.  Items that
 // finish there get their factors in out[i] and status in per_item[i];
