@@ -46,8 +46,20 @@ def _range(v, lo=0.67, hi=1.5):
 
 # ------------------------------------------------------------- FP32 tiles --
 # (M, N, K, ta, tb): the FP32 products of the mixed and plain FP32 paths on
-# the 8192^2 harmonic (rank 455, k 64) and 2048^2 image (rank 2037) workloads
+# the 8192^2 harmonic (rank 455) and 2048^2 image (rank 2037) workloads, at
+# k = 64 and at the block sizes the table's block_k rows pick (96 mixed, 128
+# plain): the deflation's K (or M) grows with the basis, so two points each
 F32_SHAPES = [
+    (8192, 96, 96, 0, 0),     # P = Y R^-1, k = 96
+    (8192, 96, 192, 0, 0),    # Y -= Q S, k = 96
+    (8192, 96, 384, 0, 0),
+    (192, 96, 8192, 1, 0),    # S = Q^T Y, k = 96
+    (384, 96, 8192, 1, 0),
+    (8192, 128, 256, 0, 0),   # Y -= Q S, k = 128
+    (256, 128, 8192, 1, 0),   # S = Q^T Y, k = 128
+    (2048, 96, 96, 0, 0),
+    (2048, 96, 768, 0, 0),
+    (768, 96, 2048, 1, 0),
     (8192, 455, 455, 0, 0),   # U = Q Qh
     (8192, 256, 256, 0, 0),   # CholQR solve, diagonal panel
     (8192, 199, 256, 0, 0),   # CholQR solve, trailing columns
@@ -214,6 +226,8 @@ def main(argv=None):
     p.add_argument("--out", required=True, help="where to write the table")
     p.add_argument("--quick", action="store_true", help="fewer cases (smoke run)")
     p.add_argument("--skip", default="", help="comma list of f32_tile,block_k,batch_workers to skip")
+    p.add_argument("--merge", action="store_true",
+                   help="keep the rows (and their notes) of skipped parts from the table already at --out")
     args = p.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -237,6 +251,21 @@ def main(argv=None):
         r, n = tune_batch_workers(eod, torch, candidates=(8, 16) if args.quick else (4, 8, 12, 16, 24, 32))
         rows += r
         notes += n
+    if args.merge and os.path.exists(args.out):
+        kept_rows, kept_notes = [], []
+        with open(args.out) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith("# measured: "):
+                    note = line[len("# measured: "):]
+                    if note.split(" ", 1)[0] in skip:
+                        kept_notes.append(note)
+                elif line and not line.startswith("#"):
+                    f = line.split()
+                    if f[0] in skip:
+                        kept_rows.append(tuple([f[0]] + [int(x) for x in f[1:]]))
+        rows += kept_rows
+        notes += kept_notes
     meta = {"when": datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%dT%H:%M:%SZ"),
             "gpu": torch.cuda.get_device_name(0), "torch": torch.__version__,
             "seconds": f"{time.time() - t0:.0f}"}

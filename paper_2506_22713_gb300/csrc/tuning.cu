@@ -17,6 +17,7 @@
 
 #include <dlfcn.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -91,20 +92,35 @@ void ensure_loaded() {
 
 }  // namespace
 
+// Among the rows of `key` whose ranges hold (a, b, c), the nearest: the
+// smallest sum over the three axes of |log(x / centre)|, centre the
+// geometric mean of the row's bounds (the shape it was measured at, for the
+// autotuner's ranges); ties go to the earlier row.
 bool tuned_value(const char *key, int64_t a, int64_t b, int64_t c, int64_t *out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     ensure_loaded();
     const int64_t x[3] = {a, b, c};
+    const TuneRow *best = nullptr;
+    double best_d = 0.0;
     for (const TuneRow &r : g_rows) {
         if (r.key != key) continue;
         bool in = true;
         for (int i = 0; i < 3; ++i) in = in && x[i] >= r.lo[i] && x[i] <= r.hi[i];
-        if (in) {
-            *out = r.value;
-            return true;
+        if (!in) continue;
+        double d = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            const double lo = std::max<double>((double)r.lo[i], 1.0), hi = std::max<double>((double)r.hi[i], 1.0);
+            const double xi = std::max<double>((double)x[i], 1.0);
+            d += std::fabs(std::log(xi) - 0.5 * (std::log(lo) + std::log(hi)));
+        }
+        if (!best || d < best_d) {
+            best = &r;
+            best_d = d;
         }
     }
-    return false;
+    if (!best) return false;
+    *out = best->value;
+    return true;
 }
 
 }  // namespace eod

@@ -106,14 +106,17 @@ def test_bounded_wait_hook_rejects_bad_budgets(eod):
 
 
 def test_tuning_table_parse_lookup_and_reload(eod, tmp_path):
-    """The autotuner's table: ranges match inclusively, the first matching
-    row wins, a malformed file is refused without touching the loaded table,
-    a missing file empties it (host-side only)."""
+    """The autotuner's table: ranges match inclusively, of several matching
+    rows the nearest (log distance to the centre of each range) wins, a
+    malformed file is refused without touching the loaded table, a missing
+    file empties it (host-side only)."""
     good = tmp_path / "t.txt"
     good.write_text("# comment\n"
                     "block_k 2 2 4096 16384 4096 16384 96   # mixed, large\n"
                     "block_k 0 3 1 100000 1 100000 48\n"
-                    "f32_tile 4096 1000000 256 512 128 100000 128\n")
+                    "f32_tile 4096 1000000 256 512 128 100000 128\n"
+                    "f32_tile 5488 12289 42 97 257 577 128   # measured at N = 64, K = 384\n"
+                    "f32_tile 5488 12289 64 145 128 577 64   # measured at N = 96, K = 272\n")
     try:
         assert eod.eod_abe_tuning_load(str(good).encode()) == eod.EOD_OK
         assert eod.tuning_lookup("block_k", 2, 8192, 8192) == 96
@@ -121,7 +124,10 @@ def test_tuning_table_parse_lookup_and_reload(eod, tmp_path):
         assert eod.tuning_lookup("block_k", 2, 2048, 8192) == 48
         assert eod.tuning_lookup("block_k", 4, 10, 10) is None
         assert eod.tuning_lookup("f32_tile", 8192, 455, 455) == 128
-        assert eod.tuning_lookup("f32_tile", 8192, 64, 455) is None
+        assert eod.tuning_lookup("f32_tile", 8192, 64, 455) == 128      # only the N = 64 row holds it
+        assert eod.tuning_lookup("f32_tile", 8192, 96, 384) == 64       # both hold it; N = 96 is nearer
+        assert eod.tuning_lookup("f32_tile", 8192, 64, 384) == 128      # both hold it; N = 64 is nearer
+        assert eod.tuning_lookup("f32_tile", 8192, 30, 384) is None
         assert eod.tuning_lookup("batch_workers", 256, 1000, 1000) is None
         bad = tmp_path / "bad.txt"
         bad.write_text("block_k 2 1 1 2 1 2 7\n")          # lo > hi
