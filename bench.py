@@ -236,7 +236,7 @@ KIND_SOURCES = {
     "batch": ["paper_2506_22713_gb300/csrc/batch.cu", "paper_2506_22713_gb300/csrc/chol_leaf.cuh"],
     "oz_gemm": ["paper_2506_22713_gb300/csrc/oz_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"],
     "tc_gemm": ["paper_2506_22713_gb300/csrc/tc_gemm.cu", "paper_2506_22713_gb300/csrc/tc_ptx.cuh"],
-    "chol": ["paper_2506_22713_gb300/csrc/chol.cu"],
+    "chol": ["paper_2506_22713_gb300/csrc/chol.cu", "paper_2506_22713_gb300/csrc/chol_leaf.cuh"],
     "gemm_simt": ["paper_2506_22713_gb300/csrc/gemm_simt.cu"],
     "gemm_simt_f32": ["paper_2506_22713_gb300/csrc/gemm_simt.cu", "paper_2506_22713_gb300/csrc/gram.cu"],
     "stream": ["paper_2506_22713_gb300/csrc/stream_kernels.cu"],
@@ -696,6 +696,10 @@ def compare_batched(eod, steps, warmup):
                 "ms": pk["ms"], "model_gflop": fl / 1e9, "achieved_gflops": ach, "bound": "alu",
                 "peak_gflops": FP32_PEAK_GFLOPS, "frac": ach / FP32_PEAK_GFLOPS,
                 "peak_source": "FP32 from unit counts: 152 SMs x 128 FFMA/clk x 2 flop x 2070 MHz"}
+            if not clip:
+                tr = _traffic_for("batch", KIND_SOURCES["batch"])
+                res["mixed_bf16"]["persistent_kernel"]["traffic"] = tr[0] if tr else None
+                res["mixed_bf16"]["persistent_kernel"]["traffic_launch"] = tr[1] if tr else None
         del r
         eq = sum(a == b for a, b in zip(ranks["mixed_bf16"], ranks["plain_f64"]))
         drel = max(abs(a - b) for a, b in zip(rels["mixed_bf16"], rels["plain_f64"]))
