@@ -78,10 +78,10 @@ constexpr int GS = 3;   // pipeline stages
 
 constexpr int GFOLD = 4;   // K steps per compensated fold (64-term partial sums)
 
-template <int BN>
+template <int BN, int TM, bool ERR>
 __host__ __device__ constexpr int gemm_smem_floats() {
     // the stage ring, then (ERR) the reference tile, BN columns of BM + 4
-    return GS * GK * ((PT / (BN / 4)) * 4 + 4) + GS * GK * (BN + 4) + BN * ((PT / (BN / 4)) * 4 + 4);
+    return GS * GK * ((PT / (BN / 4)) * TM + 4) + GS * GK * (BN + 4) + (ERR ? BN * ((PT / (BN / 4)) * TM + 4) : 0);
 }
 
 // one 4-byte asynchronous copy global -> shared, zero-filled when !valid
@@ -94,12 +94,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <int BN, bool TA, bool TB, bool ERR, bool COMP>
+template <int BN, bool TA, bool TB, bool ERR, bool COMP, int TM>
 __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const float *__restrict__ A, int64_t lda,
                                       const float *__restrict__ B, int64_t ldb, float beta, float *C, int64_t ldc,
                                       const float *__restrict__ ref, int64_t ldref, TwoSumAcc *ss, float *sm,
                                       TwoSumAcc *nrm, int *nonfinite) {
-    constexpr int TX = BN / 4, TY = PT / TX, BM = TY * 4;
+    constexpr int TX = BN / 4, TY = PT / TX, BM = TY * TM;
+    constexpr bool LO = COMP && TM == 4;   // a TwoSum pair per output; TM = 8 keeps one running FP32 sum
     constexpr int LAS = BM + 4, LBS = BN + 4;
     constexpr int AL = BM * GK / PT, BL = BN * GK / PT;
     float *As = sm;                     // [GS][GK][LAS]
@@ -111,11 +112,15 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
     int nbad = 0;
     for (int m0 = 0; m0 < M; m0 += BM) {
         for (int n0 = 0; n0 < N; n0 += BN) {
-            float acc[4][4], hi[4][4], lo[4][4];
+            float acc[TM][4], hi[COMP ? TM : 1][4], lo[LO ? TM : 1][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < TM; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = hi[a][b] = lo[a][b] = 0.f;
+                for (int b = 0; b < 4; ++b) {
+                    acc[a][b] = 0.f;
+                    if (COMP) hi[a][b] = 0.f;
+                    if (LO) lo[a][b] = 0.f;
+                }
             // stage t of the K loop into buffer t % GS: each thread copies
             // AL elements of the A tile and BL of the B tile, element (i, k)
             // of op(A) to As[k][i] and (k, j) of op(B) to Bs[k][j] (the
@@ -180,26 +185,38 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
                 if (t + GS - 1 < nk) issue(t + GS - 1);
                 cp_async_commit();
                 const int buf = t % GS;
-                const float *as = As + buf * GK * LAS + ty * 4, *bs = Bs + buf * GK * LBS + tx * 4;
+                const float *as = As + buf * GK * LAS + ty * TM, *bs = Bs + buf * GK * LBS + tx * 4;
 #pragma unroll
                 for (int kk = 0; kk < GK; ++kk) {
-                    const float4 a = *(const float4 *)(as + kk * LAS);
-                    const float4 b = *(const float4 *)(bs + kk * LBS);
-                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                    float av[TM];
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int h = 0; h < TM / 4; ++h) {
+                        const float4 a = *(const float4 *)(as + kk * LAS + 4 * h);
+                        av[4 * h] = a.x;
+                        av[4 * h + 1] = a.y;
+                        av[4 * h + 2] = a.z;
+                        av[4 * h + 3] = a.w;
+                    }
+                    const float4 b = *(const float4 *)(bs + kk * LBS);
+                    const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int x = 0; x < TM; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
                 }
                 if (COMP && ((t + 1) % GFOLD == 0 || t + 1 == nk)) {
 #pragma unroll
-                    for (int x = 0; x < 4; ++x)
+                    for (int x = 0; x < TM; ++x)
 #pragma unroll
                         for (int y = 0; y < 4; ++y) {
-                            const float a = hi[x][y], b = acc[x][y];
-                            const float t2 = a + b, z = t2 - a;
-                            lo[x][y] += (a - (t2 - z)) + (b - z);
-                            hi[x][y] = t2;
+                            if (LO) {
+                                const float a = hi[x][y], b = acc[x][y];
+                                const float t2 = a + b, z = t2 - a;
+                                lo[LO ? x : 0][y] += (a - (t2 - z)) + (b - z);
+                                hi[x][y] = t2;
+                            } else {
+                                hi[x][y] += acc[x][y];
+                            }
                             acc[x][y] = 0.f;
                         }
                 }
@@ -207,16 +224,16 @@ __device__ __noinline__ void cta_gemm(int M, int N, int K, float alpha, const fl
             cp_async_wait<0>();
             __syncthreads();                  // the buffers are reused by the next tile
 #pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const int gi = m0 + ty * 4 + x;
+            for (int x = 0; x < TM; ++x) {
+                const int gi = m0 + ty * TM + x;
                 if (gi >= M) continue;
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
                     const int gj = n0 + tx * 4 + y;
                     if (gj >= N) continue;
-                    const float v = alpha * (COMP ? hi[x][y] + lo[x][y] : acc[x][y]);
+                    const float v = alpha * (COMP ? (LO ? hi[x][y] + lo[LO ? x : 0][y] : hi[x][y]) : acc[x][y]);
                     if (ERR) {
-                        const float d = Rs[(tx * 4 + y) * LAS + ty * 4 + x] - v;
+                        const float d = Rs[(tx * 4 + y) * LAS + ty * TM + x] - v;
                         ss->add(d, d);
                     } else {
                         float *c = C + gi + (int64_t)gj * ldc;
@@ -246,14 +263,22 @@ __device__ void cta_mm(int M, int N, int K, float alpha, const float *A, int64_t
                        int *nonfinite = nullptr) {
     // whole 64-column tiles, then a remainder of at most 32 columns on the
     // narrow tile (N = 83 computes 96 columns, not 128)
+    // 64-column tiles with 8-row register blocks (256 x 64 per CTA) when M
+    // fills them, else 4-row ones (128 x 64); 32-column tiles keep 4-row
+    // blocks (256 x 32: with 8 rows their 16 copies per thread and step spill)
     const int n64 = (N % 64 != 0 && N % 64 <= 32) ? N / 64 * 64 : N;
-    if (n64 > 0)
-        cta_gemm<64, TA, TB, false, COMP>(M, n64, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr, sm,
-                                          nrm, nonfinite);
+    if (n64 > 0) {
+        if (M >= 192)
+            cta_gemm<64, TA, TB, false, COMP, 8>(M, n64, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr,
+                                                 sm, nrm, nonfinite);
+        else
+            cta_gemm<64, TA, TB, false, COMP, 4>(M, n64, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, 0, nullptr,
+                                                 sm, nrm, nonfinite);
+    }
     if (n64 < N) {
         const float *Bn = TB ? B + n64 : B + (int64_t)n64 * ldb;
-        cta_gemm<32, TA, TB, false, COMP>(M, N - n64, K, alpha, A, lda, Bn, ldb, beta, C + (int64_t)n64 * ldc, ldc,
-                                          nullptr, 0, nullptr, sm, nrm, nonfinite);
+        cta_gemm<32, TA, TB, false, COMP, 4>(M, N - n64, K, alpha, A, lda, Bn, ldb, beta, C + (int64_t)n64 * ldc,
+                                             ldc, nullptr, 0, nullptr, sm, nrm, nonfinite);
     }
     __syncthreads();
 }
@@ -640,8 +665,8 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
     double rel = -1.0;
     if (P.compute_err) {                                                   // ||A - Q C^T||_F / ||A||_F
         TwoSumAcc ssq;
-        cta_gemm<64, false, true, true, false>((int)m, (int)n, r, 1.f, it.Q, m, it.C, n, 0.f, nullptr, 0, it.A, lda,
-                                               &ssq, smf, nullptr, nullptr);
+        cta_gemm<64, false, true, true, false, 8>((int)m, (int)n, r, 1.f, it.Q, m, it.C, n, 0.f, nullptr, 0, it.A,
+                                                  lda, &ssq, smf, nullptr, nullptr);
         rel = sqrt(block_sum(ssq.value(), red)) / norm;
     }
     pc.mark(PH_ERR);
@@ -697,8 +722,9 @@ __global__ void __launch_bounds__(PT, 1) batch_kernel(PParams P) {
 size_t batch_smem_bytes() {
     size_t b = leaf_smem_bytes(kPRcap);
     b = std::max(b, gram_smem_bytes());
-    b = std::max(b, sizeof(float) * (size_t)gemm_smem_floats<32>());
-    b = std::max(b, sizeof(float) * (size_t)gemm_smem_floats<64>());
+    b = std::max(b, sizeof(float) * (size_t)gemm_smem_floats<32, 4, false>());
+    b = std::max(b, sizeof(float) * (size_t)gemm_smem_floats<64, 8, false>());
+    b = std::max(b, sizeof(float) * (size_t)gemm_smem_floats<64, 8, true>());
     return (b + 15) / 16 * 16;
 }
 
