@@ -471,7 +471,7 @@ struct PParams {
 // per-CTA scratch: FP64 k x k / r x r factors first, then the FP32 panels
 struct PLayout {
     int64_t g, r1, r1i, r2, r2i, rc;            // doubles
-    int64_t y, t1, om, sp, w, rf, rtf, w2, qh;  // floats, after the doubles
+    int64_t y, yw, t1, om, sp, w, rf, rtf, w2, qh;  // floats, after the doubles
     int64_t dbytes, bytes;
 };
 
@@ -487,7 +487,8 @@ __host__ __device__ inline PLayout playout(int64_t mmax, int64_t nmax) {
     L.rc = L.r2i + rr;
     L.dbytes = (L.rc + rr) * (int64_t)sizeof(double);
     L.y = 0;
-    L.t1 = L.y + up(mmax * kPKmax);
+    L.yw = L.y + up(mmax * kPKmax);
+    L.t1 = L.yw + up(mmax * kPKmax);
     L.om = L.t1 + up(mmax * kPKmax);
     L.sp = L.om + up(nmax * kPKmax);
     L.w = L.sp + up((int64_t)kPRcap * kPKmax);
@@ -537,7 +538,7 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
     double *G = (double *)base + L.g, *R1 = (double *)base + L.r1, *R1i = (double *)base + L.r1i;
     double *R2 = (double *)base + L.r2, *R2i = (double *)base + L.r2i, *Rc = (double *)base + L.rc;
     float *fb = (float *)(base + L.dbytes);
-    float *Y = fb + L.y, *T1 = fb + L.t1, *Om = fb + L.om, *S = fb + L.sp, *W = fb + L.w;
+    float *Y = fb + L.y, *Yw = fb + L.yw, *T1 = fb + L.t1, *Om = fb + L.om, *S = fb + L.sp, *W = fb + L.w;
     float *Rf = fb + L.rf, *Rtf = fb + L.rtf, *W2 = fb + L.w2, *Qh = fb + L.qh;
     float *smf = (float *)sm;
     constexpr double kNearId = 4e-8;   // ||G - I||_F^2 below which R = I + Phi(G - I) (FP32 panels)
@@ -566,33 +567,50 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
     const double delta_coef = 64.0 * ((double)P.k + sqrt((double)m)) * kU64;
     const double rho = 1e-6;
     bool stop = false;
+    // sketch window: Yw holds A Omega for global columns win_c0 .. win_c0 +
+    // win_w - 1; a pass over A computes two blocks at once when k <= 32
+    // (the second is wasted only if the rank is revealed in the first)
+    int64_t win_c0 = -1;
+    int win_w = 0;
     while (!stop && kept < cap) {
         const int f = (int)((int64_t)P.k < cap - kept ? (int64_t)P.k : cap - kept);
         ++blocks;
-        cta_omega(n, kept, f, P.seed, it.batch, Om);                                       // step 3
-        pc.mark(PH_OMEGA);
-        if (blocks == 1) {
-            // the first sketch reads every element of A once: ||A||_F and the
-            // finiteness check come from its shared-memory tiles
-            TwoSumAcc nrm;
-            int nf = 0;
-            cta_mm<false, false, true>((int)m, f, (int)n, 1.f, it.A, lda, Om, n, 0.f, Y, m, smf, &nrm, &nf);
-            const int bad = __syncthreads_or(nf);
-            norm = sqrt(block_sum(nrm.value(), red));
-            pc.mark(PH_SKETCH);
-            if (bad) { finish(EOD_ENONFINITE, -1.0); return; }
-            eps = P.tol_mode == EOD_TOL_REL_FRO ? P.tol * norm : P.tol;
-            eps2 = eps * eps;
-            if (norm == 0.0) {
-                if (tid == 0) tdg[0] = 0.0;
-                ntd = 1;
-                blocks = 0;
-                finish(EOD_OK, P.compute_err ? 0.0 : -1.0);
-                return;
+        if (win_c0 < 0 || kept < win_c0 || kept + f > win_c0 + win_w) {
+            int64_t w = 2 * (int64_t)P.k <= kPKmax ? 2 * (int64_t)P.k : (int64_t)P.k;
+            w = w < cap - kept ? w : cap - kept;
+            win_c0 = kept;
+            win_w = (int)w;
+            cta_omega(n, kept, win_w, P.seed, it.batch, Om);                                // step 3
+            pc.mark(PH_OMEGA);
+            if (blocks == 1) {
+                // the first sketch reads every element of A once: ||A||_F and
+                // the finiteness check come from its shared-memory tiles
+                TwoSumAcc nrm;
+                int nf = 0;
+                cta_mm<false, false, true>((int)m, win_w, (int)n, 1.f, it.A, lda, Om, n, 0.f, Yw, m, smf, &nrm, &nf);
+                const int bad = __syncthreads_or(nf);
+                norm = sqrt(block_sum(nrm.value(), red));
+                pc.mark(PH_SKETCH);
+                if (bad) { finish(EOD_ENONFINITE, -1.0); return; }
+                eps = P.tol_mode == EOD_TOL_REL_FRO ? P.tol * norm : P.tol;
+                eps2 = eps * eps;
+                if (norm == 0.0) {
+                    if (tid == 0) tdg[0] = 0.0;
+                    ntd = 1;
+                    blocks = 0;
+                    finish(EOD_OK, P.compute_err ? 0.0 : -1.0);
+                    return;
+                }
+            } else {
+                cta_mm<false, false, true>((int)m, win_w, (int)n, 1.f, it.A, lda, Om, n, 0.f, Yw, m, smf);
+                pc.mark(PH_SKETCH);
             }
-        } else {
-            cta_mm<false, false, true>((int)m, f, (int)n, 1.f, it.A, lda, Om, n, 0.f, Y, m, smf);   // Y = A Omega_j
-            pc.mark(PH_SKETCH);
+        }
+        {   // Y = the window's columns of this block (deflated below against the basis as it is now)
+            const float *src = Yw + (kept - win_c0) * m;
+            const int64_t tot = (int64_t)f * m;
+            for (int64_t e = tid; e < tot; e += PT) Y[e] = src[e];
+            __syncthreads();
         }
         int cur = 0;
         while (!stop && cur < f) {
