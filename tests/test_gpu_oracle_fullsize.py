@@ -167,6 +167,35 @@ def test_harmonic_8192_vs_oracle(eod, harmonic_case, form):
     f.close()
 
 
+# ------------------------------------------------- Alg. 1 lookahead on / off --
+@pytest.mark.parametrize("lookahead", ["0", "1"])
+def test_alg1_lookahead_on_and_off_harmonic_mixed(eod, harmonic_case, monkeypatch, lookahead):
+    """Alg. 1 with the next block's sketch and first projection on a side
+    stream during the current block's Gram and leaf (then the current
+    block's own columns projected out, then the second pass), and without:
+    the same BCGS2 result in exact arithmetic; both match the oracle."""
+    monkeypatch.setenv("EOD_LOOKAHEAD", lookahead)
+    w, A64, ref = harmonic_case
+    f = eod.factor(_to_dev(w.A, np.float32), w.tol, w.seed, block_k=64, tol_mode="rel", precision="mixed")
+    compare(f, ref, _to_dev(A64, np.float64), "mixed", f"harmonic8192 mixed lookahead={lookahead}", signal=40)
+    f.close()
+
+
+@pytest.mark.parametrize("lookahead", ["0", "1"])
+def test_alg1_lookahead_on_and_off_image_fp64(eod, monkeypatch, lookahead):
+    """The plain FP64 form: the lookahead's first projection reads the sliced
+    copies of Q from column 0, the completing pass from a multiple of 8 below
+    the previous block's first column (32 blocks at k = 64)."""
+    monkeypatch.setenv("EOD_LOOKAHEAD", lookahead)
+    w = W.image_like()
+    ref = _oracle(w.A, w.tol, 64, w.seed)
+    A = _to_dev(w.A, np.float64)
+    f = eod.factor(A, w.tol, w.seed, block_k=64, tol_mode="rel")
+    assert f.blocks >= 30
+    compare(f, ref, A, "plain_f64", f"image2048 plain fp64 lookahead={lookahead}", signal=150)
+    f.close()
+
+
 # ------------------------------------------------------ hyperspectral 262144x224 --
 @pytest.mark.parametrize("form", ["mixed", "mixed_tf32", "plain_f32", "plain_f64"])
 def test_hyperspectral_vs_oracle(eod, form):
