@@ -174,16 +174,31 @@ EOD_API eod_status eod_abe_reconstruct(const eod_factors *f, void *A_hat, int64_
 
 /* Factors `count` independent matrices (the per-image use of Sec. 4.1) in
  * one call.  A, m, n, lda, out and per_item are HOST arrays of length count;
- * A[i] is a device pointer.  Item i draws Omega with batch_index = i, so its
- * result equals a single eod_abe_factor_ex call with that batch_index.  The
- * items run concurrently on a pool of worker threads, each with its own
- * non-blocking stream (EOD_BATCH_STREAMS if set, else the tuned
- * "batch_workers", else 8), largest m*n*min(m,n) first; the workers wait
- * for the work already queued on opts->stream.  Every item gets its own
- * status in per_item[i] and, on EOD_OK, its own factors in out[i] (free each
- * with eod_abe_free).  Returns EOD_OK if every item succeeded, else the
- * status of the lowest-index failing item; EOD_EINVAL for count < 1 or NULL
- * arrays. */
+ * A[i] is a device pointer.  Item i draws Omega with batch_index = i.
+ *
+ * FP32 items (a_dtype EOD_F32, power_iters 0, block_k 0 or <= 64, m and n
+ * <= 16384) first go through one persistent launch, captured in a CUDA graph:
+ * each CTA takes items from a work queue, largest first, and factors each
+ * one start to end on the device (Alg. 1's stop decision included), with
+ * FP32 products (long dot products compensated), FP64-accurate Grams and the
+ * FP64 leaf Cholesky, whatever precision was requested; those factor sets
+ * report precision = EOD_PLAIN, block_k the k used (32 for block_k 0), and
+ * share one device allocation released by the last eod_abe_free.  An item
+ * whose rank exceeds 128, or whose core Gram the unshifted Cholesky cannot
+ * factor, is handed to the path below.  EOD_BATCH_PERSISTENT=0 skips the
+ * launch.
+ *
+ * Other items run concurrently on a pool of worker threads, each with its
+ * own non-blocking stream (EOD_BATCH_STREAMS if set, else the tuned
+ * "batch_workers", else 8), largest m*n*min(m,n) first, each an ordinary
+ * eod_abe_factor_ex call with batch_index = i (same result bit for bit).
+ *
+ * Work already queued on opts->stream is waited for first.  Every item gets
+ * its own status in per_item[i] and, on EOD_OK, its own factors in out[i]
+ * (free each with eod_abe_free).  Returns EOD_OK if every item succeeded,
+ * else the status of the lowest-index failing item (EOD_ECUDA for all if the
+ * persistent launch itself failed after starting); EOD_EINVAL for count < 1
+ * or NULL arrays. */
 EOD_API eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const int64_t *n,
                                   const int64_t *lda, int64_t count, double tol, uint64_t seed,
                                   const eod_opts *opts, eod_factors **out, eod_status *per_item);
@@ -226,7 +241,8 @@ EOD_API void eod_abe_debug_fail_alloc_after(int32_t n);
  * 4 tcgen05 tensor-core GEMM (mixed path), 5 FP64 GEMM emulated on tcgen05
  * (plain FP64 path), 6 slicing of FP64 operands into the BF16 digits of that
  * emulation, 7 SIMT GEMM and Gram in FP32 arithmetic (FP32-data paths; kind 0
- * is then the FP64 ones); eod_abe_debug_profile(0) stops it and clears.
+ * is then the FP64 ones), 8 the persistent batched launch (one record per
+ * launch); eod_abe_debug_profile(0) stops it and clears.
  * eod_abe_debug_profile_read() waits for the recorded events of one kind and
  * returns the launch count, the summed device time (ms) and the summed
  * algorithmic flops and bytes of those launches; EOD_EINVAL for an unknown
