@@ -410,6 +410,10 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     EOD_TRY(ar.get(&R2, (size_t)k * k));
     EOD_TRY(ar.get(&R2i, (size_t)k * k));
     EOD_TRY(ar.get(&tdiag_d, (size_t)cap + 1));
+    // per accepted panel, the (columns, code) of its second CholQR pass,
+    // checked once after the loop (no host round trip per panel)
+    int *pinfo;
+    EOD_TRY(ar.get(&pinfo, (size_t)2 * (cap + 1)));
     EOD_TRY(ar.get(&dsc, 8));
     EOD_TRY(ar.get(&iflag, 4));
     EOD_TRY(ar.get(&info, 2));
@@ -582,6 +586,8 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
         join_la.main = s;
         join_la.side = s2;
     }
+    int64_t nt = 0;              // T-diagonal entries recorded in tdiag_d
+    std::vector<int> panel_p;    // columns of each accepted panel
     bool ahead = false;          // Y2 holds the block at ahead_col0, projected once against Q(:, 0:ahead_q)
     int64_t ahead_col0 = -1, ahead_q = 0;
 
@@ -653,20 +659,17 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 }
                 EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, Yc, m, Ri, k, 0.0, T1, m, bup, &ws, s)));
                 EOD_CU(gram_skinny<T>(T1, m, p, m, G, k, &ws, s));
-                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, k, R2i, k, info, s, near_id_tau2<T>()));
+                int *pinf = pinfo + 2 * (int64_t)panel_p.size();
+                EOD_CU(chol_small(G, k, p, 0, 0.0, 0.0, 0.0, 0.0, R2, k, R2i, k, pinf, s, near_id_tau2<T>()));
                 const T *Ri2 = (const T *)R2i;
                 if (!std::is_same<T, double>::value) {
                     EOD_CU((copy_matrix<double, T>(R2i, k, RinvT, k, p, p, false, s)));
                     Ri2 = RinvT;
                 }
                 EOD_CU((gemm<T, T, T, T>(false, false, m, p, p, 1.0, T1, m, Ri2, k, 0.0, Qb + kept * m, m, bup, &ws, s)));
-                EOD_CU(tdiag_product(R1, R2, k, info, tdiag_d, s));
-                std::vector<double> td(p);
-                EOD_CU(cudaMemcpyAsync(hm.info, info, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
-                EOD_CU(cudaMemcpyAsync(td.data(), tdiag_d, sizeof(double) * p, cudaMemcpyDeviceToHost, s));
-                EOD_CU(cudaStreamSynchronize(s));
-                if (hm.info[0] != p || hm.info[1] != CHOL_ALL) return EOD_EPRECISION;
-                for (int j = 0; j < p; ++j) tdiag.push_back(td[j]);
+                EOD_CU(tdiag_product(R1, R2, k, pinf, tdiag_d + nt, s));
+                panel_p.push_back(p);
+                nt += p;
                 EOD_CU(oz_append(kept, p));
                 kept += p;
             }
@@ -676,16 +679,13 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                 // d_p < eps^2 - delta: |T(p,p)| <= eps for certain
                 stop = true;
                 // record the explicit residual norm of that column (diagnostics only)
-                tdiag.push_back(-1.0);
                 T *z = Yc + (int64_t)p * m;
                 for (int pass = 0; pass < 2 && kept > 0; ++pass) {
                     EOD_CU((gemm<T, T, T, T>(true, false, kept, 1, m, 1.0, Qb, m, z, m, 0.0, S, cap, ex, &ws, s)));
                     EOD_CU((gemm<T, T, T, T>(false, false, m, 1, kept, -1.0, Qb, m, S, cap, 1.0, z, m, ex, &ws, s)));
                 }
-                EOD_CU(fro_norm<T>(z, m, 1, m, d_t, iflag + 1, &ws, s));
-                EOD_CU(cudaMemcpyAsync(hm.val, d_t, sizeof(double), cudaMemcpyDeviceToHost, s));
-                EOD_CU(cudaStreamSynchronize(s));
-                tdiag.back() = hm.val[0];
+                EOD_CU(fro_norm<T>(z, m, 1, m, tdiag_d + nt, iflag + 1, &ws, s));
+                ++nt;
             } else {
                 // undecided pivot: settle column p by an explicit CGS2 residual norm
                 T *z = Yc + (int64_t)p * m;
@@ -694,10 +694,11 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
                     EOD_CU((gemm<T, T, T, T>(false, false, m, 1, kept, -1.0, Qb, m, S, cap, 1.0, z, m, ex, &ws, s)));
                 }
                 EOD_CU(fro_norm<T>(z, m, 1, m, d_t, iflag + 1, &ws, s));
+                EOD_CU(cudaMemcpyAsync(tdiag_d + nt, d_t, sizeof(double), cudaMemcpyDeviceToDevice, s));
+                ++nt;
                 EOD_CU(cudaMemcpyAsync(hm.val, d_t, sizeof(double), cudaMemcpyDeviceToHost, s));
                 EOD_CU(cudaStreamSynchronize(s));
                 const double t = hm.val[0];
-                tdiag.push_back(t);
                 ++restarts;
                 if (!(t > eps)) {
                     stop = true;
@@ -712,6 +713,18 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
         }
     }
     if (ahead) EOD_CU(stream_after(s, s2));   // an unused lookahead: its buffers are shared after this
+    // the T diagonal recorded on the device, and every panel's second pass
+    // checked: it factored all p columns
+    if (nt > 0 || !panel_p.empty()) {
+        std::vector<int> pinf(2 * panel_p.size() + 1);
+        tdiag.resize((size_t)nt);
+        if (nt > 0) EOD_CU(cudaMemcpyAsync(tdiag.data(), tdiag_d, sizeof(double) * nt, cudaMemcpyDeviceToHost, s));
+        if (!panel_p.empty())
+            EOD_CU(cudaMemcpyAsync(pinf.data(), pinfo, sizeof(int) * 2 * panel_p.size(), cudaMemcpyDeviceToHost, s));
+        EOD_CU(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < panel_p.size(); ++i)
+            if (pinf[2 * i] != panel_p[i] || pinf[2 * i + 1] != CHOL_ALL) return EOD_EPRECISION;
+    }
     const int64_t r = kept;
     F->rank = r;
     F->blocks = blocks;
