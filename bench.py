@@ -627,7 +627,9 @@ def robustness_matrices(eod):
 
 def compare_batched(eod, steps, warmup):
     """Factorisations per second of the 256-matrix pixel batch, as stated
-    (clipped to [0, 255], tol 1e-3 relative) and unclipped (same tolerance):
+    (clipped to [0, 255], tol 1e-3 relative) and unclipped (same tolerance),
+    at block_k = 0 (the persistent launch's k = 32; the tuned batch k on the
+    worker streams):
     plain FP64 (worker streams), the FP32 batch through the library's default
     route (the persistent launch, items above its rank capacity handed to the
     worker streams in the mixed BF16 form) and the same FP32 batch on the
@@ -641,13 +643,13 @@ def compare_batched(eod, steps, warmup):
         os.environ.update(env)
         try:
             for _ in range(warmup):
-                r, st = eod.factor_batched(mats, tol, seed, block_k=32, tol_mode="rel", precision=prec)
+                r, st = eod.factor_batched(mats, tol, seed, block_k=0, tol_mode="rel", precision=prec)
                 del r
             torch.cuda.synchronize()
             keep = []   # factor sets are released after the clock stops (eod_abe_free synchronises)
             t0 = time.perf_counter()
             for _ in range(steps):
-                r, st = eod.factor_batched(mats, tol, seed, block_k=32, tol_mode="rel", precision=prec)
+                r, st = eod.factor_batched(mats, tol, seed, block_k=0, tol_mode="rel", precision=prec)
                 keep.append(r)
             torch.cuda.synchronize()
             dt = (time.perf_counter() - t0) / steps
@@ -674,9 +676,10 @@ def compare_batched(eod, steps, warmup):
             dt, r, st = timed(mats, prec, tol, w.seed, env)
             ranks[form] = [x.rank for x in r]
             rels[form] = [x.rel_err for x in r]
-            flops = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, 32, True) for a, x in zip(w.A, r))
+            flops = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, x.block_k, True) for a, x in zip(w.A, r))
             res[form] = {"fact_per_s": len(mats) / dt, "ms_per_batch": dt * 1e3, "gflops": flops / dt / 1e9,
                          "statuses_ok": all(x == 0 for x in st),
+                         "block_k_used": sorted(set(int(x.block_k) for x in r)),
                          "rank_mean": float(np.mean(ranks[form])), "rank_max": int(np.max(ranks[form]))}
             if form == "mixed_bf16":
                 # items the persistent launch finished (its factor sets say EOD_PLAIN)
@@ -690,10 +693,11 @@ def compare_batched(eod, steps, warmup):
         # the graph launch) against the cost model's flops of the items it
         # finished, on the FP32 CUDA-core peak (its products are FP32 SIMT)
         eod.eod_abe_debug_profile(1)
-        r, st = eod.factor_batched(m32, tol, w.seed, block_k=32, tol_mode="rel", precision="mixed")
+        r, st = eod.factor_batched(m32, tol, w.seed, block_k=0, tol_mode="rel", precision="mixed")
         pk = eod.profile_read(eod.PROF_BATCH)
         eod.eod_abe_debug_profile(0)
-        fl = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, 32, True) for a, x in zip(w.A, r) if x.precision == 0)
+        fl = sum(eod.model_flops(a.shape[0], a.shape[1], x.rank, x.block_k, True) for a, x in zip(w.A, r)
+                 if x.precision == 0)
         if pk["launches"] and pk["ms"] > 0:
             ach = fl / (pk["ms"] / 1e3) / 1e9
             res["mixed_bf16"]["persistent_kernel"] = {

@@ -191,7 +191,9 @@ EOD_API eod_status eod_abe_reconstruct(const eod_factors *f, void *A_hat, int64_
  * Other items run concurrently on a pool of worker threads, each with its
  * own non-blocking stream (EOD_BATCH_STREAMS if set, else the tuned
  * "batch_workers", else 8), largest m*n*min(m,n) first, each an ordinary
- * eod_abe_factor_ex call with batch_index = i (same result bit for bit).
+ * eod_abe_factor_ex call with batch_index = i (same result bit for bit);
+ * with block_k = 0 they take the tuned "batch_block_k" of the form and the
+ * items' mean m, n when the table has one, else each item's own tuned k.
  *
  * Work already queued on opts->stream is waited for first.  Every item gets
  * its own status in per_item[i] and, on EOD_OK, its own factors in out[i]
@@ -382,19 +384,24 @@ EOD_API eod_status eod_abe_debug_bounded_wait(int64_t budget_cycles, int32_t arr
  * library, paper_2506_22713_gb300/autotune.py, writes them from timings on
  * the GPU).  The table is a text file of lines
  *     key a_lo a_hi b_lo b_hi c_lo c_hi value
- * (inclusive integer ranges, '#' comments, first matching row wins) read
- * once per process from $EOD_TUNING_FILE, else tuning.txt beside the
- * library; a missing file means no tuned values and the fixed defaults.
+ * (inclusive integer ranges, '#' comments; of the rows of a key whose ranges
+ * hold (a, b, c), the nearest wins: the smallest sum over the three axes of
+ * |log x - log centre|, centre the geometric mean of the row's bounds, ties
+ * to the earlier row) read once per process from $EOD_TUNING_FILE, else
+ * tuning.txt beside the library; a missing file means no tuned values and
+ * the fixed defaults.
  * Keys the library consults: "block_k" (a = form: 0 plain FP64, 1 plain
  * FP32, 2 mixed BF16, 3 mixed TF32; b = m; c = n) for opts->block_k == 0
  * (default 32); "f32_tile" (a = M, b = N, c = K) for the FP32 SIMT product
  * tile (16, 32, 64, 128); "batch_workers" (a = count, b = mean m, c = mean n)
  * for eod_abe_factor_batched's worker streams (default 8; the environment
- * variable EOD_BATCH_STREAMS overrides).
+ * variable EOD_BATCH_STREAMS overrides); "batch_block_k" (a = form, b = mean
+ * m, c = mean n) for the k of batched items on those streams when
+ * opts->block_k == 0.
  * eod_abe_tuning_load(path) replaces the table by the file at path (NULL:
  * the default location); EOD_EINVAL for a malformed line (the table is then
  * left unchanged); a missing file empties it.  eod_abe_tuning_lookup returns
- * 1 and stores the value when a row matches, else 0. */
+ * 1 and stores the nearest matching row's value, else 0. */
 EOD_API eod_status eod_abe_tuning_load(const char *path);
 EOD_API int32_t eod_abe_tuning_lookup(const char *key, int64_t a, int64_t b, int64_t c, int64_t *value);
 

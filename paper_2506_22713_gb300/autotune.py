@@ -14,13 +14,17 @@ keys in include/eod_abe.h, eod_abe_tuning_load):
                  each size class timed with k in 16 ... 128 (CUDA events,
                  median of the repetitions, L2 flushed between them);
 * batch_workers  the worker streams of the batched entry point on the
-                 256-matrix pixel batch.
+                 256-matrix pixel batch;
+* batch_block_k  k of Alg. 1 for the items of a batched call that run on
+                 the worker streams (block_k = 0): the whole clipped pixel
+                 batch timed per k and form (under concurrency fewer,
+                 wider blocks pay more than for one matrix of that size).
 
 Every row covers a range around the measured case (a factor of about 1.5
-to each side of the sizes); the first matching row wins, so the table lists
-them in the order written here.
+to each side of the sizes); of the rows that hold a case the nearest wins
+(log distance to the centre of each range).
 
-    python -m paper_2506_22713_gb300.autotune --out PATH [--quick]
+    python -m paper_2506_22713_gb300.autotune --out PATH [--quick] [--skip ...] [--merge]
 """
 from __future__ import annotations
 
@@ -209,6 +213,37 @@ def tune_batch_workers(eod, torch, candidates=(4, 8, 12, 16, 24, 32)):
     return [row], [note]
 
 
+# ---------------------------------------------------------- batch block_k --
+def tune_batch_block_k(eod, torch, ks=(32, 64, 96, 128)):
+    import numpy as np
+    import workloads as W
+
+    w = W.pixel_batch()
+    mm = int(np.mean([a.shape[0] for a in w.A]))
+    nn = int(np.mean([a.shape[1] for a in w.A]))
+    rows, notes = [], []
+    for form, dtype, prec in (("mixed", np.float32, "mixed"), ("plain_f64", np.float64, "plain")):
+        mats = [torch.from_numpy(np.asfortranarray(a.astype(dtype))).cuda() for a in w.A]
+        res = {}
+        for k in ks:
+            r, st = eod.factor_batched(mats, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
+            del r
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r, st = eod.factor_batched(mats, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
+            torch.cuda.synchronize()
+            res[k] = time.perf_counter() - t0
+            assert all(x == 0 for x in st)
+            del r
+        best = min(res, key=res.get)
+        rows.append(("batch_block_k", FORMS[form], FORMS[form], *_range(mm, 0.5, 2.0), *_range(nn, 0.5, 2.0), best))
+        notes.append(f"batch_block_k pixel batch 256 {form}: " + ", ".join(f"k={k}:{v * 1e3:.0f}ms" for k, v in res.items())
+                     + f" -> {best}")
+        del mats
+        torch.cuda.empty_cache()
+    return rows, notes
+
+
 def write_table(path, rows, notes, meta):
     with open(path, "w") as fh:
         fh.write("# Tuned parameters of libeodabe.so, written by paper_2506_22713_gb300/autotune.py\n")
@@ -225,7 +260,7 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--out", required=True, help="where to write the table")
     p.add_argument("--quick", action="store_true", help="fewer cases (smoke run)")
-    p.add_argument("--skip", default="", help="comma list of f32_tile,block_k,batch_workers to skip")
+    p.add_argument("--skip", default="", help="comma list of f32_tile,block_k,batch_workers,batch_block_k to skip")
     p.add_argument("--merge", action="store_true",
                    help="keep the rows (and their notes) of skipped parts from the table already at --out")
     args = p.parse_args(argv)
@@ -245,6 +280,10 @@ def main(argv=None):
         notes += n
     if "block_k" not in skip:
         r, n = tune_block_k(eod, torch, quick=args.quick)
+        rows += r
+        notes += n
+    if "batch_block_k" not in skip:
+        r, n = tune_batch_block_k(eod, torch, ks=(32, 96) if args.quick else (32, 64, 96, 128))
         rows += r
         notes += n
     if "batch_workers" not in skip:

@@ -1166,6 +1166,22 @@ eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const 
             workers = (int)v;
     }
     if (workers > (int64_t)order.size()) workers = (int)order.size();
+    // block_k = 0: the autotuner's k for batched items of this size class
+    // (timed under the workers' concurrency), else each item's own tuned k
+    int32_t batch_k = 0;
+    if (o.block_k == 0) {
+        double sm = 0.0, sn = 0.0;
+        for (int64_t i : order) {
+            sm += (double)m[i];
+            sn += (double)n[i];
+        }
+        const int64_t form = o.precision == EOD_MIXED_BF16 ? 2 : o.precision == EOD_MIXED_TF32 ? 3
+                             : o.a_dtype == EOD_F32 ? 1 : 0;
+        int64_t v = 0;
+        if (tuned_value("batch_block_k", form, (int64_t)(sm / order.size()), (int64_t)(sn / order.size()), &v) &&
+            v >= 1 && v <= 128)
+            batch_k = (int32_t)v;
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return EOD_ECUDA; }
     // work already queued on the caller's stream (for example the matrices
@@ -1190,6 +1206,7 @@ eod_status eod_abe_factor_batched(const void *const *A, const int64_t *m, const 
             if (j >= (int64_t)order.size()) break;
             const int64_t i = order[(size_t)j];
             eod_opts oi = o;
+            if (oi.block_k == 0 && batch_k > 0) oi.block_k = batch_k;
             oi.batch_index = (uint64_t)i;
             oi.stream = st;
             per_item[i] = factor_any(A[i], m[i], n[i], lda[i], tol, seed, &oi, &out[i]);
