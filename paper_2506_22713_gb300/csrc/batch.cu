@@ -31,6 +31,7 @@
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
+#include <type_traits>
 #include <vector>
 
 namespace eod {
@@ -461,9 +462,15 @@ struct PParams {
     double *tdiag;            // count x kPTdCap
     unsigned char *scratch;   // one region per CTA
     int64_t stride, mmax, nmax;
-    unsigned *next;           // the work queue's counter
+    unsigned *next;           // the single CTAs' queue counter (items npair .. count-1)
+    unsigned *pair_next;      // the pairs' queue counter (items 0 .. npair-1)
+    unsigned *team_bar;       // per cluster: its team barrier counter
+    int *team_slot;           // per cluster: the item its pair took
+    int *err;                 // set when a team barrier ran out
+    float *xf;                // per cluster: the team's exchange slots
+    double *xd;
     unsigned long long *phase;   // null, or kPPhases cycle counters summed over items (measurement)
-    int count, k, tol_mode, compute_err;
+    int count, npair, k, tol_mode, compute_err;
     double tol;
     uint64_t seed;
 };
@@ -526,13 +533,88 @@ struct PhaseClock {
     }
 };
 
-// One matrix, start to end, on this CTA.
-__device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *info, double *red) {
+// ----------------------------------------------------------------- teams ----
+// A team of one CTA, or of the two CTAs of a cluster, runs one item: the two
+// split the rows of m (Alg. 1, U, the error) and of n (C, the core's tall
+// panels); what spans the rows (Q^T Y, the Grams, norms, the error sum) is
+// summed over the ranks in rank order through a per-team exchange buffer, so
+// both ranks hold bit-identical values, run the leaf on identical Grams and
+// take every decision alike.  A team of one skips the exchange.
+constexpr long long kTeamWait = 4000000000ll;   // cycles (~2 s) a team barrier waits at most
+constexpr double kPairFrac = 0.5;                // items with m n >= this x the largest go to pairs
+constexpr int kXF = kPRcap * kPKmax;             // floats per exchange slot
+constexpr int kXD = kPRcap * kPRcap + 8;         // doubles per exchange slot
+
+struct Team {
+    int rank, size;
+    unsigned *bar;        // the team's barrier counter (zeroed by the launch)
+    unsigned epoch;       // barriers this CTA has passed
+    unsigned xchg;        // exchanges done (the slot parity)
+    float *xf;            // [2 parities][2 ranks][kXF]
+    double *xd;           // [2 parities][2 ranks][kXD]
+    int *err;             // set when a wait ran out
+    __device__ int64_t lo(int64_t M) const { return M * rank / size; }
+    __device__ int64_t hi(int64_t M) const { return M * (rank + 1) / size; }
+};
+
+// barrier of the team (every thread calls); false when the wait ran out
+__device__ bool team_sync(Team &t) {
+    __syncthreads();
+    if (t.size == 1) return true;
+    __shared__ int ok_sh;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned target = (unsigned)t.size * (t.epoch + 1);
+        atomicAdd(t.bar, 1u);
+        const long long t0 = clock64();
+        int ok = 1;
+        while (*(volatile unsigned *)t.bar < target) {
+            if (clock64() - t0 > kTeamWait) {
+                ok = 0;
+                atomicExch(t.err, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    ++t.epoch;
+    return ok_sh != 0;
+}
+
+// v[i * ldv + j] (i < rows, j < cols) becomes the sum over the ranks (rank
+// order); false when the team barrier ran out
+template <typename T>
+__device__ bool team_sum(Team &t, T *v, int rows, int cols, int ldv) {
+    if (t.size == 1) return true;
+    __syncthreads();
+    const unsigned par = t.xchg & 1u;
+    ++t.xchg;
+    const int slot = std::is_same<T, float>::value ? kXF : kXD;
+    T *x = std::is_same<T, float>::value ? (T *)t.xf : (T *)t.xd;
+    T *mine = x + ((size_t)par * 2 + t.rank) * slot;
+    for (int e = threadIdx.x; e < rows * cols; e += PT) mine[e] = v[(e % rows) + (e / rows) * ldv];
+    if (!team_sync(t)) return false;
+    const T *x0 = x + (size_t)par * 2 * slot, *x1 = x0 + slot;
+    for (int e = threadIdx.x; e < rows * cols; e += PT) v[(e % rows) + (e / rows) * ldv] = x0[e] + x1[e];
+    __syncthreads();
+    return true;
+}
+
+// One matrix, start to end, on a team of one or two CTAs (rows of m and n
+// split between the ranks).  Returns false when a team barrier ran out (the
+// item then reports EOD_ETIMEOUT and the CTA leaves the kernel).
+__device__ __noinline__ bool batch_item(const PParams &P, int idx, Team &T, unsigned char *sm, int *info, double *red) {
     const PItem it = P.items[idx];
     PRes *res = P.res + idx;
     double *tdg = P.tdiag + (int64_t)idx * kPTdCap;
     const int tid = threadIdx.x;
+    const bool lead = T.rank == 0;   // the rank that writes the item's shared results
     const int64_t m = it.m, n = it.n, lda = it.lda;
+    const int64_t mlo = T.lo(m), ml = T.hi(m) - mlo;   // this rank's rows of m
+    const int64_t nlo = T.lo(n), nl = T.hi(n) - nlo;   // and of n
     const PLayout L = playout(P.mmax, P.nmax);
     unsigned char *base = P.scratch + (int64_t)blockIdx.x * P.stride;
     double *G = (double *)base + L.g, *R1 = (double *)base + L.r1, *R1i = (double *)base + L.r1i;
@@ -541,12 +623,13 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
     float *Y = fb + L.y, *Yw = fb + L.yw, *T1 = fb + L.t1, *Om = fb + L.om, *S = fb + L.sp, *W = fb + L.w;
     float *Rf = fb + L.rf, *Rtf = fb + L.rtf, *W2 = fb + L.w2, *Qh = fb + L.qh;
     float *smf = (float *)sm;
+    __shared__ double dsum[2];
     constexpr double kNearId = 4e-8;   // ||G - I||_F^2 below which R = I + Phi(G - I) (FP32 panels)
 
     int kept = 0, blocks = 0, restarts = 0, ntd = 0;
     double eps = 0.0, norm = 0.0;
     auto finish = [&](int status, double rel) {
-        if (tid == 0) {
+        if (tid == 0 && lead) {
             res->status = status;
             res->rank = kept;
             res->blocks = blocks;
@@ -557,6 +640,22 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
             res->rel_err = rel;
         }
     };
+    // a value summed over the team's ranks (FP64, rank order)
+    auto tsum1 = [&](double v, double *out) -> bool {
+        if (tid == 0) dsum[0] = v;
+        __syncthreads();
+        if (!team_sum<double>(T, dsum, 1, 1, 1)) return false;
+        *out = dsum[0];
+        __syncthreads();
+        return true;
+    };
+#define TEAM_OK(call)                              \
+    do {                                           \
+        if (!(call)) {                             \
+            finish(EOD_ETIMEOUT, -1.0);            \
+            return false;                          \
+        }                                          \
+    } while (0)
 
     PhaseClock pc;
     pc.start(P.phase);
@@ -567,9 +666,10 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
     const double delta_coef = 64.0 * ((double)P.k + sqrt((double)m)) * kU64;
     const double rho = 1e-6;
     bool stop = false;
-    // sketch window: Yw holds A Omega for global columns win_c0 .. win_c0 +
-    // win_w - 1; a pass over A computes two blocks at once when k <= 32
-    // (the second is wasted only if the rank is revealed in the first)
+    // sketch window: Yw holds (this rank's rows of) A Omega for global columns
+    // win_c0 .. win_c0 + win_w - 1; a pass over A computes two blocks at once
+    // when k <= 32 (the second is wasted only if the rank is revealed in the
+    // first)
     int64_t win_c0 = -1;
     int win_w = 0;
     while (!stop && kept < cap) {
@@ -587,29 +687,36 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
                 // the finiteness check come from its shared-memory tiles
                 TwoSumAcc nrm;
                 int nf = 0;
-                cta_mm<false, false, true>((int)m, win_w, (int)n, 1.f, it.A, lda, Om, n, 0.f, Yw, m, smf, &nrm, &nf);
-                const int bad = __syncthreads_or(nf);
-                norm = sqrt(block_sum(nrm.value(), red));
+                cta_mm<false, false, true>((int)ml, win_w, (int)n, 1.f, it.A + mlo, lda, Om, n, 0.f, Yw + mlo, m, smf,
+                                           &nrm, &nf);
+                const int bad_local = __syncthreads_or(nf);
+                const double part = block_sum(nrm.value(), red);
+                double tot = 0.0, badsum = 0.0;
+                TEAM_OK(tsum1(part, &tot));
+                TEAM_OK(tsum1((double)bad_local, &badsum));
+                norm = sqrt(tot);
                 pc.mark(PH_SKETCH);
-                if (bad) { finish(EOD_ENONFINITE, -1.0); return; }
+                if (badsum != 0.0) { finish(EOD_ENONFINITE, -1.0); return true; }
                 eps = P.tol_mode == EOD_TOL_REL_FRO ? P.tol * norm : P.tol;
                 eps2 = eps * eps;
                 if (norm == 0.0) {
-                    if (tid == 0) tdg[0] = 0.0;
+                    if (tid == 0 && lead) tdg[0] = 0.0;
                     ntd = 1;
                     blocks = 0;
                     finish(EOD_OK, P.compute_err ? 0.0 : -1.0);
-                    return;
+                    return true;
                 }
             } else {
-                cta_mm<false, false, true>((int)m, win_w, (int)n, 1.f, it.A, lda, Om, n, 0.f, Yw, m, smf);
+                cta_mm<false, false, true>((int)ml, win_w, (int)n, 1.f, it.A + mlo, lda, Om, n, 0.f, Yw + mlo, m, smf);
                 pc.mark(PH_SKETCH);
             }
         }
-        {   // Y = the window's columns of this block (deflated below against the basis as it is now)
-            const float *src = Yw + (kept - win_c0) * m;
-            const int64_t tot = (int64_t)f * m;
-            for (int64_t e = tid; e < tot; e += PT) Y[e] = src[e];
+        {   // Y = the window's columns of this block (this rank's rows)
+            const int64_t tot = (int64_t)f * ml;
+            for (int64_t e = tid; e < tot; e += PT) {
+                const int64_t c = e / ml, i = mlo + (e - c * ml);
+                Y[i + c * m] = Yw[i + (kept - win_c0 + c) * m];
+            }
             __syncthreads();
         }
         int cur = 0;
@@ -617,27 +724,32 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
             float *Yc = Y + (int64_t)cur * m;
             const int wdt = f - cur;
             for (int pass = 0; pass < 2 && kept > 0; ++pass) {                             // step 4, twice
-                cta_mm<true, false, true>(kept, wdt, (int)m, 1.f, it.Q, m, Yc, m, 0.f, S, kPRcap, smf);
-                cta_mm<false, false>((int)m, wdt, kept, -1.f, it.Q, m, S, kPRcap, 1.f, Yc, m, smf);
+                cta_mm<true, false, true>(kept, wdt, (int)ml, 1.f, it.Q + mlo, m, Yc + mlo, m, 0.f, S, kPRcap, smf);
+                TEAM_OK(team_sum<float>(T, S, kept, wdt, kPRcap));
+                cta_mm<false, false>((int)ml, wdt, kept, -1.f, it.Q + mlo, m, S, kPRcap, 1.f, Yc + mlo, m, smf);
             }
             pc.mark(PH_DEFLATE);
-            cta_gram(Yc, m, wdt, m, G, kPRcap, sm);                                          // step 5, pass 1
+            cta_gram(Yc + mlo, ml, wdt, m, G, kPRcap, sm);                                   // step 5, pass 1
+            TEAM_OK(team_sum<double>(T, G, wdt, wdt, kPRcap));
             leaf(G, wdt, 1, eps2, delta_coef, rho, R1, R1i, info, 0.0, sm);                    // steps 6-11
             pc.mark(PH_GRAM_LEAF);
             const int p = info[0], code = info[1];
             __syncthreads();
             if (p > 0) {
-                if (kept + p > it.cap) { finish(kPFallback, -1.0); return; }
+                if (kept + p > it.cap) { finish(kPFallback, -1.0); return true; }
                 cta_to_f32(R1i, kPRcap, p, Rf, kPRcap, false);
-                cta_mm<false, false>((int)m, p, p, 1.f, Yc, m, Rf, kPRcap, 0.f, T1, m, smf);
-                cta_gram(T1, m, p, m, G, kPRcap, sm);                                        // pass 2
+                cta_mm<false, false>((int)ml, p, p, 1.f, Yc + mlo, m, Rf, kPRcap, 0.f, T1 + mlo, m, smf);
+                cta_gram(T1 + mlo, ml, p, m, G, kPRcap, sm);                                 // pass 2
+                TEAM_OK(team_sum<double>(T, G, p, p, kPRcap));
                 leaf(G, p, 0, 0.0, 0.0, 0.0, R2, R2i, info, kNearId, sm);
                 const int p2 = info[0], c2 = info[1];
                 __syncthreads();
-                if (p2 != p || c2 != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+                if (p2 != p || c2 != CHOL_ALL) { finish(kPFallback, -1.0); return true; }
                 cta_to_f32(R2i, kPRcap, p, Rf, kPRcap, false);
-                cta_mm<false, false>((int)m, p, p, 1.f, T1, m, Rf, kPRcap, 0.f, it.Q + (int64_t)kept * m, m, smf);
-                for (int l = tid; l < p; l += PT) tdg[ntd + l] = fabs(R1[l + l * kPRcap] * R2[l + l * kPRcap]);
+                cta_mm<false, false>((int)ml, p, p, 1.f, T1 + mlo, m, Rf, kPRcap, 0.f, it.Q + (int64_t)kept * m + mlo, m,
+                                     smf);
+                if (lead)
+                    for (int l = tid; l < p; l += PT) tdg[ntd + l] = fabs(R1[l + l * kPRcap] * R2[l + l * kPRcap]);
                 ntd += p;
                 kept += p;
                 pc.mark(PH_PANEL);
@@ -648,12 +760,15 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
                 // column p: its explicit residual after two more projections
                 float *z = Yc + (int64_t)p * m;
                 for (int pass = 0; pass < 2 && kept > 0; ++pass) {
-                    cta_tmv(kept, (int)m, it.Q, m, z, S);
-                    cta_mv_sub(m, kept, it.Q, m, S, z);
+                    cta_tmv(kept, (int)ml, it.Q + mlo, m, z + mlo, S);
+                    TEAM_OK(team_sum<float>(T, S, kept, 1, kPRcap));
+                    cta_mv_sub(ml, kept, it.Q + mlo, m, S, z + mlo);
                 }
-                const double t = sqrt(cta_norm2(z, m, red));
+                double t2 = 0.0;
+                TEAM_OK(tsum1(cta_norm2(z + mlo, ml, red), &t2));
+                const double t = sqrt(t2);
                 pc.mark(PH_RESIDUAL);
-                if (tid == 0) tdg[ntd] = t;
+                if (tid == 0 && lead) tdg[ntd] = t;
                 ++ntd;
                 if (code == CHOL_BELOW) {
                     stop = true;
@@ -662,10 +777,10 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
                     if (!(t > eps)) {
                         stop = true;
                     } else {
-                        if (kept + 1 > it.cap) { finish(kPFallback, -1.0); return; }
+                        if (kept + 1 > it.cap) { finish(kPFallback, -1.0); return true; }
                         const double inv = 1.0 / t;
                         float *q = it.Q + (int64_t)kept * m;
-                        for (int64_t i = tid; i < m; i += PT) q[i] = (float)((double)z[i] * inv);
+                        for (int64_t i = mlo + tid; i < mlo + ml; i += PT) q[i] = (float)((double)z[i] * inv);
                         __syncthreads();
                         kept += 1;
                         cur += p + 1;
@@ -675,65 +790,98 @@ __device__ void batch_item(const PParams &P, int idx, unsigned char *sm, int *in
         }
     }
     const int r = kept;
-    if (r == 0) { finish(EOD_OK, P.compute_err ? 1.0 : -1.0); return; }
+    if (r == 0) { finish(EOD_OK, P.compute_err ? 1.0 : -1.0); return true; }
 
-    // ---- Alg. 2 step 8: C (n x r) = A^T Q ----
-    cta_mm<true, false, true>((int)n, r, (int)m, 1.f, it.A, lda, it.Q, m, 0.f, it.C, n, smf);
+    // ---- Alg. 2 step 8: C (n x r) = A^T Q, this rank's rows of n (all of Q) ----
+    TEAM_OK(team_sync(T));
+    cta_mm<true, false, true>((int)nl, r, (int)m, 1.f, it.A + nlo * lda, lda, it.Q, m, 0.f, it.C + nlo, n, smf);
     pc.mark(PH_PROJECT);
+    TEAM_OK(team_sync(T));   // every row of C before the error and the core read them
     double rel = -1.0;
     if (P.compute_err) {                                                   // ||A - Q C^T||_F / ||A||_F
         TwoSumAcc ssq;
-        cta_gemm<64, false, true, true, false, 8>((int)m, (int)n, r, 1.f, it.Q, m, it.C, n, 0.f, nullptr, 0, it.A,
-                                                  lda, &ssq, smf, nullptr, nullptr);
-        rel = sqrt(block_sum(ssq.value(), red)) / norm;
+        cta_gemm<64, false, true, true, false, 8>((int)ml, (int)n, r, 1.f, it.Q + mlo, m, it.C, n, 0.f, nullptr, 0,
+                                                  it.A + mlo, lda, &ssq, smf, nullptr, nullptr);
+        double e2 = 0.0;
+        TEAM_OK(tsum1(block_sum(ssq.value(), red), &e2));
+        rel = sqrt(e2) / norm;
     }
     pc.mark(PH_ERR);
 
-    // ---- steps 9-10: C^T = V R, then R^T = Qh D (CholQR2 each) ----
-    cta_gram(it.C, n, r, n, G, kPRcap, sm);
+    // ---- steps 9-10: C^T = V R (rows of n split), then R^T = Qh D (r x r, on every rank) ----
+    cta_gram(it.C + nlo, nl, r, n, G, kPRcap, sm);
+    TEAM_OK(team_sum<double>(T, G, r, r, kPRcap));
     leaf(G, r, 0, 0.0, 0.0, 0.0, R1, R1i, info, 0.0, sm);
-    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return true; }
     cta_to_f32(R1i, kPRcap, r, Rf, kPRcap, false);
-    cta_mm<false, false>((int)n, r, r, 1.f, it.C, n, Rf, kPRcap, 0.f, W, n, smf);
-    cta_gram(W, n, r, n, G, kPRcap, sm);
+    cta_mm<false, false>((int)nl, r, r, 1.f, it.C + nlo, n, Rf, kPRcap, 0.f, W + nlo, n, smf);
+    cta_gram(W + nlo, nl, r, n, G, kPRcap, sm);
+    TEAM_OK(team_sum<double>(T, G, r, r, kPRcap));
     leaf(G, r, 0, 0.0, 0.0, 0.0, R2, R2i, info, kNearId, sm);
-    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return true; }
     cta_to_f32(R2i, kPRcap, r, Rf, kPRcap, false);
-    cta_mm<false, false>((int)n, r, r, 1.f, W, n, Rf, kPRcap, 0.f, it.V, n, smf);
+    cta_mm<false, false>((int)nl, r, r, 1.f, W + nlo, n, Rf, kPRcap, 0.f, it.V + nlo, n, smf);
     cta_triu_mul(R2, kPRcap, R1, kPRcap, Rc, kPRcap, r);                  // R = R2 R1
 
     cta_to_f32(Rc, kPRcap, r, Rtf, kPRcap, true);                         // R^T
     cta_gram(Rtf, r, r, kPRcap, G, kPRcap, sm);
     leaf(G, r, 0, 0.0, 0.0, 0.0, R1, R1i, info, 0.0, sm);
-    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return true; }
     cta_to_f32(R1i, kPRcap, r, Rf, kPRcap, false);
     cta_mm<false, false>(r, r, r, 1.f, Rtf, kPRcap, Rf, kPRcap, 0.f, W2, kPRcap, smf);
     cta_gram(W2, r, r, kPRcap, G, kPRcap, sm);
     leaf(G, r, 0, 0.0, 0.0, 0.0, R2, R2i, info, kNearId, sm);
-    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return; }
+    if (info[0] != r || info[1] != CHOL_ALL) { finish(kPFallback, -1.0); return true; }
     cta_to_f32(R2i, kPRcap, r, Rf, kPRcap, false);
     cta_mm<false, false>(r, r, r, 1.f, W2, kPRcap, Rf, kPRcap, 0.f, Qh, kPRcap, smf);
-    cta_triu_mul(R2, kPRcap, R1, kPRcap, it.D, r, r);                    // D = R2 R1 of this pair
+    if (lead) cta_triu_mul(R2, kPRcap, R1, kPRcap, it.D, r, r);          // D = R2 R1 of this pair
     pc.mark(PH_CORE);
 
-    // ---- step 11: U = Q Qh ----
-    cta_mm<false, false>((int)m, r, r, 1.f, it.Q, m, Qh, kPRcap, 0.f, it.U, m, smf);
+    // ---- step 11: U = Q Qh (this rank's rows of m) ----
+    cta_mm<false, false>((int)ml, r, r, 1.f, it.Q + mlo, m, Qh, kPRcap, 0.f, it.U + mlo, m, smf);
     pc.mark(PH_U);
     finish(EOD_OK, rel);
+    return true;
+#undef TEAM_OK
 }
 
-__global__ void __launch_bounds__(PT, 1) batch_kernel(PParams P) {
+// Pairs first: the two CTAs of each cluster take the P.npair largest items
+// together from their own queue; then every CTA alone takes the rest.  A
+// team barrier that ran out ends the CTA (its partner's next wait runs out
+// too), with the error flag set for the host.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PT, 1) batch_kernel(PParams P) {
     extern __shared__ __align__(16) unsigned char psm[];
     __shared__ int item_sh;
     __shared__ int info_sh[2];
     __shared__ double red_sh[32];
+    const int team_id = blockIdx.x >> 1;
+    Team T;
+    T.err = P.err;
+    T.epoch = 0;
+    T.xchg = 0;
+    T.xf = P.xf + (size_t)team_id * 4 * kXF;
+    T.xd = P.xd + (size_t)team_id * 4 * kXD;
+    T.bar = P.team_bar + team_id;
+    if (P.npair > 0) {
+        T.rank = (int)(blockIdx.x & 1);
+        T.size = 2;
+        for (;;) {
+            if (T.rank == 0 && threadIdx.x == 0) P.team_slot[team_id] = (int)atomicAdd(P.pair_next, 1u);
+            if (!team_sync(T)) return;
+            const int j = *(volatile int *)&P.team_slot[team_id];
+            if (j >= P.npair) break;
+            if (!batch_item(P, P.order[j], T, psm, info_sh, red_sh)) return;
+        }
+    }
+    T.rank = 0;
+    T.size = 1;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) item_sh = (int)atomicAdd(P.next, 1u);
+        if (threadIdx.x == 0) item_sh = P.npair + (int)atomicAdd(P.next, 1u);
         __syncthreads();
         const int j = item_sh;
         if (j >= P.count) return;
-        batch_item(P, P.order[j], psm, info_sh, red_sh);
+        if (!batch_item(P, P.order[j], T, psm, info_sh, red_sh)) return;
     }
 }
 
@@ -802,11 +950,20 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         fallback.clear();
         for (int64_t i = 0; i < count; ++i) fallback.push_back(i);
     };
-    // largest first (the same cost order as the single-matrix workers)
-    std::stable_sort(items.begin(), items.end(), [&](int64_t a, int64_t b) {
-        return (double)m[a] * n[a] * std::min(m[a], n[a]) > (double)m[b] * n[b] * std::min(m[b], n[b]);
-    });
+    // largest m n first (an item's work here is about m n (r + k) with
+    // r <= 128); items within a factor kPairFrac of the largest m n are taken
+    // by pairs of CTAs (EOD_BATCH_PAIR sets the factor: 0 pairs every item,
+    // above 1 none)
+    std::stable_sort(items.begin(), items.end(),
+                     [&](int64_t a, int64_t b) { return (double)m[a] * n[a] > (double)m[b] * n[b]; });
     const int64_t ne = (int64_t)items.size();
+    double pair_frac = kPairFrac;
+    if (const char *env = std::getenv("EOD_BATCH_PAIR")) pair_frac = std::atof(env);
+    int npair = 0;
+    {
+        const double top = (double)m[items[0]] * n[items[0]];
+        while (npair < ne && (double)m[items[npair]] * n[items[npair]] >= pair_frac * top) ++npair;
+    }
     int64_t mmax = 1, nmax = 1;
     for (int64_t i : items) {
         mmax = std::max(mmax, m[i]);
@@ -855,9 +1012,11 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         all_back();
         return EOD_OK;
     }
-    const int grid = (int)std::min<int64_t>(ne, sms);
+    const int grid = (int)std::min<int64_t>((ne + 1) / 2 * 2, sms / 2 * 2);   // clusters of two
+    const int nteams = grid / 2;
     const PLayout L = playout(mmax, nmax);
     std::vector<PRes> hres(ne);
+    for (PRes &rs : hres) rs.status = EOD_ETIMEOUT;   // what an item the launch did not finish reports
     std::vector<double> htd((size_t)ne * kPTdCap);
     cudaStream_t ps = nullptr;
     cudaGraph_t graph = nullptr;
@@ -871,7 +1030,9 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         PRes *dres;
         double *dtd;
         unsigned char *scratch;
-        unsigned *next;
+        unsigned *ctl;       // next, pair_next, err, team barriers, team slots
+        float *xf;
+        double *xd;
         unsigned long long *dphase = nullptr;
         const bool phases = g_phase_on.load() != 0;
         eod_status st = ar.get(&ditems, (size_t)ne);
@@ -880,11 +1041,15 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         if (st == EOD_OK) st = ar.get(&dres, (size_t)ne);
         if (st == EOD_OK) st = ar.get(&dtd, (size_t)ne * kPTdCap);
         if (st == EOD_OK) st = ar.get(&scratch, (size_t)(L.bytes * grid));
-        if (st == EOD_OK) st = ar.get(&next, (size_t)1);
+        const size_t nctl = 4 + 2 * (size_t)nteams;
+        if (st == EOD_OK) st = ar.get(&ctl, nctl);
+        if (st == EOD_OK) st = ar.get(&xf, (size_t)nteams * 4 * kXF);
+        if (st == EOD_OK) st = ar.get(&xd, (size_t)nteams * 4 * kXD);
         cudaError_t e = st == EOD_OK ? cudaSuccess : cudaErrorMemoryAllocation;
         if (e == cudaSuccess) e = cudaMemcpyAsync(ditems, hitems.data(), sizeof(PItem) * ne, cudaMemcpyHostToDevice, caller);
         if (e == cudaSuccess && dphase) e = cudaMemsetAsync(dphase, 0, sizeof(unsigned long long) * kPPhases, caller);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dorder, horder.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, caller);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dres, hres.data(), sizeof(PRes) * ne, cudaMemcpyHostToDevice, caller);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(ready, caller);
@@ -900,9 +1065,16 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         P.stride = L.bytes;
         P.mmax = mmax;
         P.nmax = nmax;
-        P.next = next;
+        P.next = ctl;
+        P.pair_next = ctl + 1;
+        P.err = (int *)(ctl + 2);
+        P.team_bar = ctl + 4;
+        P.team_slot = (int *)(ctl + 4 + nteams);
+        P.xf = xf;
+        P.xd = xd;
         P.phase = dphase;
         P.count = (int)ne;
+        P.npair = npair;
         P.k = k;
         P.tol_mode = o.tol_mode;
         P.compute_err = o.compute_err;
@@ -911,7 +1083,7 @@ eod_status factor_batched_persistent(const void *const *A, const int64_t *m, con
         // the queue reset and the persistent kernel, captured as one graph
         if (e == cudaSuccess) e = cudaStreamBeginCapture(ps, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = cudaMemsetAsync(next, 0, sizeof(unsigned), ps);
+            cudaError_t e1 = cudaMemsetAsync(ctl, 0, sizeof(unsigned) * nctl, ps);
             if (e1 == cudaSuccess) {
                 batch_kernel<<<grid, PT, smem, ps>>>(P);
                 e1 = cudaGetLastError();
