@@ -15,7 +15,10 @@ handed-back ones the requested precision, so the tests can tell them apart.
   the FP32 form's bounds of test_gpu_oracle_fullsize.compare;
 * edge cases (zero matrix, 1 x 1, wide, full rank below the capacity, a
   non-finite item beside good ones), a batch mixing persistent and
-  handed-back items, run-to-run determinism and freeing in any order.
+  handed-back items, run-to-run determinism and freeing in any order;
+* pairs of CTAs (the largest items, rows split between the two): the edge
+  cases and the mixed batch with every item on pairs and with none, and the
+  two schedules agreeing to FP32 rounding.
 """
 import hashlib
 import json
@@ -104,7 +107,12 @@ def test_persistent_factors_vs_oracle_elementwise(eod):
                 signal=min(10, ref["r"]))
 
 
-def test_persistent_edge_cases(eod):
+@pytest.mark.parametrize("pair", [None, "0"])
+def test_persistent_edge_cases(eod, monkeypatch, pair):
+    """Alone, and with every item on a pair of CTAs (EOD_BATCH_PAIR=0: the
+    1 x 1 item leaves one rank no rows)."""
+    if pair is not None:
+        monkeypatch.setenv("EOD_BATCH_PAIR", pair)
     rng = np.random.default_rng(11)
     items = [
         np.zeros((50, 40)),                                   # rank 0
@@ -129,10 +137,14 @@ def test_persistent_edge_cases(eod):
     assert res[4].rank == 37
 
 
-def test_mixed_batch_persistent_and_handed_back(eod):
+@pytest.mark.parametrize("pair", [None, "0", "2"])
+def test_mixed_batch_persistent_and_handed_back(eod, monkeypatch, pair):
     """Low-rank items finish in the persistent launch; a full-rank 300 x 260
     item exceeds its capacity and is factored by the single-matrix path with
-    the requested precision.  Every item matches the oracle's rank."""
+    the requested precision.  Every item matches the oracle's rank: with the
+    default split between pairs and single CTAs, every item on pairs, none."""
+    if pair is not None:
+        monkeypatch.setenv("EOD_BATCH_PAIR", pair)
     rng = np.random.default_rng(3)
     items = [W.exact_rank(m=400 + 10 * i, n=350, r=20 + 9 * i, seed=20 + i).A for i in range(4)]
     items.insert(2, rng.standard_normal((300, 260)))
@@ -145,6 +157,24 @@ def test_mixed_batch_persistent_and_handed_back(eod):
         assert res[i].rank == ref["r"], (i, res[i].rank, ref["r"])
         assert abs(res[i].rel_err - ref["rel_err"]) <= 1e-4
     assert res[2].rank == 260
+
+
+def test_pairs_and_single_ctas_agree(eod, monkeypatch):
+    """The same batch with every item on a pair of CTAs and with none: equal
+    ranks, RelErr and factors to FP32 rounding (the two differ only in the
+    order of the cross-row sums)."""
+    mats = [_dev32(W.exact_rank(m=900 + 57 * i, n=700 + 33 * i, r=10 + 9 * i, seed=30 + i).A) for i in range(8)]
+    monkeypatch.setenv("EOD_BATCH_PAIR", "0")
+    a, st_a = eod.factor_batched(mats, 1e-5, 3, block_k=32, tol_mode="rel", precision="mixed")
+    monkeypatch.setenv("EOD_BATCH_PAIR", "2")
+    b, st_b = eod.factor_batched(mats, 1e-5, 3, block_k=32, tol_mode="rel", precision="mixed")
+    assert st_a == st_b == [0] * 8
+    for x, y in zip(a, b):
+        assert x.precision == y.precision == EOD_PLAIN
+        assert x.rank == y.rank and x.blocks == y.blocks
+        assert abs(x.rel_err - y.rel_err) <= 1e-6
+        ax, ay = x.reconstruct(), y.reconstruct()
+        assert (torch.linalg.norm(ax - ay) / torch.linalg.norm(ay)).item() <= 1e-5
 
 
 def test_persistent_is_deterministic_and_frees_in_any_order(eod):
