@@ -699,6 +699,9 @@ __device__ __noinline__ bool batch_item(const PParams &P, int idx, Team &T, unsi
                 if (badsum != 0.0) { finish(EOD_ENONFINITE, -1.0); return true; }
                 eps = P.tol_mode == EOD_TOL_REL_FRO ? P.tol * norm : P.tol;
                 eps2 = eps * eps;
+                // below this the FP32 rounding of the sketch reaches |T(l,l)|:
+                // refused, as the single-matrix FP32 forms do
+                if (norm > 0.0 && eps < kPF32Floor * norm) { finish(EOD_EPRECISION, -1.0); return true; }
                 if (norm == 0.0) {
                     if (tid == 0 && lead) tdg[0] = 0.0;
                     ntd = 1;

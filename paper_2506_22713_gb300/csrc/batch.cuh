@@ -14,6 +14,7 @@ constexpr int kPTdCap = kPRcap + 2;
 constexpr int kPFallback = -1;    // item status: left to the single-matrix path
 constexpr int64_t kPMaxDim = 16384;   // largest m or n of an item of the persistent form
 constexpr int kPPhases = 11;          // phases of the measurement hook
+constexpr double kPF32Floor = 1e-5;   // eps below this x ||A||_F: EOD_EPRECISION (FP32 products cannot resolve it)
 
 // Factors items of FP32 data in one persistent launch on `s`.  Items that
 // finish there get their factors in out[i] and status in per_item[i];

@@ -82,7 +82,7 @@ template <typename T> constexpr double near_id_tau2() { return std::is_same<T, d
 
 // smallest eps / ||A||_F the FP32-data paths accept (see factor_impl)
 constexpr double kMixedFloor = 1e-5;
-constexpr double kF32Floor = 1e-5;
+constexpr double kF32Floor = kPF32Floor;   // the persistent batched launch applies the same
 
 template <typename T> struct Traits;
 template <> struct Traits<double> { static constexpr int dtype = EOD_F64; static constexpr double rho = 1e-10; };

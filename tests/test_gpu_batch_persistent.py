@@ -177,6 +177,16 @@ def test_pairs_and_single_ctas_agree(eod, monkeypatch):
         assert (torch.linalg.norm(ax - ay) / torch.linalg.norm(ay)).item() <= 1e-5
 
 
+def test_persistent_refuses_tol_below_the_fp32_floor(eod):
+    """eps below 1e-5 ||A||_F: EOD_EPRECISION, as a single FP32 or mixed call
+    answers (the FP32 rounding of the sketch reaches |T(l,l)| there)."""
+    a = W.exact_rank(m=200, n=150, r=10, seed=2).A
+    res, st = eod.factor_batched([_dev32(a), _dev32(a)], 1e-6, 1, block_k=16, tol_mode="rel", precision="mixed")
+    assert st == [eod.EOD_EPRECISION] * 2 and res == [None, None]
+    with pytest.raises(eod.EodError):
+        eod.factor(_dev32(a), 1e-6, 1, block_k=16, tol_mode="rel", precision="mixed")
+
+
 def test_persistent_is_deterministic_and_frees_in_any_order(eod):
     mats = [_dev32(W.exact_rank(m=200 + 31 * i, n=180 + 17 * i, r=5 + 7 * i, seed=i).A) for i in range(12)]
     a, st_a = eod.factor_batched(mats, 1e-5, 2, block_k=16, tol_mode="rel", precision="plain")
