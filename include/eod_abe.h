@@ -397,7 +397,9 @@ EOD_API eod_status eod_abe_debug_bounded_wait(int64_t budget_cycles, int32_t arr
  * for eod_abe_factor_batched's worker streams (default 8; the environment
  * variable EOD_BATCH_STREAMS overrides); "batch_block_k" (a = form, b = mean
  * m, c = mean n) for the k of batched items on those streams when
- * opts->block_k == 0.
+ * opts->block_k == 0; "core_leaf" (a = p, b = c = 0) for the leaf width (16,
+ * 32, 64, 128; default 64) of the blocked Cholesky of a p x p Gram in the
+ * CholQR passes (subspace iteration and Alg. 2 steps 9-10).
  * eod_abe_tuning_load(path) replaces the table by the file at path (NULL:
  * the default location); EOD_EINVAL for a malformed line (the table is then
  * left unchanged); a missing file empties it.  eod_abe_tuning_lookup returns

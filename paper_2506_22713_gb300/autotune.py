@@ -18,7 +18,11 @@ keys in include/eod_abe.h, eod_abe_tuning_load):
 * batch_block_k  k of Alg. 1 for the items of a batched call that run on
                  the worker streams (block_k = 0): the whole clipped pixel
                  batch timed per k and form (under concurrency fewer,
-                 wider blocks pay more than for one matrix of that size).
+                 wider blocks pay more than for one matrix of that size);
+* core_leaf      the leaf width (16, 32, 64, 128) of the blocked Cholesky in
+                 the CholQR passes, per Gram width p: whole factorisations
+                 timed with a one-row table loaded per candidate (a narrower
+                 leaf is faster per pivot but adds panel products).
 
 Every row covers a range around the measured case (a factor of about 1.5
 to each side of the sizes); of the rows that hold a case the nearest wins
@@ -244,6 +248,54 @@ def tune_batch_block_k(eod, torch, ks=(32, 64, 96, 128)):
     return rows, notes
 
 
+# -------------------------------------------------------------- core leaf --
+def tune_core_leaf(eod, torch, tmp_path, widths=(16, 32, 64, 128), reps=3):
+    import numpy as np
+    import workloads as W
+
+    # (name, workload, precision, dtype, k): the block sizes the block_k rows pick
+    cases = [("harmonic 8192^2", W.harmonic, "mixed", np.float32, 96),
+             ("harmonic 8192^2", W.harmonic, "plain", np.float64, 128),
+             ("image 2048^2", W.image_like, "plain", np.float64, 96)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rows, notes = [], []
+    try:
+        for name, make, prec, dtype, k in cases:
+            w = make()
+            A = torch.from_numpy(np.asfortranarray(w.A.astype(dtype))).cuda()
+            res, rank = {}, None
+            for nb in widths:
+                with open(tmp_path, "w") as fh:
+                    fh.write(f"core_leaf 1 1000000 0 0 0 0 {nb}\n")
+                if eod.eod_abe_tuning_load(tmp_path.encode()) != eod.EOD_OK:
+                    raise RuntimeError("tuning table did not load")
+                times = []
+                for rep in range(reps + 1):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    f = eod.factor(A, w.tol, w.seed, block_k=k, tol_mode="rel", precision=prec)
+                    e1.record()
+                    e1.synchronize()
+                    rank = f.rank
+                    f.close()
+                    if rep:
+                        times.append(e0.elapsed_time(e1))
+                res[nb] = statistics.median(times)
+            best = min(res, key=res.get)
+            form = "plain_f64" if dtype == np.float64 else prec
+            rows.append(("core_leaf", *_range(rank), 0, 0, 0, 0, best))
+            notes.append(f"core_leaf {name} {form} (p = {rank}): " + ", ".join(f"{nb}:{v:.2f}ms" for nb, v in res.items())
+                         + f" -> {best}")
+            del A
+            torch.cuda.empty_cache()
+    finally:
+        if os.path.exists(tmp_path):
+            os.remove(tmp_path)
+        eod.eod_abe_tuning_load((tmp_path + ".none").encode())
+    return rows, notes
+
+
 def write_table(path, rows, notes, meta):
     with open(path, "w") as fh:
         fh.write("# Tuned parameters of libeodabe.so, written by paper_2506_22713_gb300/autotune.py\n")
@@ -260,7 +312,7 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--out", required=True, help="where to write the table")
     p.add_argument("--quick", action="store_true", help="fewer cases (smoke run)")
-    p.add_argument("--skip", default="", help="comma list of f32_tile,block_k,batch_workers,batch_block_k to skip")
+    p.add_argument("--skip", default="", help="comma list of f32_tile,block_k,batch_workers,batch_block_k,core_leaf to skip")
     p.add_argument("--merge", action="store_true",
                    help="keep the rows (and their notes) of skipped parts from the table already at --out")
     args = p.parse_args(argv)
@@ -284,6 +336,11 @@ def main(argv=None):
         notes += n
     if "batch_block_k" not in skip:
         r, n = tune_batch_block_k(eod, torch, ks=(32, 96) if args.quick else (32, 64, 96, 128))
+        rows += r
+        notes += n
+    if "core_leaf" not in skip:
+        r, n = tune_core_leaf(eod, torch, args.out + ".leaf", widths=(32, 64) if args.quick else (16, 32, 64, 128),
+                              reps=1 if args.quick else 3)
         rows += r
         notes += n
     if "batch_workers" not in skip:

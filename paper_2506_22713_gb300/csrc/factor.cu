@@ -106,17 +106,28 @@ struct CoreWork {
     T *InvT = nullptr, *Tmp = nullptr;
     int *info = nullptr;
     int64_t pcap = 0, rows_cap = 0;
+    int nb = 64;   // leaf width of the current Cholesky (divides kPB)
 };
 
-static constexpr int kNB = 64;    // leaf width (one-CTA Cholesky)
-static constexpr int kPB = 256;   // panel width of the core Cholesky and triangular solve
+static constexpr int kNBMin = 16;   // narrowest leaf (sizes the leaves' status array)
+static constexpr int kPB = 256;     // panel width of the core Cholesky and triangular solve
+
+// Leaf width for the Cholesky of a p x p Gram: the tuned value (key
+// core_leaf, a = p), else 64.  A narrower leaf spends less time per pivot
+// (its in-CTA trailing update competes less with the pivot chain for the
+// SM's FP64 unit) at the price of more small panel products between leaves.
+static int core_leaf_width(int64_t p) {
+    int64_t v = 0;
+    if (tuned_value("core_leaf", p, 0, 0, &v) && (v == 16 || v == 32 || v == 64 || v == 128)) return (int)v;
+    return 64;
+}
 
 template <typename T>
 static eod_status chol_panel_leaves(CoreWork<T> &w, int64_t p, int64_t j0, int64_t pe, double shift, Scratch *ws,
                                     cudaStream_t s, double *Rout, double *RiJ) {
     GemmExtra ex;
-    for (int64_t l0 = j0; l0 < pe; l0 += kNB) {
-        const int64_t lb = std::min<int64_t>(kNB, pe - l0), L = l0 / kNB;
+    for (int64_t l0 = j0; l0 < pe; l0 += w.nb) {
+        const int64_t lb = std::min<int64_t>(w.nb, pe - l0), L = l0 / w.nb;
         double *RiL = RiJ + (l0 - j0) * (1 + kPB);   // the leaf's inverse, on the diagonal of R_JJ^{-1}
         if (l0 > j0)   // G(l, l:pe) -= R(j0:l0, l)^T R(j0:l0, l:pe)
             EOD_CU((gemm<double, double, double, double>(true, false, lb, pe - l0, l0 - j0, -1.0, Rout + j0 + l0 * p,
@@ -141,7 +152,7 @@ static eod_status panel_inverse(CoreWork<T> &w, int64_t p, int64_t j0, int64_t j
     GemmExtra au, bu;
     au.a_upper = true;
     bu.b_upper = true;
-    for (int64_t h = kNB; h < jb; h *= 2) {
+    for (int64_t h = w.nb; h < jb; h *= 2) {
         for (int64_t a0 = 0; a0 + h < jb; a0 += 2 * h) {
             const int64_t b0 = a0 + h, bl = std::min<int64_t>(h, jb - b0);
             // T = A^-1 B;  RiJ(a, b) = -T C^-1
@@ -178,12 +189,12 @@ static eod_status chol_panels(CoreWork<T> &w, int64_t p, double shift, HostMirro
                                                           ws, s)));
         }
     }
-    const int64_t nblk = (p + kNB - 1) / kNB;
+    const int64_t nblk = (p + w.nb - 1) / w.nb;
     std::vector<int> infos(2 * nblk);
     EOD_CU(cudaMemcpyAsync(infos.data(), w.info, sizeof(int) * 2 * nblk, cudaMemcpyDeviceToHost, s));
     EOD_CU(cudaStreamSynchronize(s));
     for (int64_t J = 0; J < nblk; ++J) {
-        const int64_t jb = std::min<int64_t>(kNB, p - J * kNB);
+        const int64_t jb = std::min<int64_t>(w.nb, p - J * w.nb);
         if (infos[2 * J] != jb || infos[2 * J + 1] != CHOL_ALL) return EOD_EPRECISION;
     }
     return EOD_OK;
@@ -258,6 +269,7 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
     GemmExtra sym;
     sym.upper_only = true;
     double *Racc = w.R;  // running product
+    w.nb = core_leaf_width(p);
     int passes = 2;
     double shift = 0.0;
     for (int pass = 0; pass < passes; ++pass) {
@@ -758,7 +770,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     // work space of the CholQR passes (subspace iteration and core)
     CoreWork<T> cw;
     cw.pcap = r;
-    const int64_t nblk = (r + kNB - 1) / kNB;
+    const int64_t nblk = (r + kNBMin - 1) / kNBMin;
     EOD_TRY(ar.get(&cw.G, (size_t)r * r));
     EOD_TRY(ar.get(&cw.R, (size_t)r * r));
     EOD_TRY(ar.get(&cw.Rp, (size_t)r * r));

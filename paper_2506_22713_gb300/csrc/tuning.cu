@@ -9,8 +9,14 @@
 //                  product (16, 32, 64 or 128)
 //   batch_workers  a = count, b = mean m, c = mean n   -> worker streams of
 //                  eod_abe_factor_batched
+//   batch_block_k  a = form, b = mean m, c = mean n    -> k of the batched
+//                  items on those streams
+//   core_leaf      a = p (b = c = 0)                   -> leaf width of the
+//                  blocked Cholesky of a p x p Gram (16, 32, 64 or 128)
 // Line format: key a_lo a_hi b_lo b_hi c_lo c_hi value (inclusive ranges);
-// '#' starts a comment; the first matching row wins.  The file is
+// '#' starts a comment; of the rows of a key whose ranges hold the query,
+// the nearest wins (smallest sum of |log x - log centre| over the axes, the
+// centre the geometric mean of the row's bounds).  The file is
 // $EOD_TUNING_FILE if set, else tuning.txt beside the library; a missing
 // file means no tuned values.
 #include "common.cuh"
