@@ -109,6 +109,8 @@ struct CoreWork {
     int nb = 64;   // leaf width of the current Cholesky (divides kPB)
 };
 
+// rows from which the mixed forms form U = Q Qh on the tensor cores
+static constexpr int64_t kTfMinRows = 1024;
 static constexpr int kNBMin = 16;   // narrowest leaf (sizes the leaves' status array)
 static constexpr int kPB = 256;     // panel width of the core Cholesky and triangular solve
 
@@ -892,6 +894,33 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
         const OzOperand qr{oz.Qr, nullptr, 1, oz.cap8, m * oz.cap8};
         const OzOperand qho{qhs, eqh, 0, r8, r * r8};
         EOD_CU(oz_gemm_ops(qr, qho, m, r, r, 1.0, 0.0, (double *)U, m, ex, ws.err_flag, s));
+    } else if (mixed && std::is_same<T, float>::value && m >= kTfMinRows && r >= 32) {
+        // U = Q Qh on the tensor cores as three TF32 products of split
+        // operands, X = X_hi + X_lo (X_hi Y_hi + X_hi Y_lo + X_lo Y_hi: about
+        // 2^-21 relative, the accuracy of an FP32 product); TF32 operands are
+        // K-major, so Q is split transposed (r4 x m)
+        const int64_t r4 = round_up(r, 4);
+        float *q_hi, *q_lo, *h_hi, *h_lo;
+        EOD_TRY(ar.get(&q_hi, (size_t)(r4 * m)));
+        EOD_TRY(ar.get(&q_lo, (size_t)(r4 * m)));
+        EOD_TRY(ar.get(&h_hi, (size_t)(r4 * r)));
+        EOD_TRY(ar.get(&h_lo, (size_t)(r4 * r)));
+        EOD_CU(split_transpose_tf32((const float *)Qb, m, r, m, q_hi, q_lo, r4, s));
+        EOD_CU(split_tf32((const float *)Rt, r, r, r, h_hi, h_lo, r4, s));
+        TcGemmDesc g;
+        g.M = m;
+        g.N = r;
+        g.K = r;
+        g.tf32 = true;
+        g.npairs = 3;
+        const TcOperand qh{q_hi, r, m, r4}, ql{q_lo, r, m, r4}, hh{h_hi, r, r, r4}, hl{h_lo, r, r, r4};
+        g.a[0] = qh, g.b[0] = hh;
+        g.a[1] = qh, g.b[1] = hl;
+        g.a[2] = ql, g.b[2] = hh;
+        g.D = (float *)U;
+        g.ldd = m;
+        g.err_flag = ws.err_flag;
+        EOD_CU(tc_gemm_run(g, &ws, s));
     } else {
         EOD_CU((gemm<T, T, T, T>(false, false, m, r, r, 1.0, Qb, m, Rt, r, 0.0, U, m, ex, &ws, s)));
     }
