@@ -106,7 +106,8 @@ struct CoreWork {
     T *InvT = nullptr, *Tmp = nullptr;
     int *info = nullptr;
     int64_t pcap = 0, rows_cap = 0;
-    int nb = 64;   // leaf width of the current Cholesky (divides kPB)
+    int nb = 64;       // leaf width of the current Cholesky (divides kPB)
+    bool tc = false;   // mixed forms: the solves' products on the tensor cores
 };
 
 // rows from which the mixed forms form U = Q Qh on the tensor cores
@@ -202,10 +203,68 @@ static eod_status chol_panels(CoreWork<T> &w, int64_t p, double shift, HostMirro
     return EOD_OK;
 }
 
+// W <- W R^{-1} on the tensor cores (the mixed forms, FP32 data): per panel
+// J, X_J = W_J R_JJ^{-1} written over W_J, then W(:, pe:p) -= X_J R(J, pe:p),
+// each as three TF32 products of split operands (X = X_hi + X_lo: about
+// 2^-21 relative, the accuracy of an FP32 product).  TF32 operands are
+// K-major, so W_J and X_J are split transposed; the FP64 blocks of R and of
+// R_JJ^{-1} (zero below the diagonal) are rounded to FP32 and split.
+// EOD_EUNSUPPORTED, with nothing launched, when the scratch has no room.
+static eod_status trsm_panels_tc(const double *RiD, float *W, int64_t rows, int64_t ldw, int64_t p,
+                                 const double *R, Scratch *ws, cudaStream_t s) {
+    const int64_t pb = round_up(std::min<int64_t>(p, kPB), 4);   // ld of the split blocks
+    const size_t mark = ws->mark();
+    float *wth = (float *)ws->take(sizeof(float) * (size_t)(pb * rows));
+    float *wtl = (float *)ws->take(sizeof(float) * (size_t)(pb * rows));
+    float *bh = (float *)ws->take(sizeof(float) * (size_t)(pb * p));
+    float *bl = (float *)ws->take(sizeof(float) * (size_t)(pb * p));
+    if (!wth || !wtl || !bh || !bl) {
+        ws->release(mark);
+        return EOD_EUNSUPPORTED;
+    }
+    // W(:, c0 : c0+N) = alpha (W_J or X_J, split in wth/wtl) (the split block in bh/bl) + beta W(:, c0 : c0+N)
+    auto product = [&](int64_t N, int64_t K, float *D, float alpha, float beta) -> cudaError_t {
+        TcGemmDesc g;
+        g.M = rows;
+        g.N = N;
+        g.K = K;
+        g.tf32 = true;
+        g.npairs = 3;
+        const TcOperand ah{wth, K, rows, pb}, al{wtl, K, rows, pb}, b_h{bh, K, N, pb}, b_l{bl, K, N, pb};
+        g.a[0] = ah, g.b[0] = b_h;
+        g.a[1] = ah, g.b[1] = b_l;
+        g.a[2] = al, g.b[2] = b_h;
+        g.D = D;
+        g.ldd = ldw;
+        g.alpha = alpha;
+        g.beta = beta;
+        g.err_flag = ws->err_flag;
+        return tc_gemm_run(g, ws, s);
+    };
+    for (int64_t j0 = 0; j0 < p; j0 += kPB) {
+        const int64_t pe = std::min<int64_t>(p, j0 + kPB), jb = pe - j0;
+        const double *RiJ = RiD + (j0 / kPB) * kPB * kPB;
+        EOD_CU(split_transpose_tf32(W + j0 * ldw, rows, jb, ldw, wth, wtl, pb, s));
+        EOD_CU(split_tf32_f64(RiJ, jb, jb, kPB, bh, bl, pb, s));
+        EOD_CU(product(jb, jb, W + j0 * ldw, 1.f, 0.f));   // X_J over W_J (read from its split copy)
+        if (pe < p) {
+            EOD_CU(split_transpose_tf32(W + j0 * ldw, rows, jb, ldw, wth, wtl, pb, s));
+            EOD_CU(split_tf32_f64(R + j0 + pe * p, jb, p - pe, p, bh, bl, pb, s));
+            EOD_CU(product(p - pe, jb, W + pe * ldw, -1.f, 1.f));
+        }
+    }
+    ws->release(mark);
+    return EOD_OK;
+}
+
 // W <- W R^{-1}, R upper p x p (ld p) with the diagonal panels' inverses in w.RiD.
 template <typename T>
 static eod_status trsm_panels(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64_t p, const double *R,
                               Scratch *ws, cudaStream_t s) {
+    if (w.tc && std::is_same<T, float>::value && rows >= kTfMinRows && p >= 128) {
+        const eod_status st = trsm_panels_tc(w.RiD, (float *)W, rows, ldw, p, R, ws, s);
+        if (st != EOD_EUNSUPPORTED) return st;
+    }
     GemmExtra ex, exb;
     exb.b_upper = true;
     for (int64_t j0 = 0; j0 < p; j0 += kPB) {
@@ -772,6 +831,7 @@ static eod_status factor_impl(const T *A, int64_t m, int64_t n, int64_t lda, dou
     // work space of the CholQR passes (subspace iteration and core)
     CoreWork<T> cw;
     cw.pcap = r;
+    cw.tc = mixed;
     const int64_t nblk = (r + kNBMin - 1) / kNBMin;
     EOD_TRY(ar.get(&cw.G, (size_t)r * r));
     EOD_TRY(ar.get(&cw.R, (size_t)r * r));

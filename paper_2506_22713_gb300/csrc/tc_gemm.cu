@@ -95,6 +95,7 @@ struct Params {
     int npairs;
     float *D;              // EPI_STORE: output (or split partial base), column-major
     int64_t ldd;
+    float alpha, beta;     // EPI_STORE: D = alpha acc + beta D (split partials: 1, 0)
     int64_t split_stride;  // elements between split partials (0: no split)
     const float *R;        // EPI_ERR: reference
     int64_t ldr;
@@ -287,14 +288,20 @@ __global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kern
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int64_t col = n0 + c + j;
-                        if (col < p.N) p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = v[j];
+                        if (col < p.N) {
+                            float *d = p.D + (int64_t)blockIdx.z * p.split_stride + row + col * p.ldd;
+                            *d = p.beta != 0.f ? fmaf(p.alpha, v[j], p.beta * *d) : p.alpha * v[j];
+                        }
                     }
                 }
             }
         } else if (iters == 0 && row < p.M) {
             for (int c = 0; c < BN_; ++c) {
                 const int64_t col = n0 + c;
-                if (col < p.N) p.D[(int64_t)blockIdx.z * p.split_stride + row + col * p.ldd] = 0.0f;
+                if (col < p.N) {
+                    float *d = p.D + (int64_t)blockIdx.z * p.split_stride + row + col * p.ldd;
+                    *d = p.beta != 0.f ? p.beta * *d : 0.0f;
+                }
             }
         }
     }
@@ -308,12 +315,13 @@ __global__ void __launch_bounds__(NTHREADS, EPI == EPI_ERR ? 2 : 1) tc_gemm_kern
 }
 
 __global__ void split_reduce_kernel(const float *__restrict__ part, int64_t M, int64_t N, int S, float *D,
-                                    int64_t ldd) {
+                                    int64_t ldd, float alpha, float beta) {
     const int64_t total = M * N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.f;
         for (int z = 0; z < S; ++z) s += part[(int64_t)z * total + e];
-        D[(e % M) + (e / M) * ldd] = s;
+        float *d = D + (e % M) + (e / M) * ldd;
+        *d = beta != 0.f ? fmaf(alpha, s, beta * *d) : alpha * s;
     }
 }
 
@@ -401,13 +409,15 @@ __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
 }
 
 // X (rows x cols, ldx) -> X_hi, X_lo (same shape, ld ldo), FP32 storage.
-__global__ void split_tf32_kernel(const float *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+// (FP64 input is rounded to FP32 first)
+template <typename TI>
+__global__ void split_tf32_kernel(const TI *__restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
                                   float *__restrict__ hi, float *__restrict__ lo, int64_t ldo) {
     const int64_t total = rows * cols;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / rows, i = e - j * rows;
         float h, l;
-        split_tf32(X[i + j * ldx], h, l);
+        split_tf32((float)X[i + j * ldx], h, l);
         hi[i + j * ldo] = h;
         lo[i + j * ldo] = l;
     }
@@ -518,10 +528,14 @@ cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s) {
         p.D = part;
         p.ldd = g.M;
         p.split_stride = g.M * g.N;
+        p.alpha = 1.f;
+        p.beta = 0.f;
     } else {
         p.D = g.D;
         p.ldd = g.ldd;
         p.split_stride = 0;
+        p.alpha = g.alpha;
+        p.beta = g.beta;
     }
     cudaError_t e;
     if (g.tf32)
@@ -537,7 +551,7 @@ cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s) {
     if (splits > 1) {
         int blocks = (int)std::min<int64_t>((g.M * g.N + 255) / 256, 4 * kNumSMs * 8);
         count_launch();
-        split_reduce_kernel<<<blocks, 256, 0, s>>>(part, g.M, g.N, splits, g.D, g.ldd);
+        split_reduce_kernel<<<blocks, 256, 0, s>>>(part, g.M, g.N, splits, g.D, g.ldd, g.alpha, g.beta);
         EOD_CUDA_TRY(cudaGetLastError());
         ws->release(mark);
     }
@@ -564,7 +578,17 @@ cudaError_t split_tf32(const float *X, int64_t rows, int64_t cols, int64_t ldx, 
     ProfScope prof(PROF_STREAM, 0.0, 12.0 * rows * cols, s);
     count_launch();
     const int64_t blocks = std::min<int64_t>((rows * cols + 255) / 256, 8LL * kNumSMs * 4);
-    tc::split_tf32_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, rows, cols, ldx, hi, lo, ldo);
+    tc::split_tf32_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(X, rows, cols, ldx, hi, lo, ldo);
+    return cudaGetLastError();
+}
+
+cudaError_t split_tf32_f64(const double *X, int64_t rows, int64_t cols, int64_t ldx, float *hi, float *lo,
+                           int64_t ldo, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    ProfScope prof(PROF_STREAM, 0.0, 16.0 * rows * cols, s);
+    count_launch();
+    const int64_t blocks = std::min<int64_t>((rows * cols + 255) / 256, 8LL * kNumSMs * 4);
+    tc::split_tf32_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(X, rows, cols, ldx, hi, lo, ldo);
     return cudaGetLastError();
 }
 

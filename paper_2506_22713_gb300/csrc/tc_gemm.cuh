@@ -17,7 +17,8 @@ struct TcOperand {
     int64_t inner = 0, outer = 0, ld = 0;
 };
 
-// D (M x N, FP32, column-major) = sum over pairs p of op(a[p]) * op(b[p]).
+// D (M x N, FP32, column-major) = alpha * sum over pairs p of op(a[p]) *
+// op(b[p]) + beta * D (D is read only when beta != 0).
 // B operands are always K-major (K = inner).  A operands are K-major (inner =
 // K, outer = M) unless a_mn_major, then inner = M and outer = K.
 // EPI_ERR: instead of storing D, each CTA writes sum((ref - D)^2) over its
@@ -36,6 +37,7 @@ struct TcGemmDesc {
     double *err_partials = nullptr;
     int *err_flag = nullptr;      // set to 1 by a CTA whose bounded wait ran out
     int bn = 0;                   // N tile (32, 64, 128, 256); 0 = by N
+    float alpha = 1.f, beta = 0.f;
 };
 
 cudaError_t tc_gemm_run(const TcGemmDesc &g, Scratch *ws, cudaStream_t s);
@@ -57,6 +59,9 @@ cudaError_t split_tf32(const float *X, int64_t rows, int64_t cols, int64_t ldx, 
                        cudaStream_t s);
 cudaError_t split_transpose_tf32(const float *X, int64_t rows, int64_t cols, int64_t ldx, float *hi, float *lo,
                                  int64_t ldt, cudaStream_t s);
+// The same split of FP64 data rounded to FP32 first (same layout, ld ldo).
+cudaError_t split_tf32_f64(const double *X, int64_t rows, int64_t cols, int64_t ldx, float *hi, float *lo,
+                           int64_t ldo, cudaStream_t s);
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
