@@ -258,10 +258,11 @@ static eod_status trsm_panels_tc(const double *RiD, float *W, int64_t rows, int6
 }
 
 // W <- W R^{-1}, R upper p x p (ld p) with the diagonal panels' inverses in w.RiD.
+// With allow_tc, the mixed forms' products run on the tensor cores.
 template <typename T>
 static eod_status trsm_panels(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64_t p, const double *R,
-                              Scratch *ws, cudaStream_t s) {
-    if (w.tc && std::is_same<T, float>::value && rows >= kTfMinRows && p >= 128) {
+                              Scratch *ws, cudaStream_t s, bool allow_tc) {
+    if (allow_tc && w.tc && std::is_same<T, float>::value && rows >= kTfMinRows && p >= 128) {
         const eod_status st = trsm_panels_tc(w.RiD, (float *)W, rows, ldw, p, R, ws, s);
         if (st != EOD_EUNSUPPORTED) return st;
     }
@@ -359,7 +360,11 @@ static eod_status cholqr2(CoreWork<T> &w, T *W, int64_t rows, int64_t ldw, int64
         }
         if (st != EOD_OK) return st;
         shift = 0.0;
-        EOD_TRY(trsm_panels(w, W, rows, ldw, p, Rpass, ws, s));
+        // The first pass's solve sets how close the next pass's Gram is to I
+        // (its near-identity test is at the FP32 level), so it stays on the
+        // FP32 FFMA products; the later passes (R near I) may take the
+        // tensor cores' TF32 products (~2^-21 relative).
+        EOD_TRY(trsm_panels(w, W, rows, ldw, p, Rpass, ws, s, pass > 0));
         if (pass > 0) {
             // Racc = Rpass * Rout (both upper), then Rout = Racc
             GemmExtra tri;
