@@ -71,11 +71,11 @@ typedef enum {
                               tensor cores with FP32 accumulation: A split into
                               three BF16 terms for the sketch (exact for FP32
                               data), two for the projection and the error;
-                              from m >= 1024 rows also U = Q Qh and the CholQR
-                              solves W R^-1 of the core (panels of >= 128
-                              columns) as three TF32 products of split
-                              operands (~2^-21 relative); Gram/Cholesky/rank
-                              test/core R factors in FP64 */
+                              from m >= 1024 rows also U = Q Qh and the
+                              solves W R^-1 of the second and later CholQR
+                              passes (Grams of >= 128 columns) as three TF32
+                              products of split operands (~2^-21 relative);
+                              Gram/Cholesky/rank test/core R factors in FP64 */
     EOD_MIXED_TF32 = 2     /* the same contractions with tcgen05 kind::tf32:
                               A, Q and C split into two TF32 terms (hi = the
                               value with 13 low significand bits cleared,
