@@ -296,6 +296,24 @@ def tune_core_leaf(eod, torch, tmp_path, widths=(16, 32, 64, 128), reps=3):
     return rows, notes
 
 
+def kept_rows(path, keys):
+    """The rows and '# measured:' notes of the given keys in the table at
+    path (what --merge keeps for the parts it skips)."""
+    rows, notes = [], []
+    with open(path) as fh:
+        for line in fh:
+            line = line.strip()
+            if line.startswith("# measured: "):
+                note = line[len("# measured: "):]
+                if note.split(" ", 1)[0] in keys:
+                    notes.append(note)
+            elif line and not line.startswith("#"):
+                f = line.split()
+                if f[0] in keys:
+                    rows.append(tuple([f[0]] + [int(x) for x in f[1:]]))
+    return rows, notes
+
+
 def write_table(path, rows, notes, meta):
     with open(path, "w") as fh:
         fh.write("# Tuned parameters of libeodabe.so, written by paper_2506_22713_gb300/autotune.py\n")
@@ -348,20 +366,9 @@ def main(argv=None):
         rows += r
         notes += n
     if args.merge and os.path.exists(args.out):
-        kept_rows, kept_notes = [], []
-        with open(args.out) as fh:
-            for line in fh:
-                line = line.strip()
-                if line.startswith("# measured: "):
-                    note = line[len("# measured: "):]
-                    if note.split(" ", 1)[0] in skip:
-                        kept_notes.append(note)
-                elif line and not line.startswith("#"):
-                    f = line.split()
-                    if f[0] in skip:
-                        kept_rows.append(tuple([f[0]] + [int(x) for x in f[1:]]))
-        rows += kept_rows
-        notes += kept_notes
+        r, n = kept_rows(args.out, skip)
+        rows += r
+        notes += n
     meta = {"when": datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%dT%H:%M:%SZ"),
             "gpu": torch.cuda.get_device_name(0), "torch": torch.__version__,
             "seconds": f"{time.time() - t0:.0f}"}

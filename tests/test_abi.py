@@ -141,6 +141,42 @@ def test_tuning_table_parse_lookup_and_reload(eod, tmp_path):
         eod.eod_abe_tuning_load(None)
 
 
+def test_autotune_merge_keeps_skipped_keys_and_round_trips(eod, tmp_path):
+    """autotune --merge keeps the rows and notes of the skipped keys from the
+    table already at --out; the table it writes parses in the library, and
+    the committed table holds the measured core leaf width at both ranks."""
+    from paper_2506_22713_gb300 import autotune
+
+    old = tmp_path / "old.txt"
+    old.write_text("# measured: block_k harmonic 8192^2 mixed: k=64:6.5ms -> 64\n"
+                   "# measured: core_leaf harmonic 8192^2 mixed (p = 455): 32:6.6ms, 64:6.3ms -> 64\n"
+                   "# measured: batch_workers pixel batch 256 mixed: 8:884ms, 12:834ms -> 12\n"
+                   "block_k 2 2 4096 16384 4096 16384 64\n"
+                   "core_leaf 304 683 0 0 0 0 64\n"
+                   "batch_workers 64 4096 563 2253 592 2371 12\n")
+    rows, notes = autotune.kept_rows(str(old), {"core_leaf", "batch_workers"})
+    assert rows == [("core_leaf", 304, 683, 0, 0, 0, 0, 64), ("batch_workers", 64, 4096, 563, 2253, 592, 2371, 12)]
+    assert [n.split(" ", 1)[0] for n in notes] == ["core_leaf", "batch_workers"]
+    new = tmp_path / "new.txt"
+    autotune.write_table(str(new), [("block_k", 2, 2, 4096, 16384, 4096, 16384, 96)] + rows,
+                         ["block_k harmonic 8192^2 mixed: k=96:6.3ms -> 96"] + notes, {"gpu": "test"})
+    text = new.read_text()
+    assert text.count("# measured: ") == 3
+    try:
+        assert eod.eod_abe_tuning_load(str(new).encode()) == eod.EOD_OK
+        assert eod.tuning_lookup("block_k", 2, 8192, 8192) == 96
+        assert eod.tuning_lookup("core_leaf", 455, 0, 0) == 64
+        assert eod.tuning_lookup("core_leaf", 2037, 0, 0) is None
+        assert eod.tuning_lookup("batch_workers", 256, 1100, 1100) == 12
+        committed = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                 "paper_2506_22713_gb300", "tuning.txt")
+        assert eod.eod_abe_tuning_load(committed.encode()) == eod.EOD_OK
+        assert eod.tuning_lookup("core_leaf", 455, 0, 0) == 64
+        assert eod.tuning_lookup("core_leaf", 2037, 0, 0) == 64
+    finally:
+        eod.eod_abe_tuning_load(None)
+
+
 def test_f32_gemm_hook_rejects_bad_arguments(eod):
     P = ctypes.c_void_p(16)   # never dereferenced: rejected before any launch
     assert eod.eod_abe_debug_f32_gemm(48, 0, 0, 8, 8, 8, 1.0, P, 8, P, 8, 0.0, P, 8, None) == eod.EOD_EINVAL
