@@ -32,3 +32,21 @@ def test_every_ncu_command_keeps_the_clocks():
         for line in text.splitlines():
             if re.match(r"\s*(\S+\s*&&\s*)?ncu\s+-", line) or re.search(r"&&\s*ncu\s+-", line):
                 assert "--clock-control none" in line, f"{os.path.basename(path)}: {line.strip()[:120]}"
+
+
+def test_roofline_arithmetic():
+    """achieved = the launches' method flops (bytes for streaming kinds) over
+    their summed device time; each kind against its own peak."""
+    peaks = (1940.0e3, 1728.0e3, 6800.0, "measured")   # BF16 burst / sustained GFLOP/s, HBM GB/s
+    rec = {"ms": 2.0, "flops": 4.0e9, "bytes": 1.0e9, "launches": 4}
+    expect = {"chol": bench.FP64_SM_PEAK_GFLOPS, "gemm_simt": bench.FP64_PEAK_GFLOPS,
+              "gemm_simt_f32": bench.FP32_PEAK_GFLOPS, "tc_gemm": 1728.0e3,
+              "oz_gemm": 1728.0e3 / bench.OZ_PAIRS}
+    for kind, peak in expect.items():
+        r = bench.roofline_of(kind, rec, peaks)
+        assert r["achieved"] == 4.0e9 / 2.0e-3 / 1e9 and r["unit"] == "GFLOP/s"
+        assert r["peak"] == peak and abs(r["frac"] - r["achieved"] / peak) < 1e-12
+        assert r["flops_per_launch"] == 1.0e9 and r["bytes_per_launch"] == 2.5e8
+    r = bench.roofline_of("stream", rec, peaks)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["achieved"] == 1.0e9 / 2.0e-3 / 1e9
+    assert abs(r["frac"] - r["achieved"] / 6800.0) < 1e-12
